@@ -1,0 +1,252 @@
+/*
+ * satsplat.h -- C ABI of the GB300 affine 2D-Gaussian-splat (surfel) rasterizer.
+ *
+ * The operation is the differentiable rasterizer of SatSplat (Song, Kim, Qin):
+ *   - affine camera x = F [p; 1], F split into the screen rows [B_xy | b_xy]
+ *     and the fixed depth row B_z = [0 0 -1], b_z = max_altitude
+ *       (Sec. 3.1 Eq. affine_camera; Sec. 3.2 Eq. decompose_affine_camera,
+ *        Eq. depth_affine_camera);
+ *   - per-camera learnable delta F'_xy = F_xy + dF_xy (Sec. 3.3);
+ *   - 2D splats P(u,v) = p + s_u t_u u + s_v t_v v (Sec. 3.1 Eq. 2dgs_splat_param),
+ *     intersected with the parallel camera rays analytically:
+ *     u = Q x + q, Q = (B_xy R S')^-1, q = -Q (B_xy p + b_xy)
+ *       (Sec. 3.2 Eq. affine2dgs_screen2uv, Eq. affine2dgs_Qq);
+ *   - lower-bounded Gaussian max(G(u), G((x - c)/sigma)); only the screen-space
+ *     term when |det(B_xy R S')| < det_eps (Sec. 3.2, degenerate solutions);
+ *   - tiles, splats ordered by the height-based depth of their centres, and
+ *     front-to-back alpha blending of colour, depth and normal
+ *       (Sec. 3.2 Eq. rasterization; normal definition);
+ *   - the sun-direction camera B_sun = B'_xy (I - [0 0 s]),
+ *     s = (cos(phi)/tan(theta), sin(phi)/tan(theta), 1), rendering depth for
+ *     shadow mapping (Sec. 3.3 Eq. sun_camera_Bxy; Supp. A);
+ *   - per-camera 3x4 colour correction C A + c (Sec. 3.1 Eq. image_formation);
+ *   - the reverse-mode adjoint of all of the above.
+ * Constants the paper leaves open (alpha threshold, alpha clamp, early-stop
+ * transmittance, sigma, det threshold) are fields of ss_raster_opts.
+ *
+ * Conventions for every entry point:
+ *   - The caller owns all memory; the library never allocates and keeps no
+ *     state between calls other than what it writes into the caller's
+ *     workspace.  Device pointers must be on the current CUDA device.
+ *   - Calls are asynchronous on the given stream, except where stated.  Host
+ *     arguments are read during the call and may be released afterwards.
+ *   - Arguments are validated on the host before anything is launched; a bad
+ *     argument returns SS_ERR_INVALID_ARG and launches nothing.  A failed
+ *     launch returns SS_ERR_CUDA.  No exception crosses the boundary.
+ *   - Gradient outputs ACCUMULATE (+=); the caller zeroes them.
+ *   - A frame is one set of (splats, cameras, passes, options, workspace).
+ *     ss_project_splats, ss_bin_and_sort, ss_rasterize_fwd and
+ *     ss_rasterize_bwd must be called in that order for the same frame; each
+ *     reads what the previous one wrote into the workspace.
+ */
+#ifndef SATSPLAT_H
+#define SATSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ss_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  SS_OK = 0,
+  SS_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment, option or layout */
+  SS_ERR_CAPACITY = 2,    /* the intersection list did not fit: see ss_bin_and_sort */
+  SS_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  SS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  SS_ERR_NONFINITE = 5    /* a splat or camera value was NaN/Inf (that splat is culled) */
+} ss_status;
+
+typedef enum { SS_F32 = 0, SS_BF16 = 1 } ss_dtype;
+
+/* Passes of a frame.  The render targets of a frame are, in this order: the main
+ * view of every camera (if SS_PASS_MAIN), then the sun view of every camera (if
+ * SS_PASS_SUN).  n_targets = n_cams * (number of bits set). */
+enum { SS_PASS_MAIN = 1, SS_PASS_SUN = 2 };
+
+/* Splat attributes (Sec. 3.1 Eq. 2dgs_splat_param).  DEVICE pointers to
+ * component-planar arrays [C][n_pad] of `dtype` (fp32 or bf16), 16-byte aligned.
+ *   means   [3][n_pad]  p = (x, y, z) in world units (normalised UTM); z is height
+ *   scales  [2][n_pad]  s_u, s_v > 0 (already activated)
+ *   quats   [4][n_pad]  rotation (w, x, y, z), any non-zero norm (normalised inside)
+ *   opacity [n_pad]     o in (0, 1) (already activated)
+ *   rgb     [3][n_pad]  per-splat colour (albedo); no spherical harmonics
+ * n_pad >= n, a multiple of 8.  Entries n..n_pad-1 are never read. */
+typedef struct {
+  const void* means;
+  const void* scales;
+  const void* quats;
+  const void* opacity;
+  const void* rgb;
+  int64_t n;
+  int64_t n_pad;
+  int32_t dtype; /* ss_dtype */
+  int32_t reserved;
+} ss_splats;
+
+/* One affine camera (HOST memory; its fixed geometry).  F_xy maps world
+ * coordinates straight to pixel coordinates: pixel (i, j) covers [i, i+1) x
+ * [j, j+1) and is sampled at its centre (i + 0.5, j + 0.5).  The depth row is
+ * fixed: depth = max_alt - height (Sec. 3.2 Eq. depth_affine_camera).  The sun
+ * view (Sec. 3.3, Supp. A) uses B_sun = shadow_scale * B'_xy (I - [0 0 s]) and
+ * b_sun = shadow_scale * b'_xy on a shadow_w x shadow_h image; its depth is the
+ * same height-based depth. */
+typedef struct {
+  float F_xy[2][4];
+  float max_alt;
+  int32_t width, height;
+  float sun_phi;   /* sun azimuth, radians */
+  float sun_theta; /* sun elevation, radians, in (0, pi/2] */
+  int32_t shadow_w, shadow_h;
+  float shadow_scale;
+} ss_camera;
+
+/* Rasterizer options.  ss_default_opts() fills the defaults in brackets. */
+typedef struct {
+  int32_t tile_w, tile_h; /* screen tile [16 x 16]; also 32 x 8 and 8 x 32 */
+  int32_t batch;          /* splats staged per block in shared memory [256]; 64, 128 or 256 */
+  int32_t persistent;     /* [0] one block per tile; 1: one persistent launch that pulls
+                             (target, tile) work items from a queue */
+  float sigma_px;         /* screen-space low-pass sigma, pixels [1/sqrt(2)] */
+  float det_eps;          /* |det M| threshold, px^2 [1e-6] */
+  float alpha_min;        /* a splat contributes iff alpha >= alpha_min [1/255] */
+  float alpha_max;        /* alpha = min(alpha_max, o G^) [0.99] */
+  float t_min;            /* stop before the splat that takes T below t_min [1e-4] */
+  int32_t reserved[3];
+} ss_raster_opts;
+
+/* Per render target I/O (device pointers; row-major [H][W] planes of the
+ * target's own size, planar [3][H][W] for 3-channel outputs).
+ *   rgb     corrected colour C A + c (main targets only; NULL = not written)
+ *   depth   sum_i w_i z_i, z_i the depth of the ray-splat intersection, not
+ *           normalised by alpha (NULL = not written)
+ *   normal  sum_i w_i n_i, n_i = R[:,2] flipped to face the sensor (main only)
+ *   alpha   1 - T_final (NULL = not written)
+ *   T_final, last  saved state for the backward pass (REQUIRED by ss_rasterize_fwd
+ *           and ss_rasterize_bwd): final transmittance and the end of the
+ *           pixel's walk in the sorted intersection list
+ *   d_rgb, d_depth, d_normal, d_alpha  upstream gradients (backward; NULL = 0) */
+typedef struct {
+  float* rgb;
+  float* depth;
+  float* normal;
+  float* alpha;
+  float* T_final;
+  uint32_t* last;
+  const float* d_rgb;
+  const float* d_depth;
+  const float* d_normal;
+  const float* d_alpha;
+} ss_target_io;
+
+/* Gradients with respect to the splat attributes: FP32 DEVICE arrays [C][n_pad]
+ * laid out like ss_splats (quats: w.r.t. the unnormalised input).  Accumulated. */
+typedef struct {
+  float* means;
+  float* scales;
+  float* quats;
+  float* opacity;
+  float* rgb;
+  int64_t n_pad;
+} ss_splat_grads;
+
+/* Fill `opts` with the defaults listed above.  Never fails. */
+void ss_default_opts(ss_raster_opts* opts);
+
+/* Human-readable name of a status code (static storage). */
+const char* ss_status_string(ss_status status);
+
+/* Bytes of device workspace a frame needs, for an intersection-list capacity
+ * of `capacity` (tile, splat) pairs over all targets.  The workspace holds the
+ * assembled cameras, the per-(target, splat) projected records, the
+ * visibility order, the sorted intersection lists, per-tile ranges, the
+ * per-(target, splat) gradient records and a status block.  Host only.
+ * Errors: SS_ERR_INVALID_ARG for bad cameras/options/sizes. */
+ss_status ss_workspace_size(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
+                            int32_t passes, const ss_raster_opts* opts, int64_t capacity,
+                            size_t* bytes);
+
+/* Camera assembly and per-splat projection (K1), Sec. 3.2-3.3: for every target
+ * and splat, F' = F + dF, the sun camera when the target is a sun view, the
+ * normalised rotation, M = B R S', det, Q = M^-1, the projected centre, the
+ * depth of the centre and its slopes along u and v, the normal flipped toward
+ * the sensor, log-opacity, the conservative screen extent and the tile
+ * rectangle.  Splats with opacity < alpha_min are culled.
+ *   dF: DEVICE [n_cams][2][4] fp32 camera deltas, or NULL (zero).
+ *   ws: DEVICE workspace of ws_bytes >= ss_workspace_size(..., capacity).
+ * Non-finite splat values are counted in the status block (ss_frame_status). */
+ss_status ss_project_splats(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
+                            int32_t passes, const float* dF, const ss_raster_opts* opts,
+                            void* ws, size_t ws_bytes, int64_t capacity, ss_stream_t stream);
+
+/* Tile binning and sorting (K2), Sec. 3.2 rasterization paragraph: one stable
+ * radix sort of the splats by height (descending; ties by the smaller index)
+ * serves every target, because the depth key is view independent; then every
+ * (target, tile, splat) overlap is emitted in that order and stably radix
+ * sorted by tile, and per-tile [start, end) ranges are built.
+ *   needed: HOST out, may be NULL.  If non-NULL the call synchronises the
+ *     stream, stores the number of intersections the frame needs, and returns
+ *     SS_ERR_CAPACITY when it exceeds `capacity` (the lists are then
+ *     truncated and the frame must be re-run with a larger workspace).  If
+ *     NULL nothing is synchronised (CUDA-graph friendly) and an overflow is
+ *     reported by ss_frame_status. */
+ss_status ss_bin_and_sort(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
+                          int32_t passes, const ss_raster_opts* opts, void* ws, size_t ws_bytes,
+                          int64_t capacity, int64_t* needed, ss_stream_t stream);
+
+/* Forward rasterization (K3), Sec. 3.2 Eq. rasterization and Sec. 3.1
+ * Eq. image_formation (the C A + c part): per pixel, front to back over the
+ * tile's list, alpha = min(alpha_max, o G^), contributing iff >= alpha_min,
+ * stop before T would fall below t_min; outputs per ss_target_io.
+ *   color: DEVICE [n_cams][3][4] fp32 [C | c], or NULL (identity).
+ *   io:    HOST array of n_targets ss_target_io (T_final and last required). */
+ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
+                           int32_t passes, const float* color, const ss_raster_opts* opts,
+                           const ss_target_io* io, void* ws, size_t ws_bytes, int64_t capacity,
+                           ss_stream_t stream);
+
+/* Backward (K4 + K5): the adjoint of ss_rasterize_fwd and ss_project_splats for
+ * the same frame.  Per pixel the walk runs in reverse from `last`, recovering
+ * the transmittance from T_final; per-splat partials are reduced across each
+ * warp and block before global atomics into per-(target, splat) records, which
+ * are then chained through the projection to the splat attributes and to the
+ * camera deltas (through the sun camera for sun targets) and summed over
+ * targets.
+ *   grads:   accumulated splat gradients (required).
+ *   d_dF:    DEVICE [n_cams][2][4] fp32, accumulated, or NULL.
+ *   d_color: DEVICE [n_cams][3][4] fp32, accumulated, or NULL. */
+ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
+                           int32_t passes, const float* dF, const float* color,
+                           const ss_raster_opts* opts, const ss_target_io* io,
+                           const ss_splat_grads* grads, float* d_dF, float* d_color, void* ws,
+                           size_t ws_bytes, int64_t capacity, ss_stream_t stream);
+
+/* Sun-direction shadow depth (K6), Sec. 3.3 and Supp. A: project, bin and
+ * rasterize the sun view of every camera (depth and alpha only).  Equivalent
+ * to the three calls above with passes = SS_PASS_SUN.  `io` holds n_cams
+ * targets; `needed` as in ss_bin_and_sort. */
+ss_status ss_shadow_depth(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
+                          const float* dF, const ss_raster_opts* opts, const ss_target_io* io,
+                          void* ws, size_t ws_bytes, int64_t capacity, int64_t* needed,
+                          ss_stream_t stream);
+
+/* Status block of a frame's workspace.  SYNCHRONISES the stream.
+ *   needed:    intersections the last ss_bin_and_sort needed
+ *   nonfinite: splats culled for non-finite values by the last projection
+ *   flags:     bit 0 = intersection overflow, bit 1 = a bounded wait timed out
+ * Returns SS_ERR_CAPACITY / SS_ERR_TIMEOUT / SS_ERR_NONFINITE when set, else SS_OK. */
+ss_status ss_frame_status(const void* ws, size_t ws_bytes, int64_t* needed, int64_t* nonfinite,
+                          int32_t* flags, ss_stream_t stream);
+
+/* Number of SMs of the current device and the library's compiled architecture
+ * (e.g. 1030 for sm_103a); a test hook to check the build.  Host only. */
+int32_t ss_device_info(int32_t* num_sms, int32_t* arch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SATSPLAT_H */

@@ -1,0 +1,230 @@
+"""ctypes binding of ``include/satsplat.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point without the ``ss_``
+prefix and forwards to it.  Tensors are passed as raw device pointers; the
+CUDA stream is torch's current stream unless one is given.  Loading fails
+loudly when the compiled library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsatsplat.so")
+
+SS_OK, SS_ERR_INVALID_ARG, SS_ERR_CAPACITY, SS_ERR_CUDA, SS_ERR_TIMEOUT, SS_ERR_NONFINITE = range(6)
+SS_F32, SS_BF16 = 0, 1
+SS_PASS_MAIN, SS_PASS_SUN = 1, 2
+
+P = ctypes.c_void_p
+
+
+class ss_splats(ctypes.Structure):
+    _fields_ = [("means", P), ("scales", P), ("quats", P), ("opacity", P), ("rgb", P),
+                ("n", ctypes.c_int64), ("n_pad", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ss_camera(ctypes.Structure):
+    _fields_ = [("F_xy", (ctypes.c_float * 4) * 2), ("max_alt", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("sun_phi", ctypes.c_float), ("sun_theta", ctypes.c_float),
+                ("shadow_w", ctypes.c_int32), ("shadow_h", ctypes.c_int32),
+                ("shadow_scale", ctypes.c_float)]
+
+
+class ss_raster_opts(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("sigma_px", ctypes.c_float),
+                ("det_eps", ctypes.c_float), ("alpha_min", ctypes.c_float),
+                ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class ss_target_io(ctypes.Structure):
+    _fields_ = [("rgb", P), ("depth", P), ("normal", P), ("alpha", P), ("T_final", P), ("last", P),
+                ("d_rgb", P), ("d_depth", P), ("d_normal", P), ("d_alpha", P)]
+
+
+class ss_splat_grads(ctypes.Structure):
+    _fields_ = [("means", P), ("scales", P), ("quats", P), ("opacity", P), ("rgb", P),
+                ("n_pad", ctypes.c_int64)]
+
+
+EXPORTS = ["ss_default_opts", "ss_status_string", "ss_workspace_size", "ss_project_splats",
+           "ss_bin_and_sort", "ss_rasterize_fwd", "ss_rasterize_bwd", "ss_shadow_depth",
+           "ss_frame_status", "ss_device_info"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SatSplatError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+def load(path: Optional[str] = None):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"CUDA library not built: {p} is missing (run paper_2606_28581_gb300.build.build())")
+        L = ctypes.CDLL(p)
+        I32, I64, SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        PS, PC, PO = ctypes.POINTER(ss_splats), ctypes.POINTER(ss_camera), ctypes.POINTER(ss_raster_opts)
+        PIO, PG = ctypes.POINTER(ss_target_io), ctypes.POINTER(ss_splat_grads)
+        L.ss_default_opts.argtypes = [PO]
+        L.ss_default_opts.restype = None
+        L.ss_status_string.argtypes = [ctypes.c_int]
+        L.ss_status_string.restype = ctypes.c_char_p
+        L.ss_workspace_size.argtypes = [PS, PC, I32, I32, PO, I64, ctypes.POINTER(SZ)]
+        L.ss_project_splats.argtypes = [PS, PC, I32, I32, P, PO, P, SZ, I64, P]
+        L.ss_bin_and_sort.argtypes = [PS, PC, I32, I32, PO, P, SZ, I64, ctypes.POINTER(I64), P]
+        L.ss_rasterize_fwd.argtypes = [PS, PC, I32, I32, P, PO, PIO, P, SZ, I64, P]
+        L.ss_rasterize_bwd.argtypes = [PS, PC, I32, I32, P, P, PO, PIO, PG, P, P, P, SZ, I64, P]
+        L.ss_shadow_depth.argtypes = [PS, PC, I32, P, PO, PIO, P, SZ, I64, ctypes.POINTER(I64), P]
+        L.ss_frame_status.argtypes = [P, SZ, ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                      ctypes.POINTER(I32), P]
+        L.ss_device_info.argtypes = [ctypes.POINTER(I32), ctypes.POINTER(I32)]
+        L.ss_device_info.restype = I32
+        for name in EXPORTS:
+            if name not in ("ss_default_opts", "ss_status_string", "ss_device_info"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().ss_status_string(int(status)).decode()
+    except Exception:  # pragma: no cover - only used in error paths
+        return "status"
+
+
+def _check(status: int, where: str, allow=()):
+    if status != SS_OK and status not in allow:
+        raise SatSplatError(status, where)
+    return status
+
+
+# ------------------------------------------------------------------------------ marshalling
+def ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+def stream_ptr(stream=None) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream) or None
+
+
+def default_opts(**overrides) -> ss_raster_opts:
+    o = ss_raster_opts()
+    load().ss_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def make_cameras(cams: Sequence) -> ctypes.Array:
+    """Array of ss_camera from objects with F_xy (2x4), max_alt, width, height, sun_phi,
+    sun_theta, shadow_w, shadow_h, shadow_scale attributes."""
+    arr = (ss_camera * len(cams))()
+    for i, c in enumerate(cams):
+        F = [[float(v) for v in row] for row in c.F_xy]
+        for a in range(2):
+            for b in range(4):
+                arr[i].F_xy[a][b] = F[a][b]
+        arr[i].max_alt = float(c.max_alt)
+        arr[i].width, arr[i].height = int(c.width), int(c.height)
+        arr[i].sun_phi, arr[i].sun_theta = float(c.sun_phi), float(c.sun_theta)
+        arr[i].shadow_w, arr[i].shadow_h = int(c.shadow_w), int(c.shadow_h)
+        arr[i].shadow_scale = float(c.shadow_scale)
+    return arr
+
+
+def make_splats(means, scales, quats, opacity, rgb, n: int) -> ss_splats:
+    """Splat descriptor of planar device tensors [C][n_pad] (fp32 or bf16)."""
+    import torch
+    dt = means.dtype
+    assert all(t.dtype == dt for t in (scales, quats, opacity, rgb)), "one storage dtype"
+    s = ss_splats()
+    s.means, s.scales, s.quats, s.opacity, s.rgb = (ptr(means), ptr(scales), ptr(quats),
+                                                    ptr(opacity), ptr(rgb))
+    s.n = int(n)
+    s.n_pad = int(means.shape[-1])
+    s.dtype = SS_BF16 if dt == torch.bfloat16 else SS_F32
+    return s
+
+
+# ------------------------------------------------------------------------------ entry points
+def workspace_size(splats, cams, n_cams, passes, opts, capacity) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().ss_workspace_size(ctypes.byref(splats), cams, n_cams, passes, ctypes.byref(opts),
+                                    int(capacity), ctypes.byref(out)), "ss_workspace_size")
+    return int(out.value)
+
+
+def project_splats(splats, cams, n_cams, passes, dF, opts, ws, ws_bytes, capacity, stream=None):
+    return _check(load().ss_project_splats(ctypes.byref(splats), cams, n_cams, passes, ptr(dF),
+                                           ctypes.byref(opts), ptr(ws), int(ws_bytes), int(capacity),
+                                           stream_ptr(stream)), "ss_project_splats")
+
+
+def bin_and_sort(splats, cams, n_cams, passes, opts, ws, ws_bytes, capacity, sync_needed=True,
+                 stream=None):
+    """Returns (status, needed).  With sync_needed the stream is synchronised and the
+    needed intersection count returned; SS_ERR_CAPACITY is returned, not raised."""
+    needed = ctypes.c_int64(-1)
+    st = load().ss_bin_and_sort(ctypes.byref(splats), cams, n_cams, passes, ctypes.byref(opts),
+                                ptr(ws), int(ws_bytes), int(capacity),
+                                ctypes.byref(needed) if sync_needed else None, stream_ptr(stream))
+    _check(st, "ss_bin_and_sort", allow=(SS_ERR_CAPACITY,))
+    return st, int(needed.value)
+
+
+def rasterize_fwd(splats, cams, n_cams, passes, color, opts, io, ws, ws_bytes, capacity, stream=None):
+    return _check(load().ss_rasterize_fwd(ctypes.byref(splats), cams, n_cams, passes, ptr(color),
+                                          ctypes.byref(opts), io, ptr(ws), int(ws_bytes), int(capacity),
+                                          stream_ptr(stream)), "ss_rasterize_fwd")
+
+
+def rasterize_bwd(splats, cams, n_cams, passes, dF, color, opts, io, grads, d_dF, d_color, ws, ws_bytes,
+                  capacity, stream=None):
+    return _check(load().ss_rasterize_bwd(ctypes.byref(splats), cams, n_cams, passes, ptr(dF), ptr(color),
+                                          ctypes.byref(opts), io, ctypes.byref(grads), ptr(d_dF),
+                                          ptr(d_color), ptr(ws), int(ws_bytes), int(capacity),
+                                          stream_ptr(stream)), "ss_rasterize_bwd")
+
+
+def shadow_depth(splats, cams, n_cams, dF, opts, io, ws, ws_bytes, capacity, sync_needed=True, stream=None):
+    needed = ctypes.c_int64(-1)
+    st = load().ss_shadow_depth(ctypes.byref(splats), cams, n_cams, ptr(dF), ctypes.byref(opts), io,
+                                ptr(ws), int(ws_bytes), int(capacity),
+                                ctypes.byref(needed) if sync_needed else None, stream_ptr(stream))
+    _check(st, "ss_shadow_depth", allow=(SS_ERR_CAPACITY,))
+    return st, int(needed.value)
+
+
+def frame_status(ws, ws_bytes, stream=None):
+    needed, nonfinite, flags = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+    st = load().ss_frame_status(ptr(ws), int(ws_bytes), ctypes.byref(needed), ctypes.byref(nonfinite),
+                                ctypes.byref(flags), stream_ptr(stream))
+    return st, int(needed.value), int(nonfinite.value), int(flags.value)
+
+
+def device_info():
+    sms, arch = ctypes.c_int32(0), ctypes.c_int32(0)
+    load().ss_device_info(ctypes.byref(sms), ctypes.byref(arch))
+    return int(sms.value), int(arch.value)

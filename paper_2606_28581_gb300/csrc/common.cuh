@@ -1,0 +1,191 @@
+// Shared device-side definitions of the GB300 affine 2DGS rasterizer.
+//
+// Data layout in HBM (one frame = one workspace):
+//   TargetCam   [T]                 assembled camera of every render target
+//   geom        [T][n_pad] 3 x f4   cx, cy, cx_lo, cy_lo | Q00 Q01 Q10 Q11 | lno, ex(sign=degenerate), ey, zc
+//   feat        [T][n_pad] 2 x f4   dzdu, dzdv, nx, ny | nz, r, g, b
+//   rect        [T][n_pad] 4 x u16  tile rectangle x0, y0, x1, y1 (empty: x0 > x1)
+//   grad        [T][n_pad] 16 f32   d(loss)/d of the projected quantities (see GradField)
+//   lists       capacity x (tile key u32, splat index u32), sorted by tile, then front to back
+//   ranges      [total tiles] uint2 [start, end) into the lists
+// The projected centre is kept as an unevaluated float pair (hi + lo): it is about
+// 10^3 px in magnitude while the per-pixel offset x - c must be accurate to ~1e-7 px.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "satsplat.h"
+
+namespace ss {
+
+constexpr int kMaxCams = 64;
+constexpr int kMaxTargets = 2 * kMaxCams;
+constexpr int kGradFields = 16;
+
+// Per-(target, splat) gradient record fields.
+enum GradField {
+  GF_Q00 = 0, GF_Q01, GF_Q10, GF_Q11,  // d/dQ
+  GF_CX, GF_CY,                        // d/dc (projected centre)
+  GF_LNO,                              // d/d(log opacity)
+  GF_ZC, GF_DZDU, GF_DZDV,             // d/d(depth at centre, depth slopes)
+  GF_NX, GF_NY, GF_NZ,                 // d/d(normal after the flip)
+  GF_R, GF_G, GF_B                     // d/d(rgb)
+};
+
+// Status block at the start of the workspace (256 bytes).
+struct StatusBlock {
+  unsigned long long n_isect;    // intersections the frame needs
+  unsigned long long nonfinite;  // splats culled for non-finite values
+  unsigned int flags;            // bit 0 overflow, bit 1 timeout
+  unsigned int work_fwd;         // persistent work-queue counters
+  unsigned int work_bwd;
+  unsigned int n_isect32;        // min(n_isect, capacity): the count the sort kernels use
+  unsigned int pad[56];
+};
+static_assert(sizeof(StatusBlock) == 256, "status block size");
+
+enum { FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2 };
+
+// Assembled camera of one render target (written on the device by the assembly kernel).
+struct __align__(16) TargetCam {
+  float B[2][3];    // F'_xy screen block, rounded
+  float Blo[2][3];  // rounding residual of F + dF
+  float b[2];
+  float blo[2];
+  float maxalt;     // b_z
+  float vs[3];      // unit viewing direction toward the sensor (z >= 0)
+  float S;          // sun view: pixels per main-view pixel (1 for main views)
+  float s[3];       // sun view: flattening direction (cos phi/tan th, sin phi/tan th, 1); 0 for main
+  int32_t W, H, tiles_x, tiles_y;
+  int32_t tile_base;
+  int32_t cam, sun, pad;
+};
+
+// Host-known static part of a target.
+struct TargetStatic {
+  int32_t W, H, tiles_x, tiles_y, tile_base, cam, sun;
+  float S;
+};
+
+struct CamRaw {
+  float F[8];
+  float max_alt, phi, theta;
+};
+
+struct TargetIO {
+  float* rgb;
+  float* depth;
+  float* normal;
+  float* alpha;
+  float* T_final;
+  uint32_t* last;
+  const float* d_rgb;
+  const float* d_depth;
+  const float* d_normal;
+  const float* d_alpha;
+};
+
+// ---------------------------------------------------------------- error-free transforms
+// Knuth's two-sum and the FMA two-product (exact rounding residuals).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+// (hi, lo) += a * b for a float-float accumulator, a = ah + al, b = bh + bl
+__device__ __forceinline__ void ff_fma(float& hi, float& lo, float ah, float al, float bh, float bl) {
+  float p, pe;
+  two_prod(ah, bh, p, pe);
+  float s, se;
+  two_sum(hi, p, s, se);
+  lo = __fadd_rn(lo, __fadd_rn(se, __fadd_rn(pe, __fmaf_rn(ah, bl, __fmul_rn(al, bh)))));
+  hi = s;
+}
+__device__ __forceinline__ void ff_renorm(float& hi, float& lo) {
+  float s, e;
+  two_sum(hi, lo, s, e);
+  hi = s;
+  lo = e;
+}
+
+// 2x2 determinant a*d - b*c with Kahan's FMA scheme (error ~1.5 ulp even under cancellation).
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+  float w = __fmul_rn(b, c);
+  float e = __fmaf_rn(-b, c, w);
+  float f = __fmaf_rn(a, d, -w);
+  return __fadd_rn(f, e);
+}
+
+// ---------------------------------------------------------------- storage loads
+__device__ __forceinline__ float load_attr(const float* p, int64_t i) { return __ldg(p + i); }
+__device__ __forceinline__ float load_attr(const __nv_bfloat16* p, int64_t i) {
+  return __bfloat162float(p[i]);
+}
+
+// Order-preserving map of a float to uint32 (ascending).
+__device__ __forceinline__ uint32_t float_order(float x) {
+  uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// ---------------------------------------------------------------- per-pixel evaluation
+// The one definition of a splat's alpha at a pixel, shared by the forward and the
+// backward kernels so that both take every threshold decision identically.
+struct PairEval {
+  float dx, dy;   // x - c
+  float u, v;     // uv coordinates (0 for degenerate splats)
+  float alpha;    // min(alpha_max, o G^)
+  bool uwin;      // the uv Gaussian won the max (ties: uv)
+  bool clamped;   // alpha_max reached
+  bool contrib;   // alpha >= alpha_min
+};
+
+struct EvalConsts {
+  float inv2s2;   // 1 / (2 sigma^2)
+  float amin, amax;
+  float ln_amin_slack;  // ln(alpha_min) - slack: below it no exp is evaluated
+};
+
+__device__ __forceinline__ PairEval eval_pair(const float4 g0, const float4 g1, const float4 g2,
+                                              float x, float y, const EvalConsts& k) {
+  PairEval e;
+  e.dx = __fsub_rn(__fsub_rn(x, g0.x), g0.z);
+  e.dy = __fsub_rn(__fsub_rn(y, g0.y), g0.w);
+  const bool deg = g2.y < 0.0f;
+  e.u = __fmaf_rn(g1.y, e.dy, __fmul_rn(g1.x, e.dx));
+  e.v = __fmaf_rn(g1.w, e.dy, __fmul_rn(g1.z, e.dx));
+  float pu = __fmul_rn(-0.5f, __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v)));
+  float ps = __fmul_rn(-__fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)), k.inv2s2);
+  if (deg) {
+    pu = -INFINITY;
+    e.u = 0.0f;
+    e.v = 0.0f;
+  }
+  e.uwin = pu >= ps;
+  const float p = e.uwin ? pu : ps;
+  const float lp = __fadd_rn(p, g2.x);  // ln(o G^)
+  e.clamped = false;
+  e.contrib = false;
+  e.alpha = 0.0f;
+  if (lp >= k.ln_amin_slack) {
+    const float og = __expf(lp);
+    e.clamped = og > k.amax;
+    e.alpha = e.clamped ? k.amax : og;
+    e.contrib = e.alpha >= k.amin;
+  }
+  return e;
+}
+
+#define SS_CUDA_TRY(expr)                              \
+  do {                                                 \
+    cudaError_t _e = (expr);                           \
+    if (_e != cudaSuccess) return SS_ERR_CUDA;         \
+  } while (0)
+
+}  // namespace ss

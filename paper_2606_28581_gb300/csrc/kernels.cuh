@@ -1,0 +1,138 @@
+// Kernel parameter blocks and launcher declarations (internal to the library).
+#pragma once
+
+#include "common.cuh"
+
+namespace ss {
+
+struct AssembleParams {
+  CamRaw cams[kMaxCams];
+  TargetStatic tg[kMaxTargets];
+  int32_t n_targets;
+  const float* dF;  // [n_cams][8] or null
+  TargetCam* out;
+};
+
+struct ProjectCommon {
+  const void* means;
+  const void* scales;
+  const void* quats;
+  const void* opacity;
+  const void* rgb;
+  int64_t n, n_pad;
+  int32_t n_targets;
+  const TargetCam* tcams;
+};
+
+struct ProjectParams {
+  ProjectCommon c;
+  float4* geom;  // [T][n_pad][3]
+  float4* feat;  // [T][n_pad][2]
+  ushort4* rect; // [T][n_pad]
+  StatusBlock* status;
+  float amin, ln_amin, sigma, det_eps;
+  int32_t tile_w, tile_h;
+};
+
+struct GradOut {
+  float* means;
+  float* scales;
+  float* quats;
+  float* opacity;
+  float* rgb;
+  int64_t n_pad;
+};
+
+struct ProjectBwdParams {
+  ProjectCommon c;
+  const ushort4* rect;
+  const float* grad;  // [T][n_pad][16]
+  GradOut g;
+  float* d_dF;        // [n_cams][8] or null
+  float amin, det_eps;
+};
+
+// Binning (K2) -----------------------------------------------------------------------
+struct BinParams {
+  const TargetCam* tcams;
+  int32_t n_targets;
+  int64_t n, n_pad;
+  const ushort4* rect;      // [T][n_pad]
+  const uint32_t* order;    // [n] splat indices, front to back
+  uint32_t* counts;         // [T * n]
+  const uint32_t* offsets;  // [T * n] exclusive scan of counts (saturated)
+  uint32_t* keys;           // [capacity] global tile id
+  uint32_t* vals;           // [capacity] splat index
+  int64_t capacity;
+  StatusBlock* status;
+};
+
+// Rasterization (K3 / K4) ----------------------------------------------------------------
+struct RasterParams {
+  const TargetCam* tcams;
+  const float4* geom;
+  const float4* feat;
+  const uint32_t* vals;    // sorted splat indices
+  const uint2* ranges;     // [total_tiles]
+  const uint32_t* items;   // optional work order of global tile ids (persistent)
+  StatusBlock* status;
+  float* grad;             // [T][n_pad][16] (backward)
+  const float* color;      // [n_cams][12] or null
+  float* d_color;          // [n_cams][12] or null
+  int64_t n_pad;
+  int32_t n_targets, total_tiles;
+  EvalConsts k;
+  float t_min;
+  TargetIO io[kMaxTargets];
+};
+
+cudaError_t launch_assemble(const AssembleParams& p, cudaStream_t st);
+cudaError_t launch_project(const ProjectParams& p, int dtype, cudaStream_t st);
+cudaError_t launch_project_bwd(const ProjectBwdParams& p, int dtype, cudaStream_t st);
+
+// radix sort / scan primitives (sort.cu)
+struct ScanPlan {
+  int64_t n;
+  int levels;
+  int64_t level_n[8];
+  size_t level_off[8];  // offsets (elements, uint64) into the scratch
+  size_t scratch_elems; // uint64 elements
+};
+ScanPlan plan_scan(int64_t n);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, unsigned long long* scratch,
+                               const ScanPlan& plan, unsigned long long* total, cudaStream_t st);
+
+struct RadixPlan {
+  int64_t capacity;     // max elements
+  int64_t nblocks;      // tiles of kRadixTile
+  ScanPlan hist_scan;   // over 256 * nblocks histogram entries
+};
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;
+RadixPlan plan_radix(int64_t capacity);
+// Stable LSD radix sort of (key, value) pairs on key bits [bit_lo, bit_hi).  The element
+// count is n_host, or *n_dev when n_dev is not null (device-resident count).  Returns in
+// *in_b whether the sorted result ended in the b buffers.
+cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
+                             int64_t n_host, const uint32_t* n_dev, int bit_lo, int bit_hi,
+                             uint32_t* hist, uint32_t* hist_off, unsigned long long* scan_scratch,
+                             const RadixPlan& plan, bool* in_b, cudaStream_t st);
+
+cudaError_t launch_height_keys(const void* means, int dtype, int64_t n, int64_t n_pad, uint32_t* keys,
+                               uint32_t* vals, cudaStream_t st);
+cudaError_t launch_counts(const BinParams& p, cudaStream_t st);
+cudaError_t launch_emit(const BinParams& p, cudaStream_t st);
+cudaError_t launch_finish_count(StatusBlock* status, const uint32_t* counts_last,
+                                const uint32_t* offsets_last, const unsigned long long* total,
+                                int64_t capacity, cudaStream_t st);
+cudaError_t launch_ranges(const uint32_t* keys, const StatusBlock* status, uint2* ranges,
+                          int64_t capacity, cudaStream_t st);
+
+// raster (raster.cu)
+cudaError_t launch_raster_fwd(const RasterParams& p, int tile_w, int tile_h, int batch, bool persistent,
+                              int num_sms, cudaStream_t st);
+cudaError_t launch_raster_bwd(const RasterParams& p, int tile_w, int tile_h, int batch, bool persistent,
+                              int num_sms, cudaStream_t st);
+
+}  // namespace ss

@@ -1,0 +1,355 @@
+// Tile binning and sorting (K2), Sec. 3.2 rasterization paragraph.
+//
+// The visibility key is the height-based depth of a splat's centre (Eq. depth_affine_camera),
+// which is the same for every view, so one stable sort of the splats by height (descending,
+// ties by index) serves all targets.  Every (target, splat, tile) overlap is then emitted in
+// that order and stably sorted by the global tile id: within a tile the list stays front to
+// back.  Both sorts are a hand-written stable LSD radix sort (8-bit digits, per-block digit
+// histograms, a device-wide exclusive scan, and a stable scatter that ranks equal digits with
+// warp match masks in element order).
+#include "kernels.cuh"
+
+namespace ss {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// ------------------------------------------------------------------------------------------
+// exclusive scan (uint32 in, uint32 out saturated, uint64 block sums)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v,
+                                                                   unsigned long long* total) {
+  __shared__ unsigned long long warp_tot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = lane < kScanThreads / 32 ? warp_tot[lane] : 0ull;
+    unsigned long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;
+    if (lane == kScanThreads / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  unsigned long long r = warp_tot[warp] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const Tin* in, int64_t n,
+                                                                    unsigned long long* sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  unsigned long long s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) s += (unsigned long long)in[base + i];
+  __shared__ unsigned long long tot;
+  (void)block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const Tin* in, Tout* out, int64_t n,
+                                                                  const unsigned long long* offs,
+                                                                  unsigned long long* total) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  unsigned long long v[kScanItems];
+  unsigned long long s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (base + i < n) ? (unsigned long long)in[base + i] : 0ull;
+    s += v[i];
+  }
+  __shared__ unsigned long long tot;
+  unsigned long long run = block_exclusive_scan(s, &tot);
+  if (offs) run += offs[blockIdx.x];
+  else if (threadIdx.x == 0 && total) *total = tot;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) {
+      if (sizeof(Tout) == 4)
+        out[base + i] = (Tout)(run > 0xffffffffull ? 0xffffffffull : run);
+      else
+        out[base + i] = (Tout)run;
+    }
+    run += v[i];
+  }
+}
+
+ScanPlan plan_scan(int64_t n) {
+  ScanPlan p{};
+  p.n = n;
+  int64_t s = n;
+  size_t off = 0;
+  p.levels = 0;
+  // level l >= 1 holds the block sums of level l - 1
+  while (s > kScanTile) {
+    s = (s + kScanTile - 1) / kScanTile;
+    p.level_n[p.levels] = s;
+    p.level_off[p.levels] = off;
+    off += (size_t)s;
+    ++p.levels;
+  }
+  p.scratch_elems = off + 1;  // + the total
+  return p;
+}
+
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, unsigned long long* scratch,
+                               const ScanPlan& plan, unsigned long long* total, cudaStream_t st) {
+  if (n == 0) return cudaMemsetAsync(total, 0, sizeof(unsigned long long), st);
+  const int L = plan.levels;
+  if (L == 0) {
+    scan_down_kernel<uint32_t, uint32_t><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
+    return cudaGetLastError();
+  }
+  // up: block sums
+  scan_reduce_kernel<uint32_t><<<(unsigned)plan.level_n[0], kScanThreads, 0, st>>>(
+      in, n, scratch + plan.level_off[0]);
+  for (int l = 1; l < L; ++l)
+    scan_reduce_kernel<unsigned long long><<<(unsigned)plan.level_n[l], kScanThreads, 0, st>>>(
+        scratch + plan.level_off[l - 1], plan.level_n[l - 1], scratch + plan.level_off[l]);
+  // top level fits one block
+  scan_down_kernel<unsigned long long, unsigned long long><<<1, kScanThreads, 0, st>>>(
+      scratch + plan.level_off[L - 1], scratch + plan.level_off[L - 1], plan.level_n[L - 1], nullptr,
+      total);
+  for (int l = L - 2; l >= 0; --l)
+    scan_down_kernel<unsigned long long, unsigned long long><<<(unsigned)plan.level_n[l + 1], kScanThreads, 0, st>>>(
+        scratch + plan.level_off[l], scratch + plan.level_off[l], plan.level_n[l],
+        scratch + plan.level_off[l + 1], nullptr);
+  scan_down_kernel<uint32_t, uint32_t><<<(unsigned)plan.level_n[0], kScanThreads, 0, st>>>(
+      in, out, n, scratch + plan.level_off[0], nullptr);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// stable LSD radix sort of (key, value) pairs
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int64_t radix_count(int64_t n_host, const uint32_t* n_dev) {
+  return n_dev ? (int64_t)(*n_dev) : n_host;
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(const uint32_t* keys, int64_t n_host,
+                                                                       const uint32_t* n_dev, int shift,
+                                                                       uint32_t mask, uint32_t* hist,
+                                                                       int64_t nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t n = radix_count(n_host, n_dev);
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  if (base < n) {
+#pragma unroll 4
+    for (int i = 0; i < kRadixItems; ++i) {
+      const int64_t idx = base + (int64_t)i * kRadixThreads + threadIdx.x;
+      if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & mask], 1u);
+    }
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, int64_t n_host, const uint32_t* n_dev, int shift, uint32_t mask,
+    const uint32_t* hist_off, int64_t nblocks) {
+  constexpr int kWarps = kRadixThreads / 32;
+  __shared__ uint32_t whist[kWarps][256];
+  __shared__ uint32_t dbase[256];
+  const int64_t n = radix_count(n_host, n_dev);
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  if (base >= n) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kWarps * 256; i += kRadixThreads) (&whist[0][0])[i] = 0;
+  dbase[threadIdx.x] = hist_off[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t wbase = base + (int64_t)warp * (kRadixItems * 32);
+  uint32_t k[kRadixItems], v[kRadixItems], rk[kRadixItems];
+#pragma unroll
+  for (int i = 0; i < kRadixItems; ++i) {
+    const int64_t idx = wbase + i * 32 + lane;
+    const bool valid = idx < n;
+    k[i] = valid ? keys_in[idx] : 0u;
+    v[i] = valid ? vals_in[idx] : 0u;
+    const uint32_t d = valid ? ((k[i] >> shift) & mask) : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = 0;
+    if (valid) before = whist[warp][d];
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) whist[warp][d] = before + __popc(peers);
+    __syncwarp();
+    rk[i] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  {
+    // exclusive scan of each digit's count over the warps (warps own consecutive sub-chunks)
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = whist[w][threadIdx.x];
+      whist[w][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kRadixItems; ++i) {
+    const int64_t idx = wbase + i * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = (k[i] >> shift) & mask;
+      const uint32_t pos = dbase[d] + whist[warp][d] + rk[i];
+      keys_out[pos] = k[i];
+      vals_out[pos] = v[i];
+    }
+  }
+}
+
+RadixPlan plan_radix(int64_t capacity) {
+  RadixPlan p{};
+  p.capacity = capacity;
+  p.nblocks = (capacity + kRadixTile - 1) / kRadixTile;
+  if (p.nblocks < 1) p.nblocks = 1;
+  p.hist_scan = plan_scan(256 * p.nblocks);
+  return p;
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
+                             int64_t n_host, const uint32_t* n_dev, int bit_lo, int bit_hi,
+                             uint32_t* hist, uint32_t* hist_off, unsigned long long* scan_scratch,
+                             const RadixPlan& plan, bool* in_b, cudaStream_t st) {
+  *in_b = false;
+  const int64_t nblocks = n_dev ? plan.nblocks : (n_host + kRadixTile - 1) / kRadixTile;
+  if (nblocks == 0) return cudaSuccess;
+  const ScanPlan hs = n_dev ? plan.hist_scan : plan_scan(256 * nblocks);
+  uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
+  for (int shift = bit_lo; shift < bit_hi; shift += 8) {
+    const int bits = (bit_hi - shift) < 8 ? (bit_hi - shift) : 8;
+    const uint32_t mask = (1u << bits) - 1u;
+    radix_upsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, n_host, n_dev, shift, mask, hist,
+                                                                       nblocks);
+    cudaError_t e = exclusive_scan_u32(hist, hist_off, 256 * nblocks, scan_scratch, hs,
+                                       scan_scratch + hs.scratch_elems - 1, st);
+    if (e != cudaSuccess) return e;
+    radix_downsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n_host, n_dev, shift,
+                                                                         mask, hist_off, nblocks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uint32_t* t;
+    t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+    *in_b = !*in_b;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// binning kernels
+// ------------------------------------------------------------------------------------------
+template <typename Tst>
+__global__ void height_keys_kernel(const Tst* means, int64_t n, int64_t n_pad, uint32_t* keys, uint32_t* vals) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  // +0.0f maps -0 to +0 so that equal heights compare equal
+  const float z = __fadd_rn(load_attr(means, 2 * n_pad + k), 0.0f);
+  keys[k] = ~float_order(z);  // ascending key = descending height
+  vals[k] = (uint32_t)k;
+}
+
+cudaError_t launch_height_keys(const void* means, int dtype, int64_t n, int64_t n_pad, uint32_t* keys,
+                               uint32_t* vals, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  if (dtype == SS_BF16)
+    height_keys_kernel<__nv_bfloat16><<<nb, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(means), n, n_pad,
+                                                           keys, vals);
+  else
+    height_keys_kernel<float><<<nb, 256, 0, st>>>(static_cast<const float*>(means), n, n_pad, keys, vals);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ uint32_t rect_count(ushort4 r) {
+  return (r.x <= r.z && r.y <= r.w) ? (uint32_t)(r.z - r.x + 1) * (uint32_t)(r.w - r.y + 1) : 0u;
+}
+
+__global__ void counts_kernel(BinParams p) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)p.n_targets * p.n) return;
+  const int64_t t = idx / p.n, r = idx - t * p.n;
+  const uint32_t k = p.order[r];
+  p.counts[idx] = rect_count(p.rect[t * p.n_pad + k]);
+}
+
+__global__ void emit_kernel(BinParams p) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)p.n_targets * p.n) return;
+  const int64_t t = idx / p.n, r = idx - t * p.n;
+  const uint32_t k = p.order[r];
+  const ushort4 rc = p.rect[t * p.n_pad + k];
+  if (!(rc.x <= rc.z && rc.y <= rc.w)) return;
+  const TargetCam& cam = p.tcams[t];
+  int64_t pos = p.offsets[idx];
+  for (int ty = rc.y; ty <= rc.w; ++ty) {
+    for (int tx = rc.x; tx <= rc.z; ++tx, ++pos) {
+      if (pos >= p.capacity) return;
+      p.keys[pos] = (uint32_t)(cam.tile_base + ty * cam.tiles_x + tx);
+      p.vals[pos] = k;
+    }
+  }
+}
+
+cudaError_t launch_counts(const BinParams& p, cudaStream_t st) {
+  const int64_t m = (int64_t)p.n_targets * p.n;
+  if (m == 0) return cudaSuccess;
+  counts_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const BinParams& p, cudaStream_t st) {
+  const int64_t m = (int64_t)p.n_targets * p.n;
+  if (m == 0) return cudaSuccess;
+  emit_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+__global__ void finish_count_kernel(StatusBlock* status, const unsigned long long* total, int64_t capacity) {
+  const unsigned long long t = *total;
+  status->n_isect = t;
+  status->n_isect32 = (unsigned int)(t > (unsigned long long)capacity ? (unsigned long long)capacity : t);
+  if (t > (unsigned long long)capacity) atomicOr(&status->flags, (unsigned int)FLAG_OVERFLOW);
+}
+
+cudaError_t launch_finish_count(StatusBlock* status, const uint32_t*, const uint32_t*,
+                                const unsigned long long* total, int64_t capacity, cudaStream_t st) {
+  finish_count_kernel<<<1, 1, 0, st>>>(status, total, capacity);
+  return cudaGetLastError();
+}
+
+__global__ void ranges_kernel(const uint32_t* keys, const StatusBlock* status, uint2* ranges) {
+  const int64_t n = status->n_isect32;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t key = keys[i];
+  if (i == 0 || keys[i - 1] != key) ranges[key].x = (uint32_t)i;
+  if (i == n - 1 || keys[i + 1] != key) ranges[key].y = (uint32_t)(i + 1);
+}
+
+cudaError_t launch_ranges(const uint32_t* keys, const StatusBlock* status, uint2* ranges, int64_t capacity,
+                          cudaStream_t st) {
+  if (capacity == 0) return cudaSuccess;
+  ranges_kernel<<<(unsigned)((capacity + 255) / 256), 256, 0, st>>>(keys, status, ranges);
+  return cudaGetLastError();
+}
+
+}  // namespace ss
