@@ -1,0 +1,522 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 affine 2DGS rasterizer (forward + backward, Mpix/s).
+
+Default workload ("batched"): 1M splats over 1 km^2, 16 views of uneven size
+(1024^2 - 2048^2) with camera deltas, plus the sun-view shadow-depth pass of
+every view at half resolution; splat attributes stored in BF16; one step =
+projection, binning, forward and backward of all 32 targets, replayed from one
+CUDA graph with persistent launches.  Mpix/s counts main-view pixels per
+forward+backward step.  Beside it: the same scene as 16 plain FP32 single-view
+calls, an end-to-end run through the public API with host buffers, live
+per-kernel timing for the roofline, and the FP64 oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank renders its own replica of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s at 1M splats (batched BF16 vs plain FP32), % of roofline"
+UNIT = "Mpix/s"
+# FP32 operations per contributing (pixel, splat) pair, counted from the kernel source
+# (FADD/FMUL = 1, FFMA = 2; the exp and the reciprocal are MUFU ops, not counted):
+#   forward: pair evaluation 20 + compositing 21
+#   backward: pair evaluation 20 + adjoint 63 + accumulation of 16 gradient fields 16
+FLOPS_FWD_PER_PAIR = 41
+FLOPS_BWD_PER_PAIR = 99
+FP32_LANES_PER_SM = 128
+
+WORKLOAD_TEXT = {
+    "batched": "1M splats over 1 km^2; 16 views of uneven size 1024^2-2048^2 with camera deltas; "
+               "a sun-view shadow-depth pass per view at half resolution",
+    "single": "500k splats over 1 km^2; one 2048^2 view with colour correction plus a 1024^2 sun view",
+    "small": "4096 splats over 100 m; one 128^2 view plus a 64^2 sun view",
+    "full": "4M splats over 2x2 km; 32 views at 2048^2 with deltas and colour correction, each with a "
+            "1024^2 sun view",
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched", choices=list(WORKLOAD_TEXT))
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 single-view arm")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (16x16, batch 256)")
+    ap.add_argument("--storage", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--profile", action="store_true",
+                    help="short run for a profiler: no tuning, plain, e2e or CPU arms")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ distributed
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        import torch.distributed as dist
+        if self.world > 1 and not dist.is_initialized():
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def gpu_smi_id(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        bus = getattr(p, "pci_bus_id", None)
+        dom = getattr(p, "pci_domain_id", 0)
+        did = getattr(p, "pci_device_id", 0)
+        if bus is not None:
+            return f"{dom:08X}:{bus:02X}:{did:02X}.0"
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------------------ helpers
+def upload_splats(torch, scene, dtype):
+    from paper_2606_28581_gb300.frame import n_pad_of, pad_planar
+    n_pad = n_pad_of(scene.n)
+    t = lambda a: pad_planar(torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda().to(dtype), n_pad)
+    return dict(means=t(scene.means), scales=t(scene.scales), quats=t(scene.quats),
+                opacity=t(scene.opacity[None]), rgb=t(scene.rgb))
+
+
+def make_upstream(torch, targets, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    ups = []
+    for t in targets:
+        r = lambda *s: torch.randn(*s, device="cuda", generator=g)
+        if t.sun:
+            ups.append(dict(depth=r(t.height, t.width), alpha=r(t.height, t.width)))
+        else:
+            ups.append(dict(rgb=r(3, t.height, t.width), depth=r(t.height, t.width),
+                            normal=r(3, t.height, t.width), alpha=r(t.height, t.width)))
+    return ups
+
+
+def time_loop(torch, fn, steps):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(steps):
+        fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def profiles_traffic(kernel: str):
+    """Per-launch DRAM traffic of `kernel` from the committed ncu summary, if the summary was
+    taken on the current kernel source (fingerprint match); else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2606_28581_gb300", "csrc", vals.get("source", "raster.cu"))
+    if not os.path.exists(src):
+        return None
+    fp = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if vals.get("source_sha256_16") != fp:
+        return None
+    try:
+        return float(vals["bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------------------ oracle arm
+def oracle_sample(scene, seconds_target: float, seed: int = 0):
+    """Time the FP64 oracle (forward + backward) on crops of view 0, growing the crop until
+    one sample takes about `seconds_target`.  Returns (Mpix/s, crop, seconds, threads)."""
+    import oracle
+    s64 = oracle.SceneF64.of(scene)
+    cam = scene.cameras[0]
+    rng = np.random.default_rng(seed)
+    side = 64
+    while True:
+        w = min(side, cam.width)
+        h = min(side, cam.height)
+        x0 = (cam.width - w) // 2
+        y0 = (cam.height - h) // 2
+        g = dict(rgb=rng.normal(size=(3, h, w)), depth=rng.normal(size=(h, w)),
+                 normal=rng.normal(size=(3, h, w)), alpha=rng.normal(size=(h, w)))
+        t0 = time.perf_counter()
+        oracle.render(s64, cam, crop=(x0, y0, w, h), color=cam.color)
+        oracle.backward(s64, cam, g, crop=(x0, y0, w, h), color=cam.color)
+        dt = time.perf_counter() - t0
+        if dt >= seconds_target or (w == cam.width and h == cam.height) or side >= 4096:
+            return (w * h) / dt / 1e6, (x0, y0, w, h), dt, oracle.num_threads()
+        side = int(side * min(4.0, max(1.3, math.sqrt(seconds_target / max(dt, 1e-3)))))
+
+
+def run_reference(args, dist):
+    """The oracle as the reference arm: each step is forward + backward of the FP64 oracle
+    on a bounded crop of the same workload, on the host cores."""
+    import scenegen
+    if dist.rank != 0:
+        return 0
+    scene = scenegen.workload(args.workload, seed=0)
+    main_px = sum(c.width * c.height for c in scene.cameras)
+    # size one step to about 1.5 s so that warm-up + steps end within a few minutes
+    per_step = max(0.5, min(3.0, 150.0 / max(1, args.steps + args.warmup)))
+    _, crop, _, threads = oracle_sample(scene, per_step)
+    import oracle
+    s64 = oracle.SceneF64.of(scene)
+    cam = scene.cameras[0]
+    x0, y0, w, h = crop
+    rng = np.random.default_rng(1)
+    g = dict(rgb=rng.normal(size=(3, h, w)), depth=rng.normal(size=(h, w)),
+             normal=rng.normal(size=(3, h, w)), alpha=rng.normal(size=(h, w)))
+
+    def step():
+        oracle.render(s64, cam, crop=crop, color=cam.color)
+        oracle.backward(s64, cam, g, crop=crop, color=cam.color)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = (w * h) / dt / 1e6
+    sample = f"{w}x{h} px crop of view 0 of the '{args.workload}' workload per step, all {scene.n} splats"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "n_splats": scene.n, "main_pixels": main_px},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ our arm
+def run_ours(args, dist):
+    import torch
+    import scenegen
+    from paper_2606_28581_gb300 import _lib as L
+    from paper_2606_28581_gb300.batched import BatchedStep, autotune, workload_key
+    from paper_2606_28581_gb300.frame import Frame, Outputs, grads_struct, zero_grads
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    dist.init("nccl")
+    L.load()
+    sms, arch = L.device_info()
+    if args.profile:
+        args.no_plain = args.no_cpu = args.no_e2e = args.no_tune = True
+
+    scene = scenegen.workload(args.workload, seed=dist.rank)
+    cams = scene.cameras
+    passes = L.SS_PASS_MAIN | L.SS_PASS_SUN
+    storage = torch.bfloat16 if args.storage == "bf16" else torch.float32
+    splats = upload_splats(torch, scene, storage)
+    dF = torch.from_numpy(np.stack([c.dF_xy for c in cams]).astype(np.float32)).cuda()
+    color = torch.from_numpy(np.stack([c.color for c in cams]).astype(np.float32)).cuda()
+    probe = Frame(cams, passes)
+    ups = make_upstream(torch, probe.targets, 1234 + dist.rank)
+    main_px = sum(t.width * t.height for t in probe.targets if not t.sun)
+    sun_px = sum(t.width * t.height for t in probe.targets if t.sun)
+
+    # ---- autotuned options (tile shape, batch), persistent launches
+    mk = lambda o: BatchedStep(cams, splats, scene.n, dF, color, ups, passes=passes, opts=o)
+    tune = None
+    if args.no_tune:
+        opts = L.default_opts(persistent=1)
+    else:
+        opts, tune = autotune(mk, workload_key(cams, scene.n, args.storage, passes), log=log)
+    step = mk(opts)
+    n_before = L.kernel_launches()
+    step.capture()
+    launches_per_step = L.kernel_launches() - n_before
+    # capture ran one eager warm-up step plus the captured one
+    launches_per_step = launches_per_step // 2
+
+    for _ in range(args.warmup):
+        step.replay()
+    torch.cuda.synchronize()
+    st, needed, walked, flags = step.check()
+    if st != L.SS_OK:
+        raise RuntimeError(f"frame status {L.status_string(st)} (needed {needed}, flags {flags})")
+
+    clk = ClockSampler(gpu_smi_id(torch, dev))
+    dist.barrier()
+    clk.start()
+    ms = time_loop(torch, step.replay, args.steps)
+    clocks = clk.stop()
+    dist.barrier()
+    ms_max = dist.max(ms)
+    total_px = dist.sum(main_px)
+    value = total_px / (ms_max * 1e-3) / 1e6
+    st, needed, walked, flags = step.check()
+    if st != L.SS_OK:
+        raise RuntimeError(f"frame status after timing: {L.status_string(st)}")
+
+    # ---- live per-kernel timing (same kernels and launch configuration, eager, events between)
+    k_steps = max(3, min(args.steps, 20))
+    names = ["project", "bin_and_sort", "rasterize_fwd", "rasterize_bwd", "project_bwd"]
+    phases = [step.project, step.bin, step.forward, step.backward_pixels, step.backward_project]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)]
+    acc = np.zeros(len(phases))
+    for _ in range(k_steps):
+        step.zero_grads()
+        evs[0].record()
+        for i, f in enumerate(phases):
+            f()
+            evs[i + 1].record()
+        torch.cuda.synchronize()
+        acc += [evs[i].elapsed_time(evs[i + 1]) for i in range(len(phases))]
+    phase_ms = {n: float(a / k_steps) for n, a in zip(names, acc)}
+    clock_mhz = clocks["sm_mhz"] if clocks else 1485.0
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    flops = {"rasterize_fwd": walked * FLOPS_FWD_PER_PAIR, "rasterize_bwd": walked * FLOPS_BWD_PER_PAIR}
+    dom = max(("rasterize_fwd", "rasterize_bwd"), key=lambda k: phase_ms[k])
+    achieved = flops[dom] / (phase_ms[dom] * 1e-3) / 1e12
+    traffic = profiles_traffic("raster_bwd") if dom == "rasterize_bwd" else None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "flops_per_launch": flops[dom], "walked_pairs": walked,
+                "flops_per_pair": FLOPS_BWD_PER_PAIR if dom == "rasterize_bwd" else FLOPS_FWD_PER_PAIR,
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz "
+                              f"(median SM clock sampled during the timed region)",
+                "frac_at_max_clock": achieved / (sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12),
+                "phase_ms": phase_ms}
+
+    # ---- plain FP32 single-view arm: the same scene as one plain call sequence per view
+    plain = None
+    if not args.no_plain:
+        splats32 = upload_splats(torch, scene, torch.float32)
+        s32 = L.make_splats(splats32["means"], splats32["scales"], splats32["quats"], splats32["opacity"],
+                            splats32["rgb"], scene.n)
+        frames, outs, ios = [], [], []
+        for v, c in enumerate(cams):
+            f = Frame([c], passes, L.default_opts())
+            f.project_and_bin(s32, dF[v:v + 1].contiguous(), sync=True)
+            f.ensure_workspace(s32, int(f.needed * 1.1) + 4096)
+            o = Outputs(f.targets, f.device)
+            u = [ups[v], ups[len(cams) + v]]
+            frames.append(f)
+            outs.append(o)
+            ios.append((o.io_array(), o.io_array(u)))
+        g32 = zero_grads(splats32["means"].shape[-1], "cuda")
+        gs = grads_struct(g32)
+        dFv = [dF[v:v + 1].contiguous() for v in range(len(cams))]
+        colv = [color[v:v + 1].contiguous() for v in range(len(cams))]
+        ddF = torch.zeros(len(cams), 2, 4, device="cuda")
+        dcol = torch.zeros(len(cams), 3, 4, device="cuda")
+
+        def plain_step():
+            for g in g32.values():
+                g.zero_()
+            for v, f in enumerate(frames):
+                L.project_splats(s32, f.cams, 1, passes, dFv[v], f.opts, f.ws, f.ws_bytes, f.capacity)
+                L.bin_and_sort(s32, f.cams, 1, passes, f.opts, f.ws, f.ws_bytes, f.capacity, sync_needed=False)
+                L.rasterize_fwd(s32, f.cams, 1, passes, colv[v], f.opts, ios[v][0], f.ws, f.ws_bytes, f.capacity)
+                L.rasterize_bwd(s32, f.cams, 1, passes, dFv[v], colv[v], f.opts, ios[v][1], gs, ddF[v:v + 1],
+                                dcol[v:v + 1], f.ws, f.ws_bytes, f.capacity)
+
+        for _ in range(max(1, min(args.warmup, 3))):
+            plain_step()
+        p_steps = max(3, min(args.steps, 20))
+        pms = time_loop(torch, plain_step, p_steps)
+        for f in frames:
+            stf = f.status()[0]
+            if stf != L.SS_OK:
+                raise RuntimeError(f"plain frame status {L.status_string(stf)}")
+        plain = {"value": main_px / (pms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": pms, "steps": p_steps,
+                 "storage": "fp32", "launch": "16 sequential single-view call sequences (eager, one block "
+                                               "per tile, 16x16 tiles)"}
+        del frames, outs, ios, splats32
+        torch.cuda.empty_cache()
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda t: t.detach().cpu().pin_memory()
+        h_in = {k: pin(v) for k, v in splats.items()}
+        h_in["dF"], h_in["color"] = pin(dF), pin(color)
+        h_ups = [{k: pin(v) for k, v in u.items()} for u in ups]
+        d_ups = step.upstream
+        h_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in step.grads.items()}
+        h_out["d_dF"] = torch.empty_like(step.d_dF, device="cpu").pin_memory()
+        h_out["d_color"] = torch.empty_like(step.d_color, device="cpu").pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in h_in.values())
+        h2d += sum(t.numel() * t.element_size() for u in h_ups for t in u.values())
+        d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+
+        def e2e_step():
+            for k in splats:
+                splats[k].copy_(h_in[k], non_blocking=True)
+            dF.copy_(h_in["dF"], non_blocking=True)
+            color.copy_(h_in["color"], non_blocking=True)
+            for du, hu in zip(d_ups, h_ups):
+                for k in du:
+                    du[k].copy_(hu[k], non_blocking=True)
+            step.replay()
+            for k, v in step.grads.items():
+                h_out[k].copy_(v, non_blocking=True)
+            h_out["d_dF"].copy_(step.d_dF, non_blocking=True)
+            h_out["d_color"].copy_(step.d_color, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        e2e_step()
+        e_steps = max(3, min(args.steps, 20))
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            e2e_step()
+        ems = (time.perf_counter() - t0) / e_steps * 1e3
+        ems = dist.max(ems)
+        e2e = {"value": total_px / (ems * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ems,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- the oracle on the host cores (rank 0, one GPU only)
+    cpu = None
+    if not args.no_cpu and dist.rank == 0 and dist.world == 1:
+        v, crop, secs, threads = oracle_sample(scene, 12.0)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"forward+backward of a {crop[2]}x{crop[3]} px crop of view 0 with all "
+                         f"{scene.n} splats ({secs:.1f} s)"}
+
+    if dist.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD_TEXT[args.workload], "n_splats": scene.n, "views": len(cams),
+                           "main_pixels_per_gpu": main_px, "sun_pixels_per_gpu": sun_px,
+                           "storage": args.storage, "tile": f"{opts.tile_w}x{opts.tile_h}", "batch": opts.batch,
+                           "launch": "one CUDA graph per step; persistent forward and backward launches over "
+                                     "all (target, tile) items",
+                           "l2": "not flushed: every step streams > 1 GB of projected records, lists and "
+                                 "upstream planes, far above the 129 MB L2",
+                           "parallelism": f"replicas x{dist.world}", "intersections": needed,
+                           "autotune": tune},
+                "roofline": roofline, "cpu_baseline": cpu, "plain_fp32": plain,
+                "batched_over_plain": (value / dist.world) / plain["value"] if plain else None,
+                "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+                "device": {"sms": sms, "arch": arch, "name": torch.cuda.get_device_name()}}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        return run_reference(args, dist)
+    return run_ours(args, dist)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -174,7 +174,8 @@ ss_status ss_workspace_size(const ss_splats* splats, const ss_camera* cams, int3
  * normalised rotation, M = B R S', det, Q = M^-1, the projected centre, the
  * depth of the centre and its slopes along u and v, the normal flipped toward
  * the sensor, log-opacity, the conservative screen extent and the tile
- * rectangle.  Splats with opacity < alpha_min are culled.
+ * rectangle, and zeroes the frame's gradient records of the visible pairs.
+ * Splats with opacity < alpha_min are culled.
  *   dF: DEVICE [n_cams][2][4] fp32 camera deltas, or NULL (zero).
  *   ws: DEVICE workspace of ws_bytes >= ss_workspace_size(..., capacity).
  * Non-finite splat values are counted in the status block (ss_frame_status). */
@@ -208,21 +209,34 @@ ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32
                            const ss_target_io* io, void* ws, size_t ws_bytes, int64_t capacity,
                            ss_stream_t stream);
 
-/* Backward (K4 + K5): the adjoint of ss_rasterize_fwd and ss_project_splats for
- * the same frame.  Per pixel the walk runs in reverse from `last`, recovering
- * the transmittance from T_final; per-splat partials are reduced across each
- * warp and block before global atomics into per-(target, splat) records, which
- * are then chained through the projection to the splat attributes and to the
- * camera deltas (through the sun camera for sun targets) and summed over
- * targets.
- *   grads:   accumulated splat gradients (required).
- *   d_dF:    DEVICE [n_cams][2][4] fp32, accumulated, or NULL.
- *   d_color: DEVICE [n_cams][3][4] fp32, accumulated, or NULL. */
+/* Backward (K4, then K5 unless grads is NULL): the adjoint of ss_rasterize_fwd
+ * and ss_project_splats for the same frame.  Per pixel the walk runs in reverse
+ * from `last`, recovering the transmittance from T_final (Sec. 3.2
+ * Eq. rasterization, differentiated); per-splat partials are reduced across
+ * each warp and block before global atomics into per-(target, splat) records
+ * in the workspace, which K5 (ss_project_bwd) chains through the projection.
+ * Call it once per ss_project_splats: the records start from zero there.
+ *   grads:   accumulated splat gradients; NULL runs K4 only, and a later
+ *            ss_project_bwd for the same frame finishes the backward.
+ *   d_dF:    DEVICE [n_cams][2][4] fp32, accumulated, or NULL (used with grads).
+ *   d_color: DEVICE [n_cams][3][4] fp32, accumulated, or NULL: gradient of the
+ *            colour correction, d C = sum g A^T, d c = sum g (Eq. image_formation). */
 ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
                            int32_t passes, const float* dF, const float* color,
                            const ss_raster_opts* opts, const ss_target_io* io,
                            const ss_splat_grads* grads, float* d_dF, float* d_color, void* ws,
                            size_t ws_bytes, int64_t capacity, ss_stream_t stream);
+
+/* Projection adjoint (K5), Sec. 3.2 Eq. affine2dgs_Qq and Sec. 3.3: chains the
+ * per-(target, splat) records left by ss_rasterize_bwd(grads = NULL) through
+ * Q = M^-1, M = B' R S', c = B' p + b', the depth row, the normal flip, the
+ * quaternion normalisation and, for sun targets, the flattening along s; sums
+ * over targets into `grads` (required, accumulated) and into d_dF (accumulated,
+ * or NULL).  d(opacity) is taken through log(opacity). */
+ss_status ss_project_bwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
+                         int32_t passes, const ss_raster_opts* opts, const ss_splat_grads* grads,
+                         float* d_dF, void* ws, size_t ws_bytes, int64_t capacity,
+                         ss_stream_t stream);
 
 /* Sun-direction shadow depth (K6), Sec. 3.3 and Supp. A: project, bin and
  * rasterize the sun view of every camera (depth and alpha only).  Equivalent
@@ -236,14 +250,22 @@ ss_status ss_shadow_depth(const ss_splats* splats, const ss_camera* cams, int32_
 /* Status block of a frame's workspace.  SYNCHRONISES the stream.
  *   needed:    intersections the last ss_bin_and_sort needed
  *   nonfinite: splats culled for non-finite values by the last projection
+ *   walked:    (pixel, splat) pairs with alpha >= alpha_min that the forward passes since
+ *              the last projection walked, the stopping pair included (algorithmic work)
  *   flags:     bit 0 = intersection overflow, bit 1 = a bounded wait timed out
+ * Any output pointer may be NULL.
  * Returns SS_ERR_CAPACITY / SS_ERR_TIMEOUT / SS_ERR_NONFINITE when set, else SS_OK. */
 ss_status ss_frame_status(const void* ws, size_t ws_bytes, int64_t* needed, int64_t* nonfinite,
-                          int32_t* flags, ss_stream_t stream);
+                          int64_t* walked, int32_t* flags, ss_stream_t stream);
 
 /* Number of SMs of the current device and the library's compiled architecture
  * (e.g. 1030 for sm_103a); a test hook to check the build.  Host only. */
 int32_t ss_device_info(int32_t* num_sms, int32_t* arch);
+
+/* Number of kernels this library has launched, or recorded into a CUDA graph under
+ * stream capture, in this process (a host-side diagnostic counter; the paper has no
+ * counterpart).  Host only; never fails. */
+int64_t ss_kernel_launches(void);
 
 #ifdef __cplusplus
 }

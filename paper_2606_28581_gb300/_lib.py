@@ -55,8 +55,8 @@ class ss_splat_grads(ctypes.Structure):
 
 
 EXPORTS = ["ss_default_opts", "ss_status_string", "ss_workspace_size", "ss_project_splats",
-           "ss_bin_and_sort", "ss_rasterize_fwd", "ss_rasterize_bwd", "ss_shadow_depth",
-           "ss_frame_status", "ss_device_info"]
+           "ss_bin_and_sort", "ss_rasterize_fwd", "ss_rasterize_bwd", "ss_project_bwd", "ss_shadow_depth",
+           "ss_frame_status", "ss_device_info", "ss_kernel_launches"]
 
 _lock = threading.Lock()
 _lib = None
@@ -91,13 +91,16 @@ def load(path: Optional[str] = None):
         L.ss_bin_and_sort.argtypes = [PS, PC, I32, I32, PO, P, SZ, I64, ctypes.POINTER(I64), P]
         L.ss_rasterize_fwd.argtypes = [PS, PC, I32, I32, P, PO, PIO, P, SZ, I64, P]
         L.ss_rasterize_bwd.argtypes = [PS, PC, I32, I32, P, P, PO, PIO, PG, P, P, P, SZ, I64, P]
+        L.ss_project_bwd.argtypes = [PS, PC, I32, I32, PO, PG, P, P, SZ, I64, P]
         L.ss_shadow_depth.argtypes = [PS, PC, I32, P, PO, PIO, P, SZ, I64, ctypes.POINTER(I64), P]
-        L.ss_frame_status.argtypes = [P, SZ, ctypes.POINTER(I64), ctypes.POINTER(I64),
+        L.ss_frame_status.argtypes = [P, SZ, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
                                       ctypes.POINTER(I32), P]
         L.ss_device_info.argtypes = [ctypes.POINTER(I32), ctypes.POINTER(I32)]
         L.ss_device_info.restype = I32
+        L.ss_kernel_launches.argtypes = []
+        L.ss_kernel_launches.restype = I64
         for name in EXPORTS:
-            if name not in ("ss_default_opts", "ss_status_string", "ss_device_info"):
+            if name not in ("ss_default_opts", "ss_status_string", "ss_device_info", "ss_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -202,10 +205,18 @@ def rasterize_fwd(splats, cams, n_cams, passes, color, opts, io, ws, ws_bytes, c
 
 def rasterize_bwd(splats, cams, n_cams, passes, dF, color, opts, io, grads, d_dF, d_color, ws, ws_bytes,
                   capacity, stream=None):
+    """``grads`` None runs the per-pixel adjoint only (finish with project_bwd)."""
+    g = None if grads is None else ctypes.byref(grads)
     return _check(load().ss_rasterize_bwd(ctypes.byref(splats), cams, n_cams, passes, ptr(dF), ptr(color),
-                                          ctypes.byref(opts), io, ctypes.byref(grads), ptr(d_dF),
+                                          ctypes.byref(opts), io, g, ptr(d_dF),
                                           ptr(d_color), ptr(ws), int(ws_bytes), int(capacity),
                                           stream_ptr(stream)), "ss_rasterize_bwd")
+
+
+def project_bwd(splats, cams, n_cams, passes, opts, grads, d_dF, ws, ws_bytes, capacity, stream=None):
+    return _check(load().ss_project_bwd(ctypes.byref(splats), cams, n_cams, passes, ctypes.byref(opts),
+                                        ctypes.byref(grads), ptr(d_dF), ptr(ws), int(ws_bytes), int(capacity),
+                                        stream_ptr(stream)), "ss_project_bwd")
 
 
 def shadow_depth(splats, cams, n_cams, dF, opts, io, ws, ws_bytes, capacity, sync_needed=True, stream=None):
@@ -218,10 +229,15 @@ def shadow_depth(splats, cams, n_cams, dF, opts, io, ws, ws_bytes, capacity, syn
 
 
 def frame_status(ws, ws_bytes, stream=None):
-    needed, nonfinite, flags = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+    """Returns (status, needed, nonfinite, walked, flags); synchronises the stream."""
+    needed, nonfinite, walked, flags = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
     st = load().ss_frame_status(ptr(ws), int(ws_bytes), ctypes.byref(needed), ctypes.byref(nonfinite),
-                                ctypes.byref(flags), stream_ptr(stream))
-    return st, int(needed.value), int(nonfinite.value), int(flags.value)
+                                ctypes.byref(walked), ctypes.byref(flags), stream_ptr(stream))
+    return st, int(needed.value), int(nonfinite.value), int(walked.value), int(flags.value)
+
+
+def kernel_launches() -> int:
+    return int(load().ss_kernel_launches())
 
 
 def device_info():

@@ -1,0 +1,199 @@
+"""Batched multi-view training step in one CUDA graph (training form b).
+
+All views and their sun views form one frame.  One step is: camera assembly +
+projection (K1), one shared height sort + binning of every target (K2), ONE
+persistent forward launch over every (target, tile) item (K3), ONE persistent
+backward launch (K4) and the projection adjoint (K5).  The step is captured once
+in a CUDA graph and replayed; the intersection capacity is fixed at capture and
+an overflow is reported through the workspace status block, which the host
+reads after a replay (``check``).
+
+The autotuner times the candidate tile shapes and per-block splat batches on
+the actual workload and caches the winner per (GPU, workload) in a JSON file.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import _lib as L
+from .frame import Frame, Outputs, grads_struct
+
+TILE_CANDIDATES = [(16, 16, 256), (16, 16, 128), (32, 8, 256), (32, 8, 128), (8, 32, 256), (8, 32, 128)]
+
+
+class BatchedStep:
+    """One training step (forward + backward) over every target of a frame.
+
+    ``splats``: dict of planar storage tensors [C, n_pad] (fp32 or bf16): means, scales,
+    quats, opacity, rgb.  ``dF`` (V, 2, 4), ``color`` (V, 3, 4) fp32.  ``upstream``: one
+    dict of upstream gradient planes per target.  Gradients go to ``grads`` (fp32 [C, n_pad]),
+    ``d_dF`` and ``d_color``; they are zeroed at the start of each step."""
+
+    def __init__(self, cameras: Sequence, splats: dict, n: int, dF, color, upstream: Sequence[dict],
+                 passes: int = L.SS_PASS_MAIN | L.SS_PASS_SUN, opts: Optional[L.ss_raster_opts] = None,
+                 capacity_slack: float = 1.10, device="cuda"):
+        self.opts = opts if opts is not None else L.default_opts(persistent=1)
+        self.frame = Frame(cameras, passes, self.opts, device=device)
+        self.tensors = splats
+        self.n = int(n)
+        self.splats = L.make_splats(splats["means"], splats["scales"], splats["quats"], splats["opacity"],
+                                    splats["rgb"], n)
+        self.dF, self.color, self.upstream = dF, color, list(upstream)
+        n_pad = int(splats["means"].shape[-1])
+        z = lambda c: torch.zeros(c, n_pad, device=device, dtype=torch.float32)
+        self.grads = dict(means=z(3), scales=z(2), quats=z(4), opacity=z(1), rgb=z(3))
+        V = self.frame.n_cams
+        self.d_dF = torch.zeros(V, 2, 4, device=device)
+        self.d_color = torch.zeros(V, 3, 4, device=device)
+        self.out = Outputs(self.frame.targets, self.frame.device)
+        self._io_f = self.out.io_array()
+        self._io_b = self.out.io_array(self.upstream)
+        self._g = grads_struct(self.grads)
+        self.graph = None
+        # size the intersection capacity with one synchronised eager run
+        needed = self.frame.project_and_bin(self.splats, self.dF, sync=True)
+        cap = max(1 << 16, int(needed * capacity_slack) + 4096)
+        self.frame.ensure_workspace(self.splats, cap)
+
+    # ------------------------------------------------------------------ phases
+    def project(self, stream=None):
+        f = self.frame
+        L.project_splats(self.splats, f.cams, f.n_cams, f.passes, self.dF, f.opts, f.ws, f.ws_bytes, f.capacity,
+                         stream)
+
+    def bin(self, stream=None):
+        f = self.frame
+        L.bin_and_sort(self.splats, f.cams, f.n_cams, f.passes, f.opts, f.ws, f.ws_bytes, f.capacity,
+                       sync_needed=False, stream=stream)
+
+    def forward(self, stream=None):
+        f = self.frame
+        L.rasterize_fwd(self.splats, f.cams, f.n_cams, f.passes, self.color, f.opts, self._io_f, f.ws, f.ws_bytes,
+                        f.capacity, stream)
+
+    def backward_pixels(self, stream=None):
+        f = self.frame
+        L.rasterize_bwd(self.splats, f.cams, f.n_cams, f.passes, None, self.color, f.opts, self._io_b, None, None,
+                        self.d_color, f.ws, f.ws_bytes, f.capacity, stream)
+
+    def backward_project(self, stream=None):
+        f = self.frame
+        L.project_bwd(self.splats, f.cams, f.n_cams, f.passes, f.opts, self._g, self.d_dF, f.ws, f.ws_bytes,
+                      f.capacity, stream)
+
+    def zero_grads(self):
+        for g in self.grads.values():
+            g.zero_()
+        self.d_dF.zero_()
+        self.d_color.zero_()
+
+    def step_eager(self, stream=None):
+        self.zero_grads()
+        self.project(stream)
+        self.bin(stream)
+        self.forward(stream)
+        self.backward_pixels(stream)
+        self.backward_project(stream)
+
+    # ------------------------------------------------------------------ graph
+    def capture(self):
+        """Capture one step in a CUDA graph (after an eager warm-up run)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step_eager()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step_eager()
+        torch.cuda.synchronize()
+        self.graph = g
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def check(self):
+        """Synchronise and read the status block: (status, needed, walked, flags)."""
+        st, needed, _, walked, flags = self.frame.status()
+        return st, needed, walked, flags
+
+    @property
+    def main_pixels(self) -> int:
+        return sum(t.width * t.height for t in self.frame.targets if not t.sun)
+
+    @property
+    def sun_pixels(self) -> int:
+        return sum(t.width * t.height for t in self.frame.targets if t.sun)
+
+
+# ------------------------------------------------------------------------------ autotuner
+def _cache_path() -> str:
+    base = os.environ.get("SATSPLAT_AUTOTUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "satsplat", "autotune.json")
+    return base
+
+
+def workload_key(cameras: Sequence, n: int, dtype, passes: int) -> str:
+    h = hashlib.sha256()
+    h.update(f"{n}|{dtype}|{passes}".encode())
+    for c in cameras:
+        h.update(f"{c.width}x{c.height}|{c.shadow_w}x{c.shadow_h}".encode())
+    name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    return f"{name}|{h.hexdigest()[:16]}"
+
+
+def autotune(make_step, key: str, candidates=TILE_CANDIDATES, warmup: int = 1, iters: int = 3,
+             use_cache: bool = True, log=None):
+    """Time ``make_step(opts)`` (a BatchedStep) for each (tile_w, tile_h, batch) candidate with
+    persistent launches and return the fastest options.  Results are cached by ``key``."""
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except Exception:
+            cache = {}
+    if use_cache and key in cache:
+        tw, th, b = cache[key]["best"]
+        return L.default_opts(tile_w=tw, tile_h=th, batch=b, persistent=1), cache[key]
+    results = {}
+    for (tw, th, b) in candidates:
+        opts = L.default_opts(tile_w=tw, tile_h=th, batch=b, persistent=1)
+        step = make_step(opts)
+        for _ in range(warmup):
+            step.step_eager()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times = []
+        for _ in range(iters):
+            ev0.record()
+            step.step_eager()
+            ev1.record()
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+        times.sort()
+        results[f"{tw}x{th}x{b}"] = times[len(times) // 2]
+        if log:
+            log(f"autotune {tw}x{th} batch {b}: {results[f'{tw}x{th}x{b}']:.3f} ms")
+        del step
+        torch.cuda.empty_cache()
+    best = min(results, key=results.get)
+    tw, th, b = (int(v) for v in best.split("x"))
+    entry = {"best": [tw, th, b], "ms": results}
+    if use_cache:
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            cache[key] = entry
+            json.dump(cache, open(path, "w"), indent=1)
+        except OSError:
+            pass
+    return L.default_opts(tile_w=tw, tile_h=th, batch=b, persistent=1), entry

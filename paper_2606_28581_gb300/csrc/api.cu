@@ -1,10 +1,16 @@
 // C ABI of the rasterizer: host-side validation, workspace layout and launch sequencing.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
 #include "kernels.cuh"
 
 using namespace ss;
+
+namespace ss {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace ss
 
 namespace {
 
@@ -248,6 +254,31 @@ ss_status fill_raster(RasterParams& rp, const ss_splats* s, const Layout& L, con
   return SS_OK;
 }
 
+ss_status check_grads(const ss_splats* s, const ss_splat_grads* g) {
+  if (!g || g->n_pad < s->n) return SS_ERR_INVALID_ARG;
+  if (s->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->rgb)) return SS_ERR_INVALID_ARG;
+  return SS_OK;
+}
+
+ss_status run_project_bwd(const ss_splats* splats, const Layout& L, const ss_raster_opts* opts,
+                          const ss_splat_grads* grads, float* d_dF, void* ws, cudaStream_t st) {
+  ProjectBwdParams pb;
+  pb.c = common_of(splats, L, ws);
+  pb.rect = at<ushort4>(ws, L.rect);
+  pb.grad = at<float>(ws, L.grad);
+  pb.g.means = grads->means;
+  pb.g.scales = grads->scales;
+  pb.g.quats = grads->quats;
+  pb.g.opacity = grads->opacity;
+  pb.g.rgb = grads->rgb;
+  pb.g.n_pad = grads->n_pad;
+  pb.d_dF = d_dF;
+  pb.amin = opts->alpha_min;
+  pb.det_eps = opts->det_eps;
+  SS_CUDA_TRY(launch_project_bwd(pb, splats->dtype, st));
+  return SS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -316,6 +347,7 @@ ss_status ss_project_splats(const ss_splats* splats, const ss_camera* cams, int3
   pp.geom = at<float4>(ws, L.geom);
   pp.feat = at<float4>(ws, L.feat);
   pp.rect = at<ushort4>(ws, L.rect);
+  pp.grad = at<float4>(ws, L.grad);
   pp.status = at<StatusBlock>(ws, L.status);
   pp.amin = opts->alpha_min;
   pp.ln_amin = logf(opts->alpha_min);
@@ -418,9 +450,7 @@ ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32
   ss_status e = make_layout(splats, cams, n_cams, passes, opts, capacity, &L);
   if (e != SS_OK) return e;
   if ((e = check_ws(L, ws, ws_bytes)) != SS_OK) return e;
-  if (!grads || grads->n_pad < splats->n) return SS_ERR_INVALID_ARG;
-  if (splats->n > 0 && (!grads->means || !grads->scales || !grads->quats || !grads->opacity || !grads->rgb))
-    return SS_ERR_INVALID_ARG;
+  if (grads && (e = check_grads(splats, grads)) != SS_OK) return e;
   RasterParams* rp = new RasterParams;
   e = fill_raster(*rp, splats, L, opts, io, color, ws, true);
   if (e != SS_OK) {
@@ -429,28 +459,26 @@ ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32
   }
   rp->d_color = d_color;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t ce = cudaMemsetAsync(at<char>(ws, L.grad), 0, (size_t)L.T * L.n_pad * 64, st);
-  if (ce == cudaSuccess && opts->persistent)
+  cudaError_t ce = cudaSuccess;
+  if (opts->persistent)
     ce = cudaMemsetAsync(&at<StatusBlock>(ws, L.status)->work_bwd, 0, sizeof(unsigned int), st);
   if (ce == cudaSuccess)
     ce = launch_raster_bwd(*rp, opts->tile_w, opts->tile_h, opts->batch, opts->persistent != 0, num_sms_cached(), st);
   delete rp;
   if (ce != cudaSuccess) return SS_ERR_CUDA;
-  ProjectBwdParams pb;
-  pb.c = common_of(splats, L, ws);
-  pb.rect = at<ushort4>(ws, L.rect);
-  pb.grad = at<float>(ws, L.grad);
-  pb.g.means = grads->means;
-  pb.g.scales = grads->scales;
-  pb.g.quats = grads->quats;
-  pb.g.opacity = grads->opacity;
-  pb.g.rgb = grads->rgb;
-  pb.g.n_pad = grads->n_pad;
-  pb.d_dF = d_dF;
-  pb.amin = opts->alpha_min;
-  pb.det_eps = opts->det_eps;
-  SS_CUDA_TRY(launch_project_bwd(pb, splats->dtype, st));
-  return SS_OK;
+  if (!grads) return SS_OK;
+  return run_project_bwd(splats, L, opts, grads, d_dF, ws, st);
+}
+
+ss_status ss_project_bwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams, int32_t passes,
+                         const ss_raster_opts* opts, const ss_splat_grads* grads, float* d_dF, void* ws,
+                         size_t ws_bytes, int64_t capacity, ss_stream_t stream) {
+  Layout L;
+  ss_status e = make_layout(splats, cams, n_cams, passes, opts, capacity, &L);
+  if (e != SS_OK) return e;
+  if ((e = check_ws(L, ws, ws_bytes)) != SS_OK) return e;
+  if ((e = check_grads(splats, grads)) != SS_OK) return e;
+  return run_project_bwd(splats, L, opts, grads, d_dF, ws, reinterpret_cast<cudaStream_t>(stream));
 }
 
 ss_status ss_shadow_depth(const ss_splats* splats, const ss_camera* cams, int32_t n_cams, const float* dF,
@@ -463,8 +491,8 @@ ss_status ss_shadow_depth(const ss_splats* splats, const ss_camera* cams, int32_
   return ss_rasterize_fwd(splats, cams, n_cams, SS_PASS_SUN, nullptr, opts, io, ws, ws_bytes, capacity, stream);
 }
 
-ss_status ss_frame_status(const void* ws, size_t ws_bytes, int64_t* needed, int64_t* nonfinite, int32_t* flags,
-                          ss_stream_t stream) {
+ss_status ss_frame_status(const void* ws, size_t ws_bytes, int64_t* needed, int64_t* nonfinite, int64_t* walked,
+                          int32_t* flags, ss_stream_t stream) {
   if (!ws || ws_bytes < sizeof(StatusBlock)) return SS_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   StatusBlock hs;
@@ -472,12 +500,15 @@ ss_status ss_frame_status(const void* ws, size_t ws_bytes, int64_t* needed, int6
   SS_CUDA_TRY(cudaStreamSynchronize(st));
   if (needed) *needed = (int64_t)hs.n_isect;
   if (nonfinite) *nonfinite = (int64_t)hs.nonfinite;
+  if (walked) *walked = (int64_t)hs.n_walked;
   if (flags) *flags = (int32_t)hs.flags;
   if (hs.flags & FLAG_OVERFLOW) return SS_ERR_CAPACITY;
   if (hs.flags & FLAG_TIMEOUT) return SS_ERR_TIMEOUT;
   if (hs.nonfinite) return SS_ERR_NONFINITE;
   return SS_OK;
 }
+
+int64_t ss_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int32_t ss_device_info(int32_t* num_sms, int32_t* arch) {
   if (num_sms) *num_sms = num_sms_cached();

@@ -42,7 +42,8 @@ struct StatusBlock {
   unsigned int work_fwd;         // persistent work-queue counters
   unsigned int work_bwd;
   unsigned int n_isect32;        // min(n_isect, capacity): the count the sort kernels use
-  unsigned int pad[56];
+  unsigned long long n_walked;   // (pixel, splat) pairs the forward walked with alpha >= alpha_min
+  unsigned int pad[54];
 };
 static_assert(sizeof(StatusBlock) == 256, "status block size");
 
@@ -182,7 +183,10 @@ __device__ __forceinline__ PairEval eval_pair(const float4 g0, const float4 g1, 
   return e;
 }
 
-#define SS_CUDA_TRY(expr)                              \
+// Host-side count of the kernels this library has launched (or captured into a graph).
+void count_launch();
+
+#define SS_CUDA_TRY(expr)                            \
   do {                                                 \
     cudaError_t _e = (expr);                           \
     if (_e != cudaSuccess) return SS_ERR_CUDA;         \

@@ -29,6 +29,7 @@ struct ProjectParams {
   float4* geom;  // [T][n_pad][3]
   float4* feat;  // [T][n_pad][2]
   ushort4* rect; // [T][n_pad]
+  float4* grad;  // [T][n_pad][4]: zeroed for visible pairs
   StatusBlock* status;
   float amin, ln_amin, sigma, det_eps;
   int32_t tile_w, tile_h;

@@ -233,6 +233,12 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectParams p) {
           float4* f = p.feat + rec * 2;
           f[0] = make_float4(-s.su * s.R[2][0], -s.sv * s.R[2][1], sp.flip * s.R[0][2], sp.flip * s.R[1][2]);
           f[1] = make_float4(sp.flip * s.R[2][2], s.rgb[0], s.rgb[1], s.rgb[2]);
+          float4* gz = p.grad + rec * 4;
+          const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          gz[0] = z4;
+          gz[1] = z4;
+          gz[2] = z4;
+          gz[3] = z4;
         }
       }
     }
@@ -416,6 +422,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdParams p) {
 // launchers
 // ------------------------------------------------------------------------------------------
 cudaError_t launch_assemble(const AssembleParams& p, cudaStream_t st) {
+  count_launch();
   assemble_kernel<<<1, kMaxTargets, 0, st>>>(p);
   return cudaGetLastError();
 }
@@ -423,20 +430,26 @@ cudaError_t launch_assemble(const AssembleParams& p, cudaStream_t st) {
 cudaError_t launch_project(const ProjectParams& p, int dtype, cudaStream_t st) {
   const int64_t nb = (p.c.n + 255) / 256;
   if (nb == 0) return cudaSuccess;
-  if (dtype == SS_BF16)
+  if (dtype == SS_BF16) {
+    count_launch();
     project_kernel<__nv_bfloat16><<<(unsigned)nb, 256, 0, st>>>(p);
-  else
+  } else {
+    count_launch();
     project_kernel<float><<<(unsigned)nb, 256, 0, st>>>(p);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_project_bwd(const ProjectBwdParams& p, int dtype, cudaStream_t st) {
   const int64_t nb = (p.c.n + 255) / 256;
   if (nb == 0) return cudaSuccess;
-  if (dtype == SS_BF16)
+  if (dtype == SS_BF16) {
+    count_launch();
     project_bwd_kernel<__nv_bfloat16><<<(unsigned)nb, 256, 0, st>>>(p);
-  else
+  } else {
+    count_launch();
     project_bwd_kernel<float><<<(unsigned)nb, 256, 0, st>>>(p);
+  }
   return cudaGetLastError();
 }
 

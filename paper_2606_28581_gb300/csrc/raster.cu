@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(const __grid_consta
 
     float T = 1.0f, D = 0.0f, A0 = 0.0f, A1 = 0.0f, A2 = 0.0f, N0 = 0.0f, N1 = 0.0f, N2 = 0.0f;
     uint32_t last = range.x;
+    uint32_t walked = 0;  // contributing pairs, the stopping one included
     bool done = !inside;
     for (uint32_t b0 = range.x; b0 < range.y; b0 += BATCH) {
       const int nb = min((int)(range.y - b0), BATCH);
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(const __grid_consta
           const float4 g2 = sg[j][2];
           const PairEval e = eval_pair(sg[j][0], sg[j][1], g2, x, y, p.k);
           if (!e.contrib) continue;
+          ++walked;
           const float Tn = T * (1.0f - e.alpha);
           if (Tn < p.t_min) {
             done = true;
@@ -167,6 +169,9 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(const __grid_consta
       io.T_final[pix] = T;
       io.last[pix] = last;
     }
+    // algorithmic work counter: one atomic per warp
+    const unsigned int wsum = __reduce_add_sync(0xffffffffu, walked);
+    if ((tid & 31) == 0 && wsum) atomicAdd(&p.status->n_walked, (unsigned long long)wsum);
   }
 }
 
@@ -367,15 +372,22 @@ template <int TW, int TH, int BATCH>
 static cudaError_t launch_fwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
   if (p.total_tiles == 0) return cudaSuccess;
   if (persistent) {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_fwd_kernel<TW, TH, BATCH, true>,
-                                                                  TW * TH, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
+    // resident blocks per SM, queried once (outside any later stream capture)
+    static int per_sm = 0;
+    if (per_sm == 0) {
+      int v = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_fwd_kernel<TW, TH, BATCH, true>,
+                                                                    TW * TH, 0);
+      if (e != cudaSuccess) return e;
+      per_sm = v < 1 ? 1 : v;
+    }
     int grid = num_sms * per_sm;
-    if (grid > p.total_tiles) grid = p.total_tiles;
+    if (grid > p.total_tiles) grid = p.total_tiles; {
+    count_launch();
     raster_fwd_kernel<TW, TH, BATCH, true><<<grid, TW * TH, 0, st>>>(p);
+  }
   } else {
+    count_launch();
     raster_fwd_kernel<TW, TH, BATCH, false><<<p.total_tiles, TW * TH, 0, st>>>(p);
   }
   return cudaGetLastError();
@@ -385,15 +397,22 @@ template <int TW, int TH, int BATCH>
 static cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
   if (p.total_tiles == 0) return cudaSuccess;
   if (persistent) {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_bwd_kernel<TW, TH, BATCH, true>,
-                                                                  TW * TH, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
+    // resident blocks per SM, queried once (outside any later stream capture)
+    static int per_sm = 0;
+    if (per_sm == 0) {
+      int v = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_bwd_kernel<TW, TH, BATCH, true>,
+                                                                    TW * TH, 0);
+      if (e != cudaSuccess) return e;
+      per_sm = v < 1 ? 1 : v;
+    }
     int grid = num_sms * per_sm;
-    if (grid > p.total_tiles) grid = p.total_tiles;
+    if (grid > p.total_tiles) grid = p.total_tiles; {
+    count_launch();
     raster_bwd_kernel<TW, TH, BATCH, true><<<grid, TW * TH, 0, st>>>(p);
+  }
   } else {
+    count_launch();
     raster_bwd_kernel<TW, TH, BATCH, false><<<p.total_tiles, TW * TH, 0, st>>>(p);
   }
   return cudaGetLastError();

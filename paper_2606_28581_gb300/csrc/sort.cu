@@ -111,23 +111,31 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uns
   if (n == 0) return cudaMemsetAsync(total, 0, sizeof(unsigned long long), st);
   const int L = plan.levels;
   if (L == 0) {
+    count_launch();
     scan_down_kernel<uint32_t, uint32_t><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
     return cudaGetLastError();
   }
   // up: block sums
+  count_launch();
   scan_reduce_kernel<uint32_t><<<(unsigned)plan.level_n[0], kScanThreads, 0, st>>>(
       in, n, scratch + plan.level_off[0]);
-  for (int l = 1; l < L; ++l)
+  for (int l = 1; l < L; ++l) {
+    count_launch();
     scan_reduce_kernel<unsigned long long><<<(unsigned)plan.level_n[l], kScanThreads, 0, st>>>(
         scratch + plan.level_off[l - 1], plan.level_n[l - 1], scratch + plan.level_off[l]);
+  }
   // top level fits one block
+  count_launch();
   scan_down_kernel<unsigned long long, unsigned long long><<<1, kScanThreads, 0, st>>>(
       scratch + plan.level_off[L - 1], scratch + plan.level_off[L - 1], plan.level_n[L - 1], nullptr,
       total);
-  for (int l = L - 2; l >= 0; --l)
+  for (int l = L - 2; l >= 0; --l) {
+    count_launch();
     scan_down_kernel<unsigned long long, unsigned long long><<<(unsigned)plan.level_n[l + 1], kScanThreads, 0, st>>>(
         scratch + plan.level_off[l], scratch + plan.level_off[l], plan.level_n[l],
         scratch + plan.level_off[l + 1], nullptr);
+  }
+  count_launch();
   scan_down_kernel<uint32_t, uint32_t><<<(unsigned)plan.level_n[0], kScanThreads, 0, st>>>(
       in, out, n, scratch + plan.level_off[0], nullptr);
   return cudaGetLastError();
@@ -237,13 +245,16 @@ cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_
   for (int shift = bit_lo; shift < bit_hi; shift += 8) {
     const int bits = (bit_hi - shift) < 8 ? (bit_hi - shift) : 8;
     const uint32_t mask = (1u << bits) - 1u;
+    count_launch();
     radix_upsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, n_host, n_dev, shift, mask, hist,
                                                                        nblocks);
     cudaError_t e = exclusive_scan_u32(hist, hist_off, 256 * nblocks, scan_scratch, hs,
                                        scan_scratch + hs.scratch_elems - 1, st);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return e; {
+    count_launch();
     radix_downsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n_host, n_dev, shift,
                                                                          mask, hist_off, nblocks);
+  }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uint32_t* t;
@@ -271,11 +282,14 @@ cudaError_t launch_height_keys(const void* means, int dtype, int64_t n, int64_t 
                                uint32_t* vals, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const unsigned nb = (unsigned)((n + 255) / 256);
-  if (dtype == SS_BF16)
+  if (dtype == SS_BF16) {
+    count_launch();
     height_keys_kernel<__nv_bfloat16><<<nb, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(means), n, n_pad,
                                                            keys, vals);
-  else
+  } else {
+    count_launch();
     height_keys_kernel<float><<<nb, 256, 0, st>>>(static_cast<const float*>(means), n, n_pad, keys, vals);
+  }
   return cudaGetLastError();
 }
 
@@ -311,15 +325,19 @@ __global__ void emit_kernel(BinParams p) {
 
 cudaError_t launch_counts(const BinParams& p, cudaStream_t st) {
   const int64_t m = (int64_t)p.n_targets * p.n;
-  if (m == 0) return cudaSuccess;
+  if (m == 0) return cudaSuccess; {
+  count_launch();
   counts_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p);
+}
   return cudaGetLastError();
 }
 
 cudaError_t launch_emit(const BinParams& p, cudaStream_t st) {
   const int64_t m = (int64_t)p.n_targets * p.n;
-  if (m == 0) return cudaSuccess;
+  if (m == 0) return cudaSuccess; {
+  count_launch();
   emit_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p);
+}
   return cudaGetLastError();
 }
 
@@ -332,6 +350,7 @@ __global__ void finish_count_kernel(StatusBlock* status, const unsigned long lon
 
 cudaError_t launch_finish_count(StatusBlock* status, const uint32_t*, const uint32_t*,
                                 const unsigned long long* total, int64_t capacity, cudaStream_t st) {
+  count_launch();
   finish_count_kernel<<<1, 1, 0, st>>>(status, total, capacity);
   return cudaGetLastError();
 }
@@ -347,8 +366,10 @@ __global__ void ranges_kernel(const uint32_t* keys, const StatusBlock* status, u
 
 cudaError_t launch_ranges(const uint32_t* keys, const StatusBlock* status, uint2* ranges, int64_t capacity,
                           cudaStream_t st) {
-  if (capacity == 0) return cudaSuccess;
+  if (capacity == 0) return cudaSuccess; {
+  count_launch();
   ranges_kernel<<<(unsigned)((capacity + 255) / 256), 256, 0, st>>>(keys, status, ranges);
+}
   return cudaGetLastError();
 }
 

@@ -148,15 +148,32 @@ class Frame:
         """Accumulate gradients into ``grads`` (dict of fp32 [C, n_pad] tensors: means,
         scales, quats, opacity, rgb) and into d_dF [V,2,4] / d_color [V,3,4]."""
         io = out.io_array(upstream)
-        g = L.ss_splat_grads()
-        g.means, g.scales, g.quats = L.ptr(grads["means"]), L.ptr(grads["scales"]), L.ptr(grads["quats"])
-        g.opacity, g.rgb = L.ptr(grads["opacity"]), L.ptr(grads["rgb"])
-        g.n_pad = int(grads["means"].shape[-1])
+        g = grads_struct(grads)
         L.rasterize_bwd(splats, self.cams, self.n_cams, self.passes, dF, color, self.opts, io, g, d_dF,
                         d_color, self.ws, self.ws_bytes, self.capacity, stream)
 
+    def backward_pixels(self, splats: L.ss_splats, out: Outputs, upstream: Sequence[dict], color=None,
+                        d_color=None, stream=None):
+        """Per-pixel adjoint only (K4); finish with :meth:`backward_project`."""
+        io = out.io_array(upstream)
+        L.rasterize_bwd(splats, self.cams, self.n_cams, self.passes, None, color, self.opts, io, None, None,
+                        d_color, self.ws, self.ws_bytes, self.capacity, stream)
+
+    def backward_project(self, splats: L.ss_splats, grads: dict, d_dF=None, stream=None):
+        """Projection adjoint (K5) of the records left by :meth:`backward_pixels`."""
+        L.project_bwd(splats, self.cams, self.n_cams, self.passes, self.opts, grads_struct(grads), d_dF,
+                      self.ws, self.ws_bytes, self.capacity, stream)
+
     def status(self, stream=None):
         return L.frame_status(self.ws, self.ws_bytes, stream)
+
+
+def grads_struct(grads: dict) -> L.ss_splat_grads:
+    g = L.ss_splat_grads()
+    g.means, g.scales, g.quats = L.ptr(grads["means"]), L.ptr(grads["scales"]), L.ptr(grads["quats"])
+    g.opacity, g.rgb = L.ptr(grads["opacity"]), L.ptr(grads["rgb"])
+    g.n_pad = int(grads["means"].shape[-1])
+    return g
 
 
 def zero_grads(n_pad: int, device) -> dict:

@@ -197,7 +197,7 @@ def test_capacity_overflow_is_reported_and_recovered():
     L.project_splats(ds.splats, frame.cams, 1, 1, ds.dF, frame.opts, frame.ws, frame.ws_bytes, 100)
     st, needed = L.bin_and_sort(ds.splats, frame.cams, 1, 1, frame.opts, frame.ws, frame.ws_bytes, 100)
     assert st == L.SS_ERR_CAPACITY and needed > 100
-    st2, needed2, _, flags = frame.status()
+    st2, needed2, _, _, flags = frame.status()
     assert st2 == L.SS_ERR_CAPACITY and needed2 == needed and flags & 1
     # the frame grows its workspace and re-runs
     out = frame.forward(ds.splats, ds.dF, ds.color)
@@ -244,7 +244,7 @@ def test_nonfinite_splat_is_culled_and_counted():
     sc2.means[0, -1] = np.nan
     ds2 = DeviceScene(sc2)
     frame, out = run_forward(ds2)
-    st, _, nonfinite, _ = frame.status()
+    st, _, nonfinite, _, _ = frame.status()
     assert st == L.SS_ERR_NONFINITE and nonfinite == 1
     assert torch.equal(out.rgb[0], ref.rgb[0])
 
@@ -258,3 +258,16 @@ def test_empty_scene():
     assert torch.all(out.alpha[0] == 0) and torch.all(out.T_final[0] == 1)
     c = torch.from_numpy(scene.cameras[0].color[:, 3]).cuda()
     assert torch.allclose(out.rgb[0], c[:, None, None].expand_as(out.rgb[0]))
+
+
+def test_walked_pair_counter_matches_oracle():
+    """The forward's count of walked (pixel, splat) pairs is the per-pixel contributor count
+    of the definition (plus the stopping pair), summed over the image."""
+    scene = ragged_scene(seed=12)
+    ds = DeviceScene(scene)
+    frame, out = run_forward(ds)
+    _, _, _, walked, _ = frame.status()
+    ora = oracle_forward(ds.stored_scene64(), scene.cameras[0])
+    ref = int(ora["ncontrib"].sum() + ora["terminated"].sum())
+    slack = int((ora["margin_fwd"] < MARGIN).sum()) * 2
+    assert abs(walked - ref) <= slack, (walked, ref)
