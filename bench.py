@@ -496,6 +496,7 @@ def run_ours(args, dist):
                 "config": {"workload": WORKLOAD_TEXT[args.workload], "n_splats": scene.n, "views": len(cams),
                            "main_pixels_per_gpu": main_px, "sun_pixels_per_gpu": sun_px,
                            "storage": args.storage, "tile": f"{opts.tile_w}x{opts.tile_h}", "batch": opts.batch,
+                           "pixels_per_thread": opts.pixels_per_thread,
                            "launch": "one CUDA graph per step; persistent forward and backward launches over "
                                      "all (target, tile) items",
                            "l2": "not flushed: every step streams > 1 GB of projected records, lists and "

@@ -107,7 +107,7 @@ typedef struct {
 /* Rasterizer options.  ss_default_opts() fills the defaults in brackets. */
 typedef struct {
   int32_t tile_w, tile_h; /* screen tile [16 x 16]; also 32 x 8 and 8 x 32 */
-  int32_t batch;          /* splats staged per block in shared memory [256]; 64, 128 or 256 */
+  int32_t batch;          /* splats staged per block in shared memory [256]; 128 or 256 */
   int32_t persistent;     /* [0] one block per tile; 1: one persistent launch that pulls
                              (target, tile) work items from a queue */
   float sigma_px;         /* screen-space low-pass sigma, pixels [1/sqrt(2)] */
@@ -115,7 +115,9 @@ typedef struct {
   float alpha_min;        /* a splat contributes iff alpha >= alpha_min [1/255] */
   float alpha_max;        /* alpha = min(alpha_max, o G^) [0.99] */
   float t_min;            /* stop before the splat that takes T below t_min [1e-4] */
-  int32_t reserved[3];
+  int32_t pixels_per_thread; /* [2]; 4 for 16 x 16 and 8 x 32 tiles.  Tile shape, batch,
+                                persistence and pixels per thread never change an output. */
+  int32_t reserved[2];
 } ss_raster_opts;
 
 /* Per render target I/O (device pointers; row-major [H][W] planes of the

@@ -23,7 +23,14 @@ import torch
 from . import _lib as L
 from .frame import Frame, Outputs, grads_struct
 
-TILE_CANDIDATES = [(16, 16, 256), (16, 16, 128), (32, 8, 256), (32, 8, 128), (8, 32, 256), (8, 32, 128)]
+# (tile_w, tile_h, batch, pixels per thread)
+TILE_CANDIDATES = [(16, 16, 256, 2), (16, 16, 256, 4), (16, 16, 128, 2), (32, 8, 256, 2), (8, 32, 256, 2),
+                   (8, 32, 256, 4)]
+
+
+def _opts(c):
+    tw, th, b, ppt = c
+    return L.default_opts(tile_w=tw, tile_h=th, batch=b, pixels_per_thread=ppt, persistent=1)
 
 
 class BatchedStep:
@@ -36,7 +43,7 @@ class BatchedStep:
 
     def __init__(self, cameras: Sequence, splats: dict, n: int, dF, color, upstream: Sequence[dict],
                  passes: int = L.SS_PASS_MAIN | L.SS_PASS_SUN, opts: Optional[L.ss_raster_opts] = None,
-                 capacity_slack: float = 1.10, device="cuda"):
+                 capacity_slack: float = 1.10, capacity: Optional[int] = None, device="cuda"):
         self.opts = opts if opts is not None else L.default_opts(persistent=1)
         self.frame = Frame(cameras, passes, self.opts, device=device)
         self.tensors = splats
@@ -57,7 +64,7 @@ class BatchedStep:
         self.graph = None
         # size the intersection capacity with one synchronised eager run
         needed = self.frame.project_and_bin(self.splats, self.dF, sync=True)
-        cap = max(1 << 16, int(needed * capacity_slack) + 4096)
+        cap = capacity if capacity is not None else max(1 << 16, int(needed * capacity_slack) + 4096)
         self.frame.ensure_workspace(self.splats, cap)
 
     # ------------------------------------------------------------------ phases
@@ -153,7 +160,7 @@ def workload_key(cameras: Sequence, n: int, dtype, passes: int) -> str:
 
 def autotune(make_step, key: str, candidates=TILE_CANDIDATES, warmup: int = 1, iters: int = 3,
              use_cache: bool = True, log=None):
-    """Time ``make_step(opts)`` (a BatchedStep) for each (tile_w, tile_h, batch) candidate with
+    """Time ``make_step(opts)`` (a BatchedStep) for each (tile_w, tile_h, batch, ppt) candidate with
     persistent launches and return the fastest options.  Results are cached by ``key``."""
     path = _cache_path()
     cache = {}
@@ -162,12 +169,11 @@ def autotune(make_step, key: str, candidates=TILE_CANDIDATES, warmup: int = 1, i
             cache = json.load(open(path))
         except Exception:
             cache = {}
-    if use_cache and key in cache:
-        tw, th, b = cache[key]["best"]
-        return L.default_opts(tile_w=tw, tile_h=th, batch=b, persistent=1), cache[key]
+    if use_cache and key in cache and len(cache[key].get("best", ())) == 4:
+        return _opts(cache[key]["best"]), cache[key]
     results = {}
-    for (tw, th, b) in candidates:
-        opts = L.default_opts(tile_w=tw, tile_h=th, batch=b, persistent=1)
+    for cand in candidates:
+        opts = _opts(cand)
         step = make_step(opts)
         for _ in range(warmup):
             step.step_eager()
@@ -181,14 +187,14 @@ def autotune(make_step, key: str, candidates=TILE_CANDIDATES, warmup: int = 1, i
             ev1.synchronize()
             times.append(ev0.elapsed_time(ev1))
         times.sort()
-        results[f"{tw}x{th}x{b}"] = times[len(times) // 2]
+        name = "x".join(str(v) for v in cand)
+        results[name] = times[len(times) // 2]
         if log:
-            log(f"autotune {tw}x{th} batch {b}: {results[f'{tw}x{th}x{b}']:.3f} ms")
+            log(f"autotune tile {cand[0]}x{cand[1]} batch {cand[2]} ppt {cand[3]}: {results[name]:.3f} ms")
         del step
         torch.cuda.empty_cache()
-    best = min(results, key=results.get)
-    tw, th, b = (int(v) for v in best.split("x"))
-    entry = {"best": [tw, th, b], "ms": results}
+    best = [int(v) for v in min(results, key=results.get).split("x")]
+    entry = {"best": best, "ms": results}
     if use_cache:
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)
@@ -196,4 +202,4 @@ def autotune(make_step, key: str, candidates=TILE_CANDIDATES, warmup: int = 1, i
             json.dump(cache, open(path, "w"), indent=1)
         except OSError:
             pass
-    return L.default_opts(tile_w=tw, tile_h=th, batch=b, persistent=1), entry
+    return _opts(best), entry

@@ -43,7 +43,9 @@ ss_status check_opts(const ss_raster_opts* o) {
   const bool shape = (o->tile_w == 16 && o->tile_h == 16) || (o->tile_w == 32 && o->tile_h == 8) ||
                      (o->tile_w == 8 && o->tile_h == 32);
   if (!shape) return SS_ERR_INVALID_ARG;
-  if (o->batch != 64 && o->batch != 128 && o->batch != 256) return SS_ERR_INVALID_ARG;
+  if (o->batch != 128 && o->batch != 256) return SS_ERR_INVALID_ARG;
+  if (o->pixels_per_thread != 2 && o->pixels_per_thread != 4) return SS_ERR_INVALID_ARG;
+  if (o->pixels_per_thread == 4 && o->tile_h < 16) return SS_ERR_INVALID_ARG;
   if (o->persistent != 0 && o->persistent != 1) return SS_ERR_INVALID_ARG;
   if (!finite(o->sigma_px) || !(o->sigma_px > 0.0f)) return SS_ERR_INVALID_ARG;
   if (!finite(o->det_eps) || !(o->det_eps >= 0.0f)) return SS_ERR_INVALID_ARG;
@@ -148,7 +150,7 @@ ss_status make_layout(const ss_splats* s, const ss_camera* cams, int32_t n_cams,
   L->tcams = take(sizeof(TargetCam) * kMaxTargets);
   L->geom = take(TN * 48);
   L->feat = take(TN * 32);
-  L->rect = take(TN * 8);
+  L->rect = take(TN * 16);
   L->grad = take(TN * 64);
   const size_t np4 = (size_t)L->n_pad * 4;
   L->hk_a = take(np4);
@@ -250,6 +252,8 @@ ss_status fill_raster(RasterParams& rp, const ss_splats* s, const Layout& L, con
   rp.k.amin = o->alpha_min;
   rp.k.amax = o->alpha_max;
   rp.k.ln_amin_slack = logf(o->alpha_min) - 1e-3f;
+  rp.cull.ln_amin = logf(o->alpha_min);
+  rp.cull.sigma2 = sig * sig;
   rp.t_min = o->t_min;
   return SS_OK;
 }
@@ -264,7 +268,7 @@ ss_status run_project_bwd(const ss_splats* splats, const Layout& L, const ss_ras
                           const ss_splat_grads* grads, float* d_dF, void* ws, cudaStream_t st) {
   ProjectBwdParams pb;
   pb.c = common_of(splats, L, ws);
-  pb.rect = at<ushort4>(ws, L.rect);
+  pb.rect = at<uint4>(ws, L.rect);
   pb.grad = at<float>(ws, L.grad);
   pb.g.means = grads->means;
   pb.g.scales = grads->scales;
@@ -295,6 +299,7 @@ void ss_default_opts(ss_raster_opts* o) {
   o->alpha_min = 1.0f / 255.0f;
   o->alpha_max = 0.99f;
   o->t_min = 1e-4f;
+  o->pixels_per_thread = 2;
 }
 
 const char* ss_status_string(ss_status s) {
@@ -346,13 +351,15 @@ ss_status ss_project_splats(const ss_splats* splats, const ss_camera* cams, int3
   pp.c = common_of(splats, L, ws);
   pp.geom = at<float4>(ws, L.geom);
   pp.feat = at<float4>(ws, L.feat);
-  pp.rect = at<ushort4>(ws, L.rect);
+  pp.rect = at<uint4>(ws, L.rect);
   pp.grad = at<float4>(ws, L.grad);
   pp.status = at<StatusBlock>(ws, L.status);
   pp.amin = opts->alpha_min;
   pp.ln_amin = logf(opts->alpha_min);
   pp.sigma = opts->sigma_px;
   pp.det_eps = opts->det_eps;
+  pp.cull.ln_amin = pp.ln_amin;
+  pp.cull.sigma2 = opts->sigma_px * opts->sigma_px;
   pp.tile_w = opts->tile_w;
   pp.tile_h = opts->tile_h;
   SS_CUDA_TRY(launch_project(pp, splats->dtype, st));
@@ -385,7 +392,7 @@ ss_status ss_bin_and_sort(const ss_splats* splats, const ss_camera* cams, int32_
   bp.n_targets = (int32_t)L.T;
   bp.n = L.n;
   bp.n_pad = L.n_pad;
-  bp.rect = at<ushort4>(ws, L.rect);
+  bp.rect = at<uint4>(ws, L.rect);
   bp.order = order;
   bp.counts = at<uint32_t>(ws, L.counts);
   bp.offsets = at<uint32_t>(ws, L.offsets);
@@ -436,7 +443,8 @@ ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32
   if (opts->persistent)
     ce = cudaMemsetAsync(&at<StatusBlock>(ws, L.status)->work_fwd, 0, sizeof(unsigned int), st);
   if (ce == cudaSuccess)
-    ce = launch_raster_fwd(*rp, opts->tile_w, opts->tile_h, opts->batch, opts->persistent != 0, num_sms_cached(), st);
+    ce = launch_raster_fwd(*rp, opts->tile_w, opts->tile_h, opts->pixels_per_thread, opts->batch,
+                           opts->persistent != 0, num_sms_cached(), st);
   delete rp;
   return ce == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }
@@ -463,7 +471,8 @@ ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32
   if (opts->persistent)
     ce = cudaMemsetAsync(&at<StatusBlock>(ws, L.status)->work_bwd, 0, sizeof(unsigned int), st);
   if (ce == cudaSuccess)
-    ce = launch_raster_bwd(*rp, opts->tile_w, opts->tile_h, opts->batch, opts->persistent != 0, num_sms_cached(), st);
+    ce = launch_raster_bwd(*rp, opts->tile_w, opts->tile_h, opts->pixels_per_thread, opts->batch,
+                           opts->persistent != 0, num_sms_cached(), st);
   delete rp;
   if (ce != cudaSuccess) return SS_ERR_CUDA;
   if (!grads) return SS_OK;

@@ -183,6 +183,52 @@ __device__ __forceinline__ PairEval eval_pair(const float4 g0, const float4 g1, 
   return e;
 }
 
+// ---------------------------------------------------------------- footprint culling
+// Can the splat reach alpha >= alpha_min at a pixel centre inside [xa, xb] x [ya, yb]?
+// The support is the ellipse |Q (x - c)|^2 <= r2 united with the disc |x - c|^2 <= sigma^2 r2,
+// r2 = 2 (ln o - ln alpha_min).  The test is conservative: the radius, the rectangle and the
+// centre (its low part is ignored) carry slack far above the FP32 error of eval_pair, so
+// it never rejects a pair that eval_pair accepts.  Used for warp blocks (raster) and for
+// whole tiles (binning).
+struct CullConsts {
+  float ln_amin;
+  float sigma2;  // sigma^2
+};
+
+__device__ __forceinline__ float edge_min_sq(float px, float py, float qx, float qy, float len) {
+  // min over t in [0, len] of |p + t q|^2
+  const float qq = qx * qx + qy * qy;
+  float t = qq > 0.0f ? -(px * qx + py * qy) / qq : 0.0f;
+  t = fminf(fmaxf(t, 0.0f), len);
+  const float ax = fmaf(t, qx, px), ay = fmaf(t, qy, py);
+  return ax * ax + ay * ay;
+}
+
+__device__ __forceinline__ bool may_touch(const float4 g0, const float4 g1, const float4 g2, float xa, float xb,
+                                          float ya, float yb, const CullConsts& cc) {
+  xa -= 1e-3f; ya -= 1e-3f; xb += 1e-3f; yb += 1e-3f;
+  const float cx = g0.x, cy = g0.y;
+  const float nx = fminf(fmaxf(cx, xa), xb), ny = fminf(fmaxf(cy, ya), yb);
+  const float ddx = nx - cx, ddy = ny - cy;
+  if (fabsf(ddx) > fabsf(g2.y) || fabsf(ddy) > g2.z) return false;  // axis-aligned extent
+  const float r2 = fmaxf(2.0f * (g2.x - cc.ln_amin), 0.0f) * 1.001f + 1e-3f;
+  if (ddx * ddx + ddy * ddy <= r2 * cc.sigma2 * 1.001f + 1e-3f) return true;  // screen-space disc
+  if (g2.y < 0.0f) return false;                                             // degenerate: disc only
+  if (ddx == 0.0f && ddy == 0.0f) return true;                               // centre inside
+  // the ellipse: its nearest approach lies on an edge facing the centre
+  const float Q00 = g1.x, Q01 = g1.y, Q10 = g1.z, Q11 = g1.w;
+  float best = INFINITY;
+  if (ddx != 0.0f) {  // vertical edge x = nx, y in [ya, yb]
+    const float ax = nx - cx, ay = ya - cy;
+    best = fminf(best, edge_min_sq(Q00 * ax + Q01 * ay, Q10 * ax + Q11 * ay, Q01, Q11, yb - ya));
+  }
+  if (ddy != 0.0f) {  // horizontal edge y = ny, x in [xa, xb]
+    const float ax = xa - cx, ay = ny - cy;
+    best = fminf(best, edge_min_sq(Q00 * ax + Q01 * ay, Q10 * ax + Q11 * ay, Q00, Q10, xb - xa));
+  }
+  return best <= r2;
+}
+
 // Host-side count of the kernels this library has launched (or captured into a graph).
 void count_launch();
 

@@ -28,10 +28,11 @@ struct ProjectParams {
   ProjectCommon c;
   float4* geom;  // [T][n_pad][3]
   float4* feat;  // [T][n_pad][2]
-  ushort4* rect; // [T][n_pad]
+  uint4* rect;   // [T][n_pad] tile records (see emit_kernel)
   float4* grad;  // [T][n_pad][4]: zeroed for visible pairs
   StatusBlock* status;
   float amin, ln_amin, sigma, det_eps;
+  CullConsts cull;
   int32_t tile_w, tile_h;
 };
 
@@ -46,7 +47,7 @@ struct GradOut {
 
 struct ProjectBwdParams {
   ProjectCommon c;
-  const ushort4* rect;
+  const uint4* rect;
   const float* grad;  // [T][n_pad][16]
   GradOut g;
   float* d_dF;        // [n_cams][8] or null
@@ -58,7 +59,7 @@ struct BinParams {
   const TargetCam* tcams;
   int32_t n_targets;
   int64_t n, n_pad;
-  const ushort4* rect;      // [T][n_pad]
+  const uint4* rect;        // [T][n_pad] tile records
   const uint32_t* order;    // [n] splat indices, front to back
   uint32_t* counts;         // [T * n]
   const uint32_t* offsets;  // [T * n] exclusive scan of counts (saturated)
@@ -83,6 +84,7 @@ struct RasterParams {
   int64_t n_pad;
   int32_t n_targets, total_tiles;
   EvalConsts k;
+  CullConsts cull;
   float t_min;
   TargetIO io[kMaxTargets];
 };
@@ -131,9 +133,9 @@ cudaError_t launch_ranges(const uint32_t* keys, const StatusBlock* status, uint2
                           int64_t capacity, cudaStream_t st);
 
 // raster (raster.cu)
-cudaError_t launch_raster_fwd(const RasterParams& p, int tile_w, int tile_h, int batch, bool persistent,
+cudaError_t launch_raster_fwd(const RasterParams& p, int tile_w, int tile_h, int ppt, int batch, bool persistent,
                               int num_sms, cudaStream_t st);
-cudaError_t launch_raster_bwd(const RasterParams& p, int tile_w, int tile_h, int batch, bool persistent,
+cudaError_t launch_raster_bwd(const RasterParams& p, int tile_w, int tile_h, int ppt, int batch, bool persistent,
                               int num_sms, cudaStream_t st);
 
 }  // namespace ss

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectParams p) {
   for (int t = 0; t < p.c.n_targets; ++t) {
     const TargetCam& cam = scam[t];
     const int64_t rec = (int64_t)t * np + k;
-    ushort4 rect = make_ushort4(1, 1, 0, 0);
+    uint4 trec = make_uint4(0u, 0u, 0u, 0u);
     if (alive) {
       const SplatProj sp = project_one(s, cam, p.det_eps);
       const float m0 = sp.deg ? 0.0f : sqrtf(sp.M[0][0] * sp.M[0][0] + sp.M[0][1] * sp.M[0][1]);
@@ -223,13 +223,42 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectParams p) {
         float ihi = fminf(floorf(cx + ex - 0.5f), (float)(cam.W - 1));
         float jlo = fmaxf(ceilf(cy - ey - 0.5f), 0.0f);
         float jhi = fminf(floorf(cy + ey - 0.5f), (float)(cam.H - 1));
+        const float4 g0 = make_float4(sp.chi[0], sp.chi[1], sp.clo[0], sp.clo[1]);
+        const float4 g1 = make_float4(sp.Q[0][0], sp.Q[0][1], sp.Q[1][0], sp.Q[1][1]);
+        const float4 g2 = make_float4(lno, sp.deg ? -ex : ex, ey, cam.maxalt - s.p[2]);
+        uint32_t count = 0, mask = 0;
+        int tx0 = 0, ty0 = 0, tx1 = -1, ty1 = -1;
         if (ilo <= ihi && jlo <= jhi) {
-          rect = make_ushort4((unsigned short)((int)ilo / p.tile_w), (unsigned short)((int)jlo / p.tile_h),
-                              (unsigned short)((int)ihi / p.tile_w), (unsigned short)((int)jhi / p.tile_h));
+          tx0 = (int)ilo / p.tile_w; tx1 = (int)ihi / p.tile_w;
+          ty0 = (int)jlo / p.tile_h; ty1 = (int)jhi / p.tile_h;
+          const int ntx = tx1 - tx0 + 1, nty = ty1 - ty0 + 1;
+          if (ntx * nty > 32) {
+            // large footprint: keep every tile of the rectangle
+            mask = 0xffffffffu;
+            count = (uint32_t)(ntx * nty);
+          } else {
+            // exact footprint against each tile's pixel-centre rectangle
+            for (int ty = ty0; ty <= ty1; ++ty) {
+              const float ya = (float)(ty * p.tile_h) + 0.5f;
+              const float yb = (float)(min((ty + 1) * p.tile_h, cam.H) - 1) + 0.5f;
+              for (int tx = tx0; tx <= tx1; ++tx) {
+                const float xa = (float)(tx * p.tile_w) + 0.5f;
+                const float xb = (float)(min((tx + 1) * p.tile_w, cam.W) - 1) + 0.5f;
+                if (may_touch(g0, g1, g2, xa, xb, ya, yb, p.cull)) {
+                  mask |= 1u << ((ty - ty0) * ntx + (tx - tx0));
+                  ++count;
+                }
+              }
+            }
+          }
+        }
+        if (count > 0) {
+          trec = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16), mask,
+                            count);
           float4* g = p.geom + rec * 3;
-          g[0] = make_float4(sp.chi[0], sp.chi[1], sp.clo[0], sp.clo[1]);
-          g[1] = make_float4(sp.Q[0][0], sp.Q[0][1], sp.Q[1][0], sp.Q[1][1]);
-          g[2] = make_float4(lno, sp.deg ? -ex : ex, ey, cam.maxalt - s.p[2]);
+          g[0] = g0;
+          g[1] = g1;
+          g[2] = g2;
           float4* f = p.feat + rec * 2;
           f[0] = make_float4(-s.su * s.R[2][0], -s.sv * s.R[2][1], sp.flip * s.R[0][2], sp.flip * s.R[1][2]);
           f[1] = make_float4(sp.flip * s.R[2][2], s.rgb[0], s.rgb[1], s.rgb[2]);
@@ -242,7 +271,7 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectParams p) {
         }
       }
     }
-    p.rect[rec] = rect;
+    p.rect[rec] = trec;
   }
 }
 
@@ -298,8 +327,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdParams p) {
     const int64_t rec = (int64_t)t * np + k;
     bool live = false;
     if (alive) {
-      const ushort4 rc = p.rect[rec];
-      live = rc.x <= rc.z;
+      live = p.rect[rec].w > 0u;  // the pair was emitted to at least one tile
     }
     if (live) {
       const float4* gp = reinterpret_cast<const float4*>(p.grad + rec * kGradFields);

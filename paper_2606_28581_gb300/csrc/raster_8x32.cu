@@ -1,0 +1,7 @@
+// Rasterizer kernels for 8 x 32 pixel tiles (see raster_impl.cuh).
+#include "raster_impl.cuh"
+
+namespace ss {
+SS_RASTER_DISPATCH(fwd, 8, 32, 4)
+SS_RASTER_DISPATCH(bwd, 8, 32, 4)
+}  // namespace ss

@@ -293,16 +293,16 @@ cudaError_t launch_height_keys(const void* means, int dtype, int64_t n, int64_t 
   return cudaGetLastError();
 }
 
-__device__ __forceinline__ uint32_t rect_count(ushort4 r) {
-  return (r.x <= r.z && r.y <= r.w) ? (uint32_t)(r.z - r.x + 1) * (uint32_t)(r.w - r.y + 1) : 0u;
-}
-
+// Tile record of a (target, splat) (written by the projection): x = x0 | y0 << 16,
+// y = x1 | y1 << 16 (tile rectangle), z = bitmask of the tiles of the rectangle, in row-major
+// order, that the footprint touches (all ones when the rectangle has more than 32 tiles),
+// w = number of tiles kept (0: culled).
 __global__ void counts_kernel(BinParams p) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)p.n_targets * p.n) return;
   const int64_t t = idx / p.n, r = idx - t * p.n;
   const uint32_t k = p.order[r];
-  p.counts[idx] = rect_count(p.rect[t * p.n_pad + k]);
+  p.counts[idx] = p.rect[t * p.n_pad + k].w;
 }
 
 __global__ void emit_kernel(BinParams p) {
@@ -310,15 +310,19 @@ __global__ void emit_kernel(BinParams p) {
   if (idx >= (int64_t)p.n_targets * p.n) return;
   const int64_t t = idx / p.n, r = idx - t * p.n;
   const uint32_t k = p.order[r];
-  const ushort4 rc = p.rect[t * p.n_pad + k];
-  if (!(rc.x <= rc.z && rc.y <= rc.w)) return;
+  const uint4 rc = p.rect[t * p.n_pad + k];
+  if (rc.w == 0u) return;
+  const int x0 = (int)(rc.x & 0xffffu), y0 = (int)(rc.x >> 16), x1 = (int)(rc.y & 0xffffu), y1 = (int)(rc.y >> 16);
   const TargetCam& cam = p.tcams[t];
   int64_t pos = p.offsets[idx];
-  for (int ty = rc.y; ty <= rc.w; ++ty) {
-    for (int tx = rc.x; tx <= rc.z; ++tx, ++pos) {
+  int bit = 0;
+  for (int ty = y0; ty <= y1; ++ty) {
+    for (int tx = x0; tx <= x1; ++tx, ++bit) {
+      if (bit < 32 && !((rc.z >> bit) & 1u)) continue;
       if (pos >= p.capacity) return;
       p.keys[pos] = (uint32_t)(cam.tile_base + ty * cam.tiles_x + tx);
       p.vals[pos] = k;
+      ++pos;
     }
   }
 }

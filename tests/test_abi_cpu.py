@@ -59,7 +59,10 @@ def test_workspace_size_validates_on_the_host(lib):
     size = L.workspace_size(s, cams, 1, L.SS_PASS_MAIN | L.SS_PASS_SUN, o, 1 << 20)
     assert size > 2 * sc.n * (48 + 32 + 8 + 64)
     out = ctypes.c_size_t(0)
-    bad = L.default_opts(batch=100)
+    for bad in (L.default_opts(batch=100), L.default_opts(pixels_per_thread=3),
+                L.default_opts(tile_w=32, tile_h=8, pixels_per_thread=4)):
+        assert lib.ss_workspace_size(ctypes.byref(s), cams, 1, 1, ctypes.byref(bad), 1 << 20,
+                                     ctypes.byref(out)) == L.SS_ERR_INVALID_ARG
     assert lib.ss_workspace_size(ctypes.byref(s), cams, 1, 1, ctypes.byref(bad), 1 << 20,
                                  ctypes.byref(out)) == L.SS_ERR_INVALID_ARG
     s.n_pad = sc.n + 1

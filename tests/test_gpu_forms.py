@@ -50,6 +50,11 @@ def loss_of(outs, ws):
     return sum((o[k] * w[k]).sum() for o, w in zip(outs, ws) for k in w)
 
 
+def loss64(outs, ws):
+    """The same loss accumulated in float64 (finite differences need it)."""
+    return sum(float((o[k].double() * w[k].double()).sum()) for o, w in zip(outs, ws) for k in w)
+
+
 @pytest.mark.parametrize("storage", [torch.float32, torch.bfloat16])
 def test_autograd_matches_oracle_adjoint(storage):
     scene = scene3()
@@ -94,8 +99,10 @@ def test_autograd_matches_central_differences():
            for k, v in dict(rgb=r, depth=d, normal=n, alpha=a).items()}]
     outs = render(frame, P["means"], P["scales"], P["quats"], P["opacity"], P["rgb"], P["dF"], P["color"])
     loss_of(outs, ws).backward()
-    scale = dict(means=2e-4, scales=5e-5, quats=2e-3, opacity=2e-3, rgb=2e-3, dF=np.array([2e-1] * 3 + [5e-3]),
-                 color=2e-3)
+    # perturbations of ~1e-3 px in screen position, ~0.1 % in size, ~1e-4 rad in orientation:
+    # small enough that no weighted pixel crosses the 1/255 threshold (margin mask 2e-2)
+    scale = dict(means=3e-5, scales=2e-5, quats=1e-4, opacity=5e-4, rgb=5e-4, dF=np.array([1e-3] * 3 + [1e-3]),
+                 color=5e-4)
     dirs = {}
     for k, v in P.items():
         dk = rng.normal(size=tuple(v.shape)) * (scale[k] if k != "dF" else scale[k][None, None, :])
@@ -107,7 +114,7 @@ def test_autograd_matches_central_differences():
             q = {k: (P[k] + h * dirs[k]).contiguous() for k in P}
             fr = Frame(scene.cameras, L.SS_PASS_MAIN)
             outs = render(fr, q["means"], q["scales"], q["quats"], q["opacity"], q["rgb"], q["dF"], q["color"])
-            return float(loss_of(outs, ws).double())
+            return loss64(outs, ws)
 
     fd = (f(1.0) - f(-1.0)) / 2.0
     assert abs(fd - analytic) <= 2e-2 * max(abs(analytic), 1e-3), (fd, analytic)
@@ -139,8 +146,9 @@ def test_batched_graph_replay_matches_eager_and_oracle():
         if a is not None:
             assert torch.equal(a, b)
     for k in eager:
+        # the same sums in another atomic order
         grad_close(step.grads[k].cpu().numpy().astype(np.float64), eager[k].cpu().numpy().astype(np.float64),
-                   rtol=1e-5, name=k)
+                   rtol=1e-4, name=k)
     # the single-view plain path gives the same forward as the batched persistent launch
     frame1 = Frame([scene.cameras[1]], 3)
     sub = DeviceScene(scene, dtype=torch.bfloat16)
@@ -155,7 +163,7 @@ def test_batched_capacity_overflow_flag_after_replay():
     frame0 = Frame(scene.cameras, 3)
     ups = [dict(depth=torch.ones(t.height, t.width, device="cuda")) for t in frame0.targets]
     splats = dict(means=ds.means, scales=ds.scales, quats=ds.quats, opacity=ds.opacity, rgb=ds.rgb)
-    step = BatchedStep(scene.cameras, splats, ds.n, ds.dF, ds.color, ups, capacity_slack=0.5)
+    step = BatchedStep(scene.cameras, splats, ds.n, ds.dF, ds.color, ups, capacity=1000)
     step.capture()
     step.replay()
     st, needed, _, flags = step.check()
@@ -171,9 +179,9 @@ def test_autotuner_picks_and_caches(tmp_path):
         ups = [dict(depth=torch.ones(t.height, t.width, device="cuda")) for t in frame0.targets]
         splats = dict(means=ds.means, scales=ds.scales, quats=ds.quats, opacity=ds.opacity, rgb=ds.rgb)
         mk = lambda o: BatchedStep(scene.cameras, splats, ds.n, ds.dF, ds.color, ups, opts=o)
-        cands = [(16, 16, 256), (32, 8, 128)]
+        cands = [(16, 16, 256, 2), (8, 32, 128, 4)]
         opts, entry = autotune(mk, "test-key", candidates=cands)
-        assert (opts.tile_w, opts.tile_h, opts.batch) in cands and opts.persistent == 1
+        assert (opts.tile_w, opts.tile_h, opts.batch, opts.pixels_per_thread) in cands and opts.persistent == 1
         assert len(entry["ms"]) == 2
         opts2, entry2 = autotune(mk, "test-key", candidates=cands)
         assert entry2["best"] == entry["best"]
