@@ -115,8 +115,9 @@ typedef struct {
   float alpha_min;        /* a splat contributes iff alpha >= alpha_min [1/255] */
   float alpha_max;        /* alpha = min(alpha_max, o G^) [0.99] */
   float t_min;            /* stop before the splat that takes T below t_min [1e-4] */
-  int32_t pixels_per_thread; /* [2]; 4 for 16 x 16 and 8 x 32 tiles.  Tile shape, batch,
-                                persistence and pixels per thread never change an output. */
+  int32_t pixels_per_thread; /* [2], the only value: each lane owns two pixels of a 4 x 4
+                                sub-block.  Tile shape, batch and persistence never change an
+                                output. */
   int32_t reserved[2];
 } ss_raster_opts;
 

@@ -24,8 +24,8 @@ from . import _lib as L
 from .frame import Frame, Outputs, grads_struct
 
 # (tile_w, tile_h, batch, pixels per thread)
-TILE_CANDIDATES = [(16, 16, 256, 2), (16, 16, 256, 4), (16, 16, 128, 2), (32, 8, 256, 2), (8, 32, 256, 2),
-                   (8, 32, 256, 4)]
+TILE_CANDIDATES = [(16, 16, 256, 2), (16, 16, 128, 2), (32, 8, 256, 2), (32, 8, 128, 2), (8, 32, 256, 2),
+                   (8, 32, 128, 2)]
 
 
 def _opts(c):

@@ -44,8 +44,7 @@ ss_status check_opts(const ss_raster_opts* o) {
                      (o->tile_w == 8 && o->tile_h == 32);
   if (!shape) return SS_ERR_INVALID_ARG;
   if (o->batch != 128 && o->batch != 256) return SS_ERR_INVALID_ARG;
-  if (o->pixels_per_thread != 2 && o->pixels_per_thread != 4) return SS_ERR_INVALID_ARG;
-  if (o->pixels_per_thread == 4 && o->tile_h < 16) return SS_ERR_INVALID_ARG;
+  if (o->pixels_per_thread != 2) return SS_ERR_INVALID_ARG;
   if (o->persistent != 0 && o->persistent != 1) return SS_ERR_INVALID_ARG;
   if (!finite(o->sigma_px) || !(o->sigma_px > 0.0f)) return SS_ERR_INVALID_ARG;
   if (!finite(o->det_eps) || !(o->det_eps >= 0.0f)) return SS_ERR_INVALID_ARG;
@@ -443,7 +442,7 @@ ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32
   if (opts->persistent)
     ce = cudaMemsetAsync(&at<StatusBlock>(ws, L.status)->work_fwd, 0, sizeof(unsigned int), st);
   if (ce == cudaSuccess)
-    ce = launch_raster_fwd(*rp, opts->tile_w, opts->tile_h, opts->pixels_per_thread, opts->batch,
+    ce = launch_raster_fwd(*rp, opts->tile_w, opts->tile_h, opts->batch,
                            opts->persistent != 0, num_sms_cached(), st);
   delete rp;
   return ce == cudaSuccess ? SS_OK : SS_ERR_CUDA;
@@ -471,7 +470,7 @@ ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32
   if (opts->persistent)
     ce = cudaMemsetAsync(&at<StatusBlock>(ws, L.status)->work_bwd, 0, sizeof(unsigned int), st);
   if (ce == cudaSuccess)
-    ce = launch_raster_bwd(*rp, opts->tile_w, opts->tile_h, opts->pixels_per_thread, opts->batch,
+    ce = launch_raster_bwd(*rp, opts->tile_w, opts->tile_h, opts->batch,
                            opts->persistent != 0, num_sms_cached(), st);
   delete rp;
   if (ce != cudaSuccess) return SS_ERR_CUDA;

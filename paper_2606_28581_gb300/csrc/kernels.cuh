@@ -133,9 +133,9 @@ cudaError_t launch_ranges(const uint32_t* keys, const StatusBlock* status, uint2
                           int64_t capacity, cudaStream_t st);
 
 // raster (raster.cu)
-cudaError_t launch_raster_fwd(const RasterParams& p, int tile_w, int tile_h, int ppt, int batch, bool persistent,
+cudaError_t launch_raster_fwd(const RasterParams& p, int tile_w, int tile_h, int batch, bool persistent,
                               int num_sms, cudaStream_t st);
-cudaError_t launch_raster_bwd(const RasterParams& p, int tile_w, int tile_h, int ppt, int batch, bool persistent,
+cudaError_t launch_raster_bwd(const RasterParams& p, int tile_w, int tile_h, int batch, bool persistent,
                               int num_sms, cudaStream_t st);
 
 }  // namespace ss

@@ -3,26 +3,26 @@
 
 namespace ss {
 
-cudaError_t launch_raster_fwd_16x16(const RasterParams&, int, int, bool, int, cudaStream_t);
-cudaError_t launch_raster_bwd_16x16(const RasterParams&, int, int, bool, int, cudaStream_t);
-cudaError_t launch_raster_fwd_32x8(const RasterParams&, int, int, bool, int, cudaStream_t);
-cudaError_t launch_raster_bwd_32x8(const RasterParams&, int, int, bool, int, cudaStream_t);
-cudaError_t launch_raster_fwd_8x32(const RasterParams&, int, int, bool, int, cudaStream_t);
-cudaError_t launch_raster_bwd_8x32(const RasterParams&, int, int, bool, int, cudaStream_t);
+cudaError_t launch_raster_fwd_16x16(const RasterParams&, int, bool, int, cudaStream_t);
+cudaError_t launch_raster_bwd_16x16(const RasterParams&, int, bool, int, cudaStream_t);
+cudaError_t launch_raster_fwd_32x8(const RasterParams&, int, bool, int, cudaStream_t);
+cudaError_t launch_raster_bwd_32x8(const RasterParams&, int, bool, int, cudaStream_t);
+cudaError_t launch_raster_fwd_8x32(const RasterParams&, int, bool, int, cudaStream_t);
+cudaError_t launch_raster_bwd_8x32(const RasterParams&, int, bool, int, cudaStream_t);
 
-cudaError_t launch_raster_fwd(const RasterParams& p, int tile_w, int tile_h, int ppt, int batch, bool persistent,
-                              int num_sms, cudaStream_t st) {
-  if (tile_w == 16 && tile_h == 16) return launch_raster_fwd_16x16(p, ppt, batch, persistent, num_sms, st);
-  if (tile_w == 32 && tile_h == 8) return launch_raster_fwd_32x8(p, ppt, batch, persistent, num_sms, st);
-  if (tile_w == 8 && tile_h == 32) return launch_raster_fwd_8x32(p, ppt, batch, persistent, num_sms, st);
+cudaError_t launch_raster_fwd(const RasterParams& p, int tile_w, int tile_h, int batch, bool persistent, int num_sms,
+                              cudaStream_t st) {
+  if (tile_w == 16 && tile_h == 16) return launch_raster_fwd_16x16(p, batch, persistent, num_sms, st);
+  if (tile_w == 32 && tile_h == 8) return launch_raster_fwd_32x8(p, batch, persistent, num_sms, st);
+  if (tile_w == 8 && tile_h == 32) return launch_raster_fwd_8x32(p, batch, persistent, num_sms, st);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_raster_bwd(const RasterParams& p, int tile_w, int tile_h, int ppt, int batch, bool persistent,
-                              int num_sms, cudaStream_t st) {
-  if (tile_w == 16 && tile_h == 16) return launch_raster_bwd_16x16(p, ppt, batch, persistent, num_sms, st);
-  if (tile_w == 32 && tile_h == 8) return launch_raster_bwd_32x8(p, ppt, batch, persistent, num_sms, st);
-  if (tile_w == 8 && tile_h == 32) return launch_raster_bwd_8x32(p, ppt, batch, persistent, num_sms, st);
+cudaError_t launch_raster_bwd(const RasterParams& p, int tile_w, int tile_h, int batch, bool persistent, int num_sms,
+                              cudaStream_t st) {
+  if (tile_w == 16 && tile_h == 16) return launch_raster_bwd_16x16(p, batch, persistent, num_sms, st);
+  if (tile_w == 32 && tile_h == 8) return launch_raster_bwd_32x8(p, batch, persistent, num_sms, st);
+  if (tile_w == 8 && tile_h == 32) return launch_raster_bwd_8x32(p, batch, persistent, num_sms, st);
   return cudaErrorInvalidValue;
 }
 

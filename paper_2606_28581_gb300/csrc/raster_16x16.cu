@@ -2,6 +2,6 @@
 #include "raster_impl.cuh"
 
 namespace ss {
-SS_RASTER_DISPATCH(fwd, 16, 16, 4)
-SS_RASTER_DISPATCH(bwd, 16, 16, 4)
+SS_RASTER_DISPATCH(fwd, 16, 16)
+SS_RASTER_DISPATCH(bwd, 16, 16)
 }  // namespace ss

@@ -2,6 +2,6 @@
 #include "raster_impl.cuh"
 
 namespace ss {
-SS_RASTER_DISPATCH(fwd, 32, 8, 2)
-SS_RASTER_DISPATCH(bwd, 32, 8, 2)
+SS_RASTER_DISPATCH(fwd, 32, 8)
+SS_RASTER_DISPATCH(bwd, 32, 8)
 }  // namespace ss

@@ -2,6 +2,6 @@
 #include "raster_impl.cuh"
 
 namespace ss {
-SS_RASTER_DISPATCH(fwd, 8, 32, 4)
-SS_RASTER_DISPATCH(bwd, 8, 32, 4)
+SS_RASTER_DISPATCH(fwd, 8, 32)
+SS_RASTER_DISPATCH(bwd, 8, 32)
 }  // namespace ss

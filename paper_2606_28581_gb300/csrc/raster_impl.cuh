@@ -1,25 +1,30 @@
 // Forward (K3) and backward (K4) rasterization, Sec. 3.2 Eq. rasterization.
 //
-// One block renders one screen tile of one target.  The block stages the tile's sorted splat
-// list batch by batch in shared memory.  Each warp owns an 8 x (4 PPT) pixel block, each lane
-// PPT pixels of one column (rows ly, ly + 4, ...).  Per batch every warp ballots which staged
-// splats can reach its block (exact footprint test, `may_touch`) and walks only those, in list
-// order (forward) or reverse list order (backward); a pixel's walk is therefore exactly the
-// per-pixel definition.  With PERSIST one launch sized to the GPU pulls (target, tile) items
-// from a queue, so views of uneven size and sun views share a single launch.
+// One block renders one screen tile of one target and stages the tile's sorted splat list,
+// batch by batch, in shared memory.  Each warp owns an 8 x 8 pixel block made of four 4 x 4
+// sub-blocks; the 8 lanes of a group own one sub-block, two pixels per lane (rows r, r + 2).
+// For every 32 staged splats each group tests which of them can reach its sub-block (exact
+// footprint test, `may_touch`) and walks only those, in list order (forward) or reverse list
+// order (backward), independently of the other groups.  A pixel's walk is therefore exactly
+// the per-pixel definition, whatever the tile shape or schedule.  With PERSIST one launch
+// sized to the GPU pulls (target, tile) items from a queue, so views of uneven size and sun
+// views share a single launch.
 //
 // Backward: with T_i the transmittance in front of splat i and S_i the composite behind it
 // (normalised to T_{i+1}), d f / d alpha_i = T_i (f_i - S_i); the alpha output adds
 // T_final / (1 - alpha_i).  T_i is recovered as T_{i+1} / (1 - alpha_i) from the saved
 // T_final (alpha <= alpha_max < 1 keeps the division safe); only T_final and the end of the
-// walk are stored per pixel.  A lane first sums its PPT pixels' gradient contributions, the
-// warp reduces the 16 fields with a transposed butterfly (16 shuffles), warps meet in shared
-// memory, and one global atomic per (tile, splat, field) leaves the block.
+// walk are stored per pixel.  A lane first sums its two pixels' gradient contributions, the
+// 8 lanes of a group reduce the 16 fields with a transposed butterfly (14 shuffles, each lane
+// ends with 2 fields), groups meet in shared memory, and one global atomic per (tile, splat,
+// field) leaves the block.
 #pragma once
 
 #include "kernels.cuh"
 
 namespace ss {
+
+constexpr int kSaccStride = kGradFields + 1;  // padded rows: groups on different splats hit different banks
 
 __device__ __forceinline__ int find_target(const TargetCam* tc, int n_targets, int tile) {
   int lo = 0, hi = n_targets - 1;
@@ -28,6 +33,33 @@ __device__ __forceinline__ int find_target(const TargetCam* tc, int n_targets, i
     if (tc[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Transposed reduction of 16 values over the 8 lanes of a group: lane gl of the group ends
+// with the group sums of fields 2 gl and 2 gl + 1 (in v[0], v[1]).
+__device__ __forceinline__ void group_reduce16(float v[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool up = lane & 4;
+    const float send = up ? v[i] : v[i + 8];
+    const float keep = up ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool up = lane & 2;
+    const float send = up ? v[i] : v[i + 4];
+    const float keep = up ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool up = lane & 1;
+    const float send = up ? v[i] : v[i + 2];
+    const float keep = up ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+  }
 }
 
 // Transposed warp reduction of 16 values: lanes 2f and 2f + 1 end with the warp sum of field f.
@@ -79,42 +111,56 @@ __device__ __forceinline__ bool next_item(const RasterParams& p, unsigned int* c
   return true;
 }
 
-// Geometry of one block's work item.
-struct TileGeom {
-  int t;             // target
-  int px;            // this lane's pixel column
-  int py0;           // this lane's first pixel row (rows py0 + 4 k)
-  float xa, xb, ya, yb;  // the warp block's pixel-centre rectangle
+// Pixels of this lane and the rectangle of its group's 4 x 4 sub-block.
+struct LaneGeom {
+  int px;                // pixel column
+  int py0;               // first pixel row; the second is py0 + 2
+  float xa, xb, ya, yb;  // the sub-block's pixel-centre rectangle
 };
 
-template <int TW, int TH, int PPT>
-__device__ __forceinline__ TileGeom tile_geom(const TargetCam& cam, int tile, int t) {
-  constexpr int WBH = 4 * PPT;
+template <int TW, int TH>
+__device__ __forceinline__ LaneGeom lane_geom(const TargetCam& cam, int tile) {
   constexpr int WBX = TW / 8;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane >> 3, gl = lane & 7;
   const int local = tile - cam.tile_base;
   const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
-  const int bx = tx * TW + (warp % WBX) * 8;
-  const int by = ty * TH + (warp / WBX) * WBH;
-  TileGeom g;
-  g.t = t;
-  g.px = bx + (lane & 7);
-  g.py0 = by + (lane >> 3);
-  g.xa = (float)bx + 0.5f;
-  g.xb = (float)bx + 7.5f;
-  g.ya = (float)by + 0.5f;
-  g.yb = (float)(by + WBH - 1) + 0.5f;
+  const int sbx = tx * TW + (warp % WBX) * 8 + (grp & 1) * 4;
+  const int sby = ty * TH + (warp / WBX) * 8 + (grp >> 1) * 4;
+  LaneGeom g;
+  g.px = sbx + (gl & 3);
+  g.py0 = sby + (gl >> 2);
+  g.xa = (float)sbx + 0.5f;
+  g.xb = (float)sbx + 3.5f;
+  g.ya = (float)sby + 0.5f;
+  g.yb = (float)sby + 3.5f;
   return g;
+}
+
+// The 32 bits of this lane's group: which of the chunk's staged splats [c0, c0 + 32) can reach
+// the group's sub-block (bit b <-> splat c0 + b).  Every lane tests 4 splats.
+__device__ __forceinline__ uint32_t group_mask(const float4 (*sg)[3], int c0, int nb, const LaneGeom& lg,
+                                               const CullConsts& cc) {
+  const int lane = threadIdx.x & 31;
+  const int grp = lane >> 3, gl = lane & 7;
+  uint32_t m = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = c0 + gl + 8 * i;
+    const bool keep = j < nb && may_touch(sg[j][0], sg[j][1], sg[j][2], lg.xa, lg.xb, lg.ya, lg.yb, cc);
+    const uint32_t b = __ballot_sync(0xffffffffu, keep);
+    m |= ((b >> (8 * grp)) & 0xffu) << (8 * i);
+  }
+  return m;
 }
 
 // ------------------------------------------------------------------------------------------
 // K3 forward
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH, int PPT, int BATCH, bool PERSIST>
-__global__ void __launch_bounds__(TW * TH / PPT) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
-  constexpr int NT = TW * TH / PPT;
-  static_assert(TW % 8 == 0 && TH % (4 * PPT) == 0, "tile must be a whole number of warp blocks");
-  static_assert((TW / 8) * (TH / (4 * PPT)) * 32 == NT, "one warp per warp block");
+template <int TW, int TH, int BATCH, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH / 2) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
+  constexpr int NT = TW * TH / 2;
+  static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are whole 8 x 8 warp blocks");
   __shared__ float4 sg[BATCH][3];
   __shared__ float4 sf[BATCH][2];
   __shared__ int s_item;
@@ -127,22 +173,22 @@ __global__ void __launch_bounds__(TW * TH / PPT) raster_fwd_kernel(const __grid_
     if (!next_item<PERSIST>(p, &p.status->work_fwd, tile, s_item)) break;
     const int t = find_target(p.tcams, p.n_targets, tile);
     const TargetCam& cam = p.tcams[t];
-    const TileGeom tg = tile_geom<TW, TH, PPT>(cam, tile, t);
+    const LaneGeom lg = lane_geom<TW, TH>(cam, tile);
     const bool sun = cam.sun != 0;
-    const float x = (float)tg.px + 0.5f;
+    const float x = (float)lg.px + 0.5f;
     const uint2 range = p.ranges[tile];
     const int64_t recbase = (int64_t)t * p.n_pad;
 
-    float T[PPT], D[PPT], A0[PPT], A1[PPT], A2[PPT], N0[PPT], N1[PPT], N2[PPT], y[PPT];
-    uint32_t last[PPT];
-    bool done[PPT];
+    float T[2], D[2], A0[2], A1[2], A2[2], N0[2], N1[2], N2[2], y[2];
+    uint32_t last[2];
+    bool done[2];
     uint32_t walked = 0;  // contributing pairs, the stopping one included
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
+    for (int k = 0; k < 2; ++k) {
       T[k] = 1.0f; D[k] = A0[k] = A1[k] = A2[k] = N0[k] = N1[k] = N2[k] = 0.0f;
-      y[k] = (float)(tg.py0 + 4 * k) + 0.5f;
+      y[k] = (float)(lg.py0 + 2 * k) + 0.5f;
       last[k] = range.x;
-      done[k] = !(tg.px < cam.W && tg.py0 + 4 * k < cam.H);
+      done[k] = !(lg.px < cam.W && lg.py0 + 2 * k < cam.H);
     }
     for (uint32_t b0 = range.x; b0 < range.y; b0 += BATCH) {
       const int nb = min((int)(range.y - b0), BATCH);
@@ -157,24 +203,18 @@ __global__ void __launch_bounds__(TW * TH / PPT) raster_fwd_kernel(const __grid_
         sf[i][0] = f[0];
         if (!sun) sf[i][1] = f[1];
       }
-      bool all_done = true;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) all_done &= done[k];
+      const bool all_done = done[0] && done[1];
       if (__syncthreads_and(all_done)) break;
-      const int nch = (nb + 31) >> 5;
-      // one copy of the walk body: the chunk loop stays rolled
 #pragma unroll 1
-      for (int c = 0; c < nch; ++c) {
-        const int jl = c * 32 + lane;
-        const bool keep = jl < nb && may_touch(sg[jl][0], sg[jl][1], sg[jl][2], tg.xa, tg.xb, tg.ya, tg.yb, p.cull);
-        uint32_t m = __ballot_sync(0xffffffffu, keep);
+      for (int c0 = 0; c0 < nb; c0 += 32) {
+        uint32_t m = group_mask(sg, c0, nb, lg, p.cull);
         if (all_done) continue;
         while (m) {
-          const int j = c * 32 + (__ffs(m) - 1);
+          const int j = c0 + __ffs(m) - 1;
           m &= m - 1;
           const float4 g0 = sg[j][0], g1 = sg[j][1], g2 = sg[j][2];
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) {
+          for (int k = 0; k < 2; ++k) {
             if (done[k]) continue;
             const PairEval e = eval_pair(g0, g1, g2, x, y[k], p.k);
             if (!e.contrib) continue;
@@ -210,10 +250,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) raster_fwd_kernel(const __grid_
       for (int i = 0; i < 12; ++i) C[i] = p.color[cam.cam * 12 + i];
     }
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const int py = tg.py0 + 4 * k;
-      if (!(tg.px < cam.W && py < cam.H)) continue;
-      const int64_t pix = (int64_t)py * cam.W + tg.px;
+    for (int k = 0; k < 2; ++k) {
+      const int py = lg.py0 + 2 * k;
+      if (!(lg.px < cam.W && py < cam.H)) continue;
+      const int64_t pix = (int64_t)py * cam.W + lg.px;
       if (io.rgb) {
         io.rgb[pix] = C[0] * A0[k] + C[1] * A1[k] + C[2] * A2[k] + C[3];
         io.rgb[hw + pix] = C[4] * A0[k] + C[5] * A1[k] + C[6] * A2[k] + C[7];
@@ -238,19 +278,19 @@ __global__ void __launch_bounds__(TW * TH / PPT) raster_fwd_kernel(const __grid_
 // ------------------------------------------------------------------------------------------
 // K4 backward
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH, int PPT, int BATCH, bool PERSIST>
-__global__ void __launch_bounds__(TW * TH / PPT) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
-  constexpr int NT = TW * TH / PPT;
+template <int TW, int TH, int BATCH, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
+  constexpr int NT = TW * TH / 2;
   constexpr int NW = NT / 32;
-  static_assert(TW % 8 == 0 && TH % (4 * PPT) == 0, "tile must be a whole number of warp blocks");
+  static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are whole 8 x 8 warp blocks");
   __shared__ float4 sg[BATCH][3];
   __shared__ float4 sf[BATCH][2];
   __shared__ uint32_t sk[BATCH];
-  __shared__ float sacc[BATCH][kGradFields];
+  __shared__ float sacc[BATCH][kSaccStride];
   __shared__ float scol[NW][16];
   __shared__ int s_item;
   __shared__ unsigned int s_hi;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gl = lane & 7;
   int tile;
   bool first = true;
   while (true) {
@@ -259,24 +299,24 @@ __global__ void __launch_bounds__(TW * TH / PPT) raster_bwd_kernel(const __grid_
     if (!next_item<PERSIST>(p, &p.status->work_bwd, tile, s_item)) break;
     const int t = find_target(p.tcams, p.n_targets, tile);
     const TargetCam& cam = p.tcams[t];
-    const TileGeom tg = tile_geom<TW, TH, PPT>(cam, tile, t);
+    const LaneGeom lg = lane_geom<TW, TH>(cam, tile);
     const bool sun = cam.sun != 0;
-    const float x = (float)tg.px + 0.5f;
+    const float x = (float)lg.px + 0.5f;
     const uint2 range = p.ranges[tile];
     const int64_t recbase = (int64_t)t * p.n_pad;
     const TargetIO io = p.io[t];
     const int64_t hw = (int64_t)cam.W * cam.H;
     const float* Cm = p.color ? p.color + cam.cam * 12 : nullptr;
 
-    float T[PPT], Tfin[PPT], y[PPT], Sg[PPT], gD[PPT], gAl[PPT];
-    float gA[PPT][3], gN[PPT][3], gR[PPT][3], Aacc[PPT][3];
-    uint32_t lastp[PPT];
+    float T[2], Tfin[2], y[2], Sg[2], gD[2], gAl[2];
+    float gA[2][3], gN[2][3], gR[2][3], Aacc[2][3];
+    uint32_t lastp[2];
     if (tid == 0) s_hi = range.x;
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const int py = tg.py0 + 4 * k;
-      const bool inside = tg.px < cam.W && py < cam.H;
+    for (int k = 0; k < 2; ++k) {
+      const int py = lg.py0 + 2 * k;
+      const bool inside = lg.px < cam.W && py < cam.H;
       y[k] = (float)py + 0.5f;
       T[k] = Tfin[k] = 1.0f;
       Sg[k] = gD[k] = gAl[k] = 0.0f;
@@ -284,7 +324,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) raster_bwd_kernel(const __grid_
 #pragma unroll
       for (int c = 0; c < 3; ++c) gA[k][c] = gN[k][c] = gR[k][c] = Aacc[k][c] = 0.0f;
       if (inside) {
-        const int64_t pix = (int64_t)py * cam.W + tg.px;
+        const int64_t pix = (int64_t)py * cam.W + lg.px;
         T[k] = io.T_final[pix];
         Tfin[k] = T[k];
         // the saved end of the walk, clamped to this tile's list
@@ -330,94 +370,101 @@ __global__ void __launch_bounds__(TW * TH / PPT) raster_bwd_kernel(const __grid_
         sf[i][0] = f[0];
         if (!sun) sf[i][1] = f[1];
       }
-      for (int i = tid; i < nb * kGradFields; i += NT) (&sacc[0][0])[i] = 0.0f;
+      for (int i = tid; i < nb * kSaccStride; i += NT) (&sacc[0][0])[i] = 0.0f;
       __syncthreads();
-      const int nch = (nb + 31) >> 5;
-      // reverse list order, one copy of the walk body: the chunk loop stays rolled
+      // chunks in reverse list order; within a chunk each group walks its own splats backwards
 #pragma unroll 1
-      for (int c = nch - 1; c >= 0; --c) {
-        const int jl = c * 32 + lane;
-        const bool keep = jl < nb && may_touch(sg[jl][0], sg[jl][1], sg[jl][2], tg.xa, tg.xb, tg.ya, tg.yb, p.cull);
-        uint32_t m = __ballot_sync(0xffffffffu, keep);
-        while (m) {
-          const int bit = 31 - __clz(m);
-          m &= ~(1u << bit);
-          const int jj = c * 32 + bit;
-          const uint32_t j = b0 + (uint32_t)jj;
-          const float4 g0 = sg[jj][0], g1 = sg[jj][1], g2 = sg[jj][2];
-          const bool deg = g2.y < 0.0f;
+      for (int c0 = ((nb - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+        uint32_t m = group_mask(sg, c0, nb, lg, p.cull);
+        while (__any_sync(0xffffffffu, m != 0u)) {
+          int jj = -1;
+          if (m) {
+            const int bit = 31 - __clz(m);
+            m &= ~(1u << bit);
+            jj = c0 + bit;
+          }
           float G[16];
 #pragma unroll
           for (int f = 0; f < 16; ++f) G[f] = 0.0f;
           bool any = false;
+          if (jj >= 0) {
+            const uint32_t j = b0 + (uint32_t)jj;
+            const float4 g0 = sg[jj][0], g1 = sg[jj][1], g2 = sg[jj][2];
+            const bool deg = g2.y < 0.0f;
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) {
-            if (j >= lastp[k]) continue;
-            const PairEval e = eval_pair(g0, g1, g2, x, y[k], p.k);
-            if (!e.contrib) continue;
-            any = true;
-            const float4 f0 = sf[jj][0];
-            const float om = 1.0f - e.alpha;
-            const float Ti = T[k] / om;
-            const float w = e.alpha * Ti;
-            const float z = g2.w + f0.x * e.u + f0.y * e.v;
-            float gf = gD[k] * z;
-            float4 f1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (!sun) {
-              f1 = sf[jj][1];
-              gf += gA[k][0] * f1.y + gA[k][1] * f1.z + gA[k][2] * f1.w + gN[k][0] * f0.z + gN[k][1] * f0.w +
-                    gN[k][2] * f1.x;
-            }
-            const float dal = Ti * (gf - Sg[k]) + gAl[k] * Tfin[k] / om;
-            Sg[k] = e.alpha * gf + om * Sg[k];
-            T[k] = Ti;
-            if (!sun) {
-              Aacc[k][0] += w * f1.y;
-              Aacc[k][1] += w * f1.z;
-              Aacc[k][2] += w * f1.w;
-              G[GF_R] += w * gA[k][0];
-              G[GF_G] += w * gA[k][1];
-              G[GF_B] += w * gA[k][2];
-              G[GF_NX] += w * gN[k][0];
-              G[GF_NY] += w * gN[k][1];
-              G[GF_NZ] += w * gN[k][2];
-            }
-            const float dz = w * gD[k];
-            G[GF_ZC] += dz;
-            G[GF_DZDU] += dz * e.u;
-            G[GF_DZDV] += dz * e.v;
-            float du = deg ? 0.0f : dz * f0.x;
-            float dv = deg ? 0.0f : dz * f0.y;
-            if (!e.clamped) {
-              const float dpw = dal * e.alpha;  // d / d ln(o G^)
-              G[GF_LNO] += dpw;
-              if (e.uwin) {
-                du -= dpw * e.u;
-                dv -= dpw * e.v;
-              } else {
-                G[GF_CX] += dpw * e.dx * two_inv2s2;
-                G[GF_CY] += dpw * e.dy * two_inv2s2;
+            for (int k = 0; k < 2; ++k) {
+              if (j >= lastp[k]) continue;
+              const PairEval e = eval_pair(g0, g1, g2, x, y[k], p.k);
+              if (!e.contrib) continue;
+              any = true;
+              const float4 f0 = sf[jj][0];
+              const float om = 1.0f - e.alpha;
+              const float rom = __fdividef(1.0f, om);  // om >= 1 - alpha_max
+              const float Ti = T[k] * rom;
+              const float w = e.alpha * Ti;
+              const float z = g2.w + f0.x * e.u + f0.y * e.v;
+              float gf = gD[k] * z;
+              float4 f1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+              if (!sun) {
+                f1 = sf[jj][1];
+                gf += gA[k][0] * f1.y + gA[k][1] * f1.z + gA[k][2] * f1.w + gN[k][0] * f0.z + gN[k][1] * f0.w +
+                      gN[k][2] * f1.x;
               }
-            }
-            if (!deg) {
-              G[GF_Q00] += du * e.dx;
-              G[GF_Q01] += du * e.dy;
-              G[GF_Q10] += dv * e.dx;
-              G[GF_Q11] += dv * e.dy;
-              G[GF_CX] -= g1.x * du + g1.z * dv;
-              G[GF_CY] -= g1.y * du + g1.w * dv;
+              const float dal = Ti * (gf - Sg[k]) + gAl[k] * Tfin[k] * rom;
+              Sg[k] = e.alpha * gf + om * Sg[k];
+              T[k] = Ti;
+              if (!sun) {
+                Aacc[k][0] += w * f1.y;
+                Aacc[k][1] += w * f1.z;
+                Aacc[k][2] += w * f1.w;
+                G[GF_R] += w * gA[k][0];
+                G[GF_G] += w * gA[k][1];
+                G[GF_B] += w * gA[k][2];
+                G[GF_NX] += w * gN[k][0];
+                G[GF_NY] += w * gN[k][1];
+                G[GF_NZ] += w * gN[k][2];
+              }
+              const float dz = w * gD[k];
+              G[GF_ZC] += dz;
+              G[GF_DZDU] += dz * e.u;
+              G[GF_DZDV] += dz * e.v;
+              float du = deg ? 0.0f : dz * f0.x;
+              float dv = deg ? 0.0f : dz * f0.y;
+              if (!e.clamped) {
+                const float dpw = dal * e.alpha;  // d / d ln(o G^)
+                G[GF_LNO] += dpw;
+                if (e.uwin) {
+                  du -= dpw * e.u;
+                  dv -= dpw * e.v;
+                } else {
+                  G[GF_CX] += dpw * e.dx * two_inv2s2;
+                  G[GF_CY] += dpw * e.dy * two_inv2s2;
+                }
+              }
+              if (!deg) {
+                G[GF_Q00] += du * e.dx;
+                G[GF_Q01] += du * e.dy;
+                G[GF_Q10] += dv * e.dx;
+                G[GF_Q11] += dv * e.dy;
+                G[GF_CX] -= g1.x * du + g1.z * dv;
+                G[GF_CY] -= g1.y * du + g1.w * dv;
+              }
             }
           }
           if (__any_sync(0xffffffffu, any)) {
-            const float r = warp_reduce16_transposed(G);
-            if (!(lane & 1) && r != 0.0f) atomicAdd(&sacc[jj][lane >> 1], r);
+            group_reduce16(G);
+            if (jj >= 0) {
+              if (G[0] != 0.0f) atomicAdd(&sacc[jj][2 * gl], G[0]);
+              if (G[1] != 0.0f) atomicAdd(&sacc[jj][2 * gl + 1], G[1]);
+            }
           }
         }
       }
       __syncthreads();
       for (int i = tid; i < nb * kGradFields; i += NT) {
-        const float v = (&sacc[0][0])[i];
-        if (v != 0.0f) atomicAdd(p.grad + (recbase + sk[i >> 4]) * kGradFields + (i & 15), v);
+        const int s = i >> 4, f = i & 15;
+        const float v = sacc[s][f];
+        if (v != 0.0f) atomicAdd(p.grad + (recbase + sk[s]) * kGradFields + f, v);
       }
       hi = b0;
     }
@@ -427,7 +474,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) raster_bwd_kernel(const __grid_
 #pragma unroll
       for (int a = 0; a < 16; ++a) cv[a] = 0.0f;
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
+      for (int k = 0; k < 2; ++k) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           cv[4 * a + 0] += gR[k][a] * Aacc[k][0];
@@ -452,66 +499,62 @@ __global__ void __launch_bounds__(TW * TH / PPT) raster_bwd_kernel(const __grid_
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH, int PPT, int BATCH>
+template <int TW, int TH, int BATCH>
 cudaError_t launch_fwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
-  constexpr int NT = TW * TH / PPT;
+  constexpr int NT = TW * TH / 2;
   if (p.total_tiles == 0) return cudaSuccess;
   if (persistent) {
     // resident blocks per SM, queried once (outside any later stream capture)
     static int per_sm = 0;
     if (per_sm == 0) {
       int v = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_fwd_kernel<TW, TH, PPT, BATCH, true>,
-                                                                    NT, 0);
+      cudaError_t e =
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_fwd_kernel<TW, TH, BATCH, true>, NT, 0);
       if (e != cudaSuccess) return e;
       per_sm = v < 1 ? 1 : v;
     }
     int grid = num_sms * per_sm;
     if (grid > p.total_tiles) grid = p.total_tiles;
     count_launch();
-    raster_fwd_kernel<TW, TH, PPT, BATCH, true><<<grid, NT, 0, st>>>(p);
+    raster_fwd_kernel<TW, TH, BATCH, true><<<grid, NT, 0, st>>>(p);
   } else {
     count_launch();
-    raster_fwd_kernel<TW, TH, PPT, BATCH, false><<<p.total_tiles, NT, 0, st>>>(p);
+    raster_fwd_kernel<TW, TH, BATCH, false><<<p.total_tiles, NT, 0, st>>>(p);
   }
   return cudaGetLastError();
 }
 
-template <int TW, int TH, int PPT, int BATCH>
+template <int TW, int TH, int BATCH>
 cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
-  constexpr int NT = TW * TH / PPT;
+  constexpr int NT = TW * TH / 2;
   if (p.total_tiles == 0) return cudaSuccess;
   if (persistent) {
     static int per_sm = 0;
     if (per_sm == 0) {
       int v = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_bwd_kernel<TW, TH, PPT, BATCH, true>,
-                                                                    NT, 0);
+      cudaError_t e =
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_bwd_kernel<TW, TH, BATCH, true>, NT, 0);
       if (e != cudaSuccess) return e;
       per_sm = v < 1 ? 1 : v;
     }
     int grid = num_sms * per_sm;
     if (grid > p.total_tiles) grid = p.total_tiles;
     count_launch();
-    raster_bwd_kernel<TW, TH, PPT, BATCH, true><<<grid, NT, 0, st>>>(p);
+    raster_bwd_kernel<TW, TH, BATCH, true><<<grid, NT, 0, st>>>(p);
   } else {
     count_launch();
-    raster_bwd_kernel<TW, TH, PPT, BATCH, false><<<p.total_tiles, NT, 0, st>>>(p);
+    raster_bwd_kernel<TW, TH, BATCH, false><<<p.total_tiles, NT, 0, st>>>(p);
   }
   return cudaGetLastError();
 }
 
-// Instantiates the launchers of one tile shape for every supported (pixels per thread, batch).
-#define SS_RASTER_DISPATCH(KIND, TW, TH, PPT_MAX)                                                         \
-  cudaError_t launch_raster_##KIND##_##TW##x##TH(const RasterParams& p, int ppt, int batch, bool persistent,\
-                                                 int num_sms, cudaStream_t st) {                          \
-    if (ppt == 2 && batch == 128) return launch_##KIND##_t<TW, TH, 2, 128>(p, persistent, num_sms, st);    \
-    if (ppt == 2 && batch == 256) return launch_##KIND##_t<TW, TH, 2, 256>(p, persistent, num_sms, st);    \
-    if (PPT_MAX >= 4 && ppt == 4 && batch == 128)                                                          \
-      return launch_##KIND##_t<TW, TH, (PPT_MAX >= 4 ? 4 : 2), 128>(p, persistent, num_sms, st);          \
-    if (PPT_MAX >= 4 && ppt == 4 && batch == 256)                                                          \
-      return launch_##KIND##_t<TW, TH, (PPT_MAX >= 4 ? 4 : 2), 256>(p, persistent, num_sms, st);          \
-    return cudaErrorInvalidValue;                                                                          \
+// Instantiates the launchers of one tile shape for both batch sizes.
+#define SS_RASTER_DISPATCH(KIND, TW, TH)                                                                    \
+  cudaError_t launch_raster_##KIND##_##TW##x##TH(const RasterParams& p, int batch, bool persistent,        \
+                                                 int num_sms, cudaStream_t st) {                            \
+    if (batch == 128) return launch_##KIND##_t<TW, TH, 128>(p, persistent, num_sms, st);                    \
+    if (batch == 256) return launch_##KIND##_t<TW, TH, 256>(p, persistent, num_sms, st);                    \
+    return cudaErrorInvalidValue;                                                                            \
   }
 
 }  // namespace ss

@@ -155,15 +155,13 @@ def test_bf16_backward_parity():
     grad_close(d_dF[0].cpu().numpy().astype(np.float64), ref["dF"], name="dF")
 
 
-@pytest.mark.parametrize("tile,batch,persistent,ppt", [((32, 8), 256, 0, 2), ((8, 32), 256, 0, 4),
-                                                       ((16, 16), 128, 0, 4), ((16, 16), 128, 1, 2),
-                                                       ((32, 8), 128, 1, 2), ((8, 32), 128, 1, 2)])
-def test_tile_shape_and_schedule_do_not_change_outputs(tile, batch, persistent, ppt):
+@pytest.mark.parametrize("tile,batch,persistent", [((32, 8), 256, 0), ((8, 32), 256, 0), ((16, 16), 128, 0),
+                                                   ((16, 16), 128, 1), ((32, 8), 128, 1), ((8, 32), 128, 1)])
+def test_tile_shape_and_schedule_do_not_change_outputs(tile, batch, persistent):
     scene = ragged_scene(seed=2)
     ds = DeviceScene(scene)
     _, ref = run_forward(ds, passes=3)
-    opts = L.default_opts(tile_w=tile[0], tile_h=tile[1], batch=batch, persistent=persistent,
-                          pixels_per_thread=ppt)
+    opts = L.default_opts(tile_w=tile[0], tile_h=tile[1], batch=batch, persistent=persistent)
     _, out = run_forward(ds, passes=3, opts=opts)
     for i in range(2):
         for k in ("rgb", "depth", "normal", "alpha", "T_final"):
