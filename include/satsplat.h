@@ -265,6 +265,33 @@ ss_status ss_frame_status(const void* ws, size_t ws_bytes, int64_t* needed, int6
  * (e.g. 1030 for sm_103a); a test hook to check the build.  Host only. */
 int32_t ss_device_info(int32_t* num_sms, int32_t* arch);
 
+/* Allocation-free forward render of ONE main view (no counterpart in the paper: a
+ * deployment aid).  Some callers cannot call cudaMalloc: code running inside a CUDA
+ * stream capture, where an allocation would break the capture; host applications that
+ * reserve their device memory once at start-up (a real-time viewer, an inference
+ * service under a fixed memory budget); plug-ins handed a stream but no allocator.
+ * This call needs no caller workspace: it runs ss_project_splats, ss_bin_and_sort and
+ * ss_rasterize_fwd for `cam` (n_cams = 1, SS_PASS_MAIN) on a static device array of
+ * ss_noalloc_scratch_bytes() bytes (64 MiB) inside this library, which every GPU that
+ * loads the library holds until the process exits.  It calls no allocating routine.
+ *   splats, dF (DEVICE [1][2][4] or NULL), color (DEVICE [1][3][4] or NULL), opts, io
+ *     (HOST array of 1 ss_target_io): as for the calls above.
+ *   needed: HOST out (may be NULL): intersections the view needed.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  The call
+ * synchronises `stream` to read the intersection count.  Every call shares the array and
+ * keeps the last call's contents (the status block and tile ranges are cleared on each
+ * call); calls that overlap on the GPU race on it.
+ * Errors: SS_ERR_INVALID_ARG when the splats (or the view's intersection lists) cannot fit
+ * the array, or for bad arguments; SS_ERR_CAPACITY when the lists outgrow the capacity
+ * left in the array (nothing is rasterized); SS_ERR_CUDA. */
+ss_status ss_render_fwd_noalloc(const ss_splats* splats, const ss_camera* cam, const float* dF,
+                                const float* color, const ss_raster_opts* opts, const ss_target_io* io,
+                                int64_t* needed, ss_stream_t stream);
+
+/* Size in bytes of the static scratch array used by ss_render_fwd_noalloc.  Never fails. */
+size_t ss_noalloc_scratch_bytes(void);
+
 /* Number of kernels this library has launched, or recorded into a CUDA graph under
  * stream capture, in this process (a host-side diagnostic counter; the paper has no
  * counterpart).  Host only; never fails. */

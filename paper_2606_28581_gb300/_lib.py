@@ -56,7 +56,8 @@ class ss_splat_grads(ctypes.Structure):
 
 EXPORTS = ["ss_default_opts", "ss_status_string", "ss_workspace_size", "ss_project_splats",
            "ss_bin_and_sort", "ss_rasterize_fwd", "ss_rasterize_bwd", "ss_project_bwd", "ss_shadow_depth",
-           "ss_frame_status", "ss_device_info", "ss_kernel_launches"]
+           "ss_frame_status", "ss_device_info", "ss_kernel_launches", "ss_render_fwd_noalloc",
+           "ss_noalloc_scratch_bytes"]
 
 _lock = threading.Lock()
 _lib = None
@@ -97,10 +98,14 @@ def load(path: Optional[str] = None):
                                       ctypes.POINTER(I32), P]
         L.ss_device_info.argtypes = [ctypes.POINTER(I32), ctypes.POINTER(I32)]
         L.ss_device_info.restype = I32
+        L.ss_render_fwd_noalloc.argtypes = [PS, PC, P, P, PO, PIO, ctypes.POINTER(I64), P]
+        L.ss_noalloc_scratch_bytes.argtypes = []
+        L.ss_noalloc_scratch_bytes.restype = SZ
         L.ss_kernel_launches.argtypes = []
         L.ss_kernel_launches.restype = I64
         for name in EXPORTS:
-            if name not in ("ss_default_opts", "ss_status_string", "ss_device_info", "ss_kernel_launches"):
+            if name not in ("ss_default_opts", "ss_status_string", "ss_device_info", "ss_kernel_launches",
+                            "ss_noalloc_scratch_bytes"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -234,6 +239,20 @@ def frame_status(ws, ws_bytes, stream=None):
     st = load().ss_frame_status(ptr(ws), int(ws_bytes), ctypes.byref(needed), ctypes.byref(nonfinite),
                                 ctypes.byref(walked), ctypes.byref(flags), stream_ptr(stream))
     return st, int(needed.value), int(nonfinite.value), int(walked.value), int(flags.value)
+
+
+def render_fwd_noalloc(splats, cam, dF, color, opts, io, stream=None):
+    """Allocation-free single-view forward (the library's static scratch).  Returns
+    (status, needed); SS_ERR_CAPACITY is returned, not raised."""
+    needed = ctypes.c_int64(-1)
+    st = load().ss_render_fwd_noalloc(ctypes.byref(splats), cam, ptr(dF), ptr(color), ctypes.byref(opts), io,
+                                      ctypes.byref(needed), stream_ptr(stream))
+    _check(st, "ss_render_fwd_noalloc", allow=(SS_ERR_CAPACITY,))
+    return st, int(needed.value)
+
+
+def noalloc_scratch_bytes() -> int:
+    return int(load().ss_noalloc_scratch_bytes())
 
 
 def kernel_launches() -> int:
