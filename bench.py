@@ -403,7 +403,7 @@ def run_ours(args, dist):
         frames, outs, ios = [], [], []
         for v, c in enumerate(cams):
             f = Frame([c], passes, L.default_opts())
-            f.project_and_bin(s32, dF[v:v + 1].contiguous(), sync=True)
+            f.project_and_bin(s32, dF[v:v + 1].contiguous(), color[v:v + 1].contiguous(), sync=True)
             f.ensure_workspace(s32, int(f.needed * 1.1) + 4096)
             o = Outputs(f.targets, f.device)
             u = [ups[v], ups[len(cams) + v]]
@@ -421,10 +421,10 @@ def run_ours(args, dist):
             for g in g32.values():
                 g.zero_()
             for v, f in enumerate(frames):
-                L.project_splats(s32, f.cams, 1, passes, dFv[v], f.opts, f.ws, f.ws_bytes, f.capacity)
+                L.project_splats(s32, f.cams, 1, passes, dFv[v], colv[v], f.opts, f.ws, f.ws_bytes, f.capacity)
                 L.bin_and_sort(s32, f.cams, 1, passes, f.opts, f.ws, f.ws_bytes, f.capacity, sync_needed=False)
-                L.rasterize_fwd(s32, f.cams, 1, passes, colv[v], f.opts, ios[v][0], f.ws, f.ws_bytes, f.capacity)
-                L.rasterize_bwd(s32, f.cams, 1, passes, dFv[v], colv[v], f.opts, ios[v][1], gs, ddF[v:v + 1],
+                L.rasterize_fwd(s32, f.cams, 1, passes, f.opts, ios[v][0], f.ws, f.ws_bytes, f.capacity)
+                L.rasterize_bwd(s32, f.cams, 1, passes, f.opts, ios[v][1], gs, ddF[v:v + 1],
                                 dcol[v:v + 1], f.ws, f.ws_bytes, f.capacity)
 
         for _ in range(max(1, min(args.warmup, 3))):

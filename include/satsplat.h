@@ -178,13 +178,18 @@ ss_status ss_workspace_size(const ss_splats* splats, const ss_camera* cams, int3
  * depth of the centre and its slopes along u and v, the normal flipped toward
  * the sensor, log-opacity, the conservative screen extent and the tile
  * rectangle, and zeroes the frame's gradient records of the visible pairs.
- * Splats with opacity < alpha_min are culled.
- *   dF: DEVICE [n_cams][2][4] fp32 camera deltas, or NULL (zero).
- *   ws: DEVICE workspace of ws_bytes >= ss_workspace_size(..., capacity).
+ * Splats with opacity < alpha_min are culled.  The colour correction of a main
+ * view (Sec. 3.1 Eq. image_formation) is applied here to the splat colour, since
+ * C (sum_i w_i rgb_i) = sum_i w_i (C rgb_i); its offset c is added per pixel by
+ * ss_rasterize_fwd.
+ *   dF:    DEVICE [n_cams][2][4] fp32 camera deltas, or NULL (zero).
+ *   color: DEVICE [n_cams][3][4] fp32 [C | c], or NULL (identity).
+ *   ws:    DEVICE workspace of ws_bytes >= ss_workspace_size(..., capacity).
  * Non-finite splat values are counted in the status block (ss_frame_status). */
 ss_status ss_project_splats(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
-                            int32_t passes, const float* dF, const ss_raster_opts* opts,
-                            void* ws, size_t ws_bytes, int64_t capacity, ss_stream_t stream);
+                            int32_t passes, const float* dF, const float* color,
+                            const ss_raster_opts* opts, void* ws, size_t ws_bytes, int64_t capacity,
+                            ss_stream_t stream);
 
 /* Tile binning and sorting (K2), Sec. 3.2 rasterization paragraph: one stable
  * radix sort of the splats by height (descending; ties by the smaller index)
@@ -204,13 +209,12 @@ ss_status ss_bin_and_sort(const ss_splats* splats, const ss_camera* cams, int32_
 /* Forward rasterization (K3), Sec. 3.2 Eq. rasterization and Sec. 3.1
  * Eq. image_formation (the C A + c part): per pixel, front to back over the
  * tile's list, alpha = min(alpha_max, o G^), contributing iff >= alpha_min,
- * stop before T would fall below t_min; outputs per ss_target_io.
- *   color: DEVICE [n_cams][3][4] fp32 [C | c], or NULL (identity).
+ * stop before T would fall below t_min; outputs per ss_target_io; the colour
+ * correction given to ss_project_splats completes rgb = C A + c.
  *   io:    HOST array of n_targets ss_target_io (T_final and last required). */
 ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
-                           int32_t passes, const float* color, const ss_raster_opts* opts,
-                           const ss_target_io* io, void* ws, size_t ws_bytes, int64_t capacity,
-                           ss_stream_t stream);
+                           int32_t passes, const ss_raster_opts* opts, const ss_target_io* io,
+                           void* ws, size_t ws_bytes, int64_t capacity, ss_stream_t stream);
 
 /* Backward (K4, then K5 unless grads is NULL): the adjoint of ss_rasterize_fwd
  * and ss_project_splats for the same frame.  Per pixel the walk runs in reverse
@@ -223,10 +227,11 @@ ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32
  *            ss_project_bwd for the same frame finishes the backward.
  *   d_dF:    DEVICE [n_cams][2][4] fp32, accumulated, or NULL (used with grads).
  *   d_color: DEVICE [n_cams][3][4] fp32, accumulated, or NULL: gradient of the
- *            colour correction, d C = sum g A^T, d c = sum g (Eq. image_formation). */
+ *            colour correction (Eq. image_formation): here d c = sum over pixels of
+ *            d(rgb_out); d C = sum g A^T is accumulated by the projection adjoint
+ *            (with grads, or ss_project_bwd) as sum_i H_i rgb_i^T, H_i = sum w_i g. */
 ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
-                           int32_t passes, const float* dF, const float* color,
-                           const ss_raster_opts* opts, const ss_target_io* io,
+                           int32_t passes, const ss_raster_opts* opts, const ss_target_io* io,
                            const ss_splat_grads* grads, float* d_dF, float* d_color, void* ws,
                            size_t ws_bytes, int64_t capacity, ss_stream_t stream);
 
@@ -234,11 +239,12 @@ ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32
  * per-(target, splat) records left by ss_rasterize_bwd(grads = NULL) through
  * Q = M^-1, M = B' R S', c = B' p + b', the depth row, the normal flip, the
  * quaternion normalisation and, for sun targets, the flattening along s; sums
- * over targets into `grads` (required, accumulated) and into d_dF (accumulated,
- * or NULL).  d(opacity) is taken through log(opacity). */
+ * over targets into `grads` (required, accumulated), into d_dF and into the 3x3
+ * block C of d_color (both accumulated, or NULL).  d(opacity) is taken through
+ * log(opacity). */
 ss_status ss_project_bwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams,
                          int32_t passes, const ss_raster_opts* opts, const ss_splat_grads* grads,
-                         float* d_dF, void* ws, size_t ws_bytes, int64_t capacity,
+                         float* d_dF, float* d_color, void* ws, size_t ws_bytes, int64_t capacity,
                          ss_stream_t stream);
 
 /* Sun-direction shadow depth (K6), Sec. 3.3 and Supp. A: project, bin and

@@ -88,11 +88,11 @@ def load(path: Optional[str] = None):
         L.ss_status_string.argtypes = [ctypes.c_int]
         L.ss_status_string.restype = ctypes.c_char_p
         L.ss_workspace_size.argtypes = [PS, PC, I32, I32, PO, I64, ctypes.POINTER(SZ)]
-        L.ss_project_splats.argtypes = [PS, PC, I32, I32, P, PO, P, SZ, I64, P]
+        L.ss_project_splats.argtypes = [PS, PC, I32, I32, P, P, PO, P, SZ, I64, P]
         L.ss_bin_and_sort.argtypes = [PS, PC, I32, I32, PO, P, SZ, I64, ctypes.POINTER(I64), P]
-        L.ss_rasterize_fwd.argtypes = [PS, PC, I32, I32, P, PO, PIO, P, SZ, I64, P]
-        L.ss_rasterize_bwd.argtypes = [PS, PC, I32, I32, P, P, PO, PIO, PG, P, P, P, SZ, I64, P]
-        L.ss_project_bwd.argtypes = [PS, PC, I32, I32, PO, PG, P, P, SZ, I64, P]
+        L.ss_rasterize_fwd.argtypes = [PS, PC, I32, I32, PO, PIO, P, SZ, I64, P]
+        L.ss_rasterize_bwd.argtypes = [PS, PC, I32, I32, PO, PIO, PG, P, P, P, SZ, I64, P]
+        L.ss_project_bwd.argtypes = [PS, PC, I32, I32, PO, PG, P, P, P, SZ, I64, P]
         L.ss_shadow_depth.argtypes = [PS, PC, I32, P, PO, PIO, P, SZ, I64, ctypes.POINTER(I64), P]
         L.ss_frame_status.argtypes = [P, SZ, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
                                       ctypes.POINTER(I32), P]
@@ -184,8 +184,8 @@ def workspace_size(splats, cams, n_cams, passes, opts, capacity) -> int:
     return int(out.value)
 
 
-def project_splats(splats, cams, n_cams, passes, dF, opts, ws, ws_bytes, capacity, stream=None):
-    return _check(load().ss_project_splats(ctypes.byref(splats), cams, n_cams, passes, ptr(dF),
+def project_splats(splats, cams, n_cams, passes, dF, color, opts, ws, ws_bytes, capacity, stream=None):
+    return _check(load().ss_project_splats(ctypes.byref(splats), cams, n_cams, passes, ptr(dF), ptr(color),
                                            ctypes.byref(opts), ptr(ws), int(ws_bytes), int(capacity),
                                            stream_ptr(stream)), "ss_project_splats")
 
@@ -202,26 +202,26 @@ def bin_and_sort(splats, cams, n_cams, passes, opts, ws, ws_bytes, capacity, syn
     return st, int(needed.value)
 
 
-def rasterize_fwd(splats, cams, n_cams, passes, color, opts, io, ws, ws_bytes, capacity, stream=None):
-    return _check(load().ss_rasterize_fwd(ctypes.byref(splats), cams, n_cams, passes, ptr(color),
+def rasterize_fwd(splats, cams, n_cams, passes, opts, io, ws, ws_bytes, capacity, stream=None):
+    return _check(load().ss_rasterize_fwd(ctypes.byref(splats), cams, n_cams, passes,
                                           ctypes.byref(opts), io, ptr(ws), int(ws_bytes), int(capacity),
                                           stream_ptr(stream)), "ss_rasterize_fwd")
 
 
-def rasterize_bwd(splats, cams, n_cams, passes, dF, color, opts, io, grads, d_dF, d_color, ws, ws_bytes,
+def rasterize_bwd(splats, cams, n_cams, passes, opts, io, grads, d_dF, d_color, ws, ws_bytes,
                   capacity, stream=None):
     """``grads`` None runs the per-pixel adjoint only (finish with project_bwd)."""
     g = None if grads is None else ctypes.byref(grads)
-    return _check(load().ss_rasterize_bwd(ctypes.byref(splats), cams, n_cams, passes, ptr(dF), ptr(color),
+    return _check(load().ss_rasterize_bwd(ctypes.byref(splats), cams, n_cams, passes,
                                           ctypes.byref(opts), io, g, ptr(d_dF),
                                           ptr(d_color), ptr(ws), int(ws_bytes), int(capacity),
                                           stream_ptr(stream)), "ss_rasterize_bwd")
 
 
-def project_bwd(splats, cams, n_cams, passes, opts, grads, d_dF, ws, ws_bytes, capacity, stream=None):
+def project_bwd(splats, cams, n_cams, passes, opts, grads, d_dF, d_color, ws, ws_bytes, capacity, stream=None):
     return _check(load().ss_project_bwd(ctypes.byref(splats), cams, n_cams, passes, ctypes.byref(opts),
-                                        ctypes.byref(grads), ptr(d_dF), ptr(ws), int(ws_bytes), int(capacity),
-                                        stream_ptr(stream)), "ss_project_bwd")
+                                        ctypes.byref(grads), ptr(d_dF), ptr(d_color), ptr(ws), int(ws_bytes),
+                                        int(capacity), stream_ptr(stream)), "ss_project_bwd")
 
 
 def shadow_depth(splats, cams, n_cams, dF, opts, io, ws, ws_bytes, capacity, sync_needed=True, stream=None):

@@ -55,7 +55,7 @@ class _RenderFn(torch.autograd.Function):
         splats = L.make_splats(*ctx.store, ctx.n)
         if getattr(frame, "_generation", 0) != ctx.generation:
             # the frame's workspace was reused by a later forward: rebuild this frame's lists
-            frame.project_and_bin(splats, ctx.dF)
+            frame.project_and_bin(splats, ctx.dF, ctx.color)
         up = []
         it = iter(gouts)
         c = lambda g: None if g is None else g.float().contiguous()
@@ -68,7 +68,7 @@ class _RenderFn(torch.autograd.Function):
         grads = zero_grads(ctx.n_pad, dev)
         d_dF = torch.zeros(frame.n_cams, 2, 4, device=dev) if ctx.has_dF else None
         d_color = torch.zeros(frame.n_cams, 3, 4, device=dev) if ctx.has_color else None
-        frame.backward(splats, ctx.out, up, grads, dF=ctx.dF, color=ctx.color, d_dF=d_dF, d_color=d_color)
+        frame.backward(splats, ctx.out, up, grads, d_dF=d_dF, d_color=d_color)
         n = ctx.n
         return (None, None, grads["means"][:, :n], grads["scales"][:, :n], grads["quats"][:, :n],
                 grads["opacity"][0, :n], grads["rgb"][:, :n], d_dF, d_color)

@@ -63,14 +63,15 @@ class BatchedStep:
         self._g = grads_struct(self.grads)
         self.graph = None
         # size the intersection capacity with one synchronised eager run
-        needed = self.frame.project_and_bin(self.splats, self.dF, sync=True)
+        needed = self.frame.project_and_bin(self.splats, self.dF, self.color, sync=True)
         cap = capacity if capacity is not None else max(1 << 16, int(needed * capacity_slack) + 4096)
         self.frame.ensure_workspace(self.splats, cap)
 
     # ------------------------------------------------------------------ phases
     def project(self, stream=None):
         f = self.frame
-        L.project_splats(self.splats, f.cams, f.n_cams, f.passes, self.dF, f.opts, f.ws, f.ws_bytes, f.capacity,
+        L.project_splats(self.splats, f.cams, f.n_cams, f.passes, self.dF, self.color, f.opts, f.ws, f.ws_bytes,
+                         f.capacity,
                          stream)
 
     def bin(self, stream=None):
@@ -80,17 +81,18 @@ class BatchedStep:
 
     def forward(self, stream=None):
         f = self.frame
-        L.rasterize_fwd(self.splats, f.cams, f.n_cams, f.passes, self.color, f.opts, self._io_f, f.ws, f.ws_bytes,
+        L.rasterize_fwd(self.splats, f.cams, f.n_cams, f.passes, f.opts, self._io_f, f.ws, f.ws_bytes,
                         f.capacity, stream)
 
     def backward_pixels(self, stream=None):
         f = self.frame
-        L.rasterize_bwd(self.splats, f.cams, f.n_cams, f.passes, None, self.color, f.opts, self._io_b, None, None,
+        L.rasterize_bwd(self.splats, f.cams, f.n_cams, f.passes, f.opts, self._io_b, None, None,
                         self.d_color, f.ws, f.ws_bytes, f.capacity, stream)
 
     def backward_project(self, stream=None):
         f = self.frame
-        L.project_bwd(self.splats, f.cams, f.n_cams, f.passes, f.opts, self._g, self.d_dF, f.ws, f.ws_bytes,
+        L.project_bwd(self.splats, f.cams, f.n_cams, f.passes, f.opts, self._g, self.d_dF, self.d_color, f.ws,
+                      f.ws_bytes,
                       f.capacity, stream)
 
     def zero_grads(self):

@@ -215,7 +215,7 @@ ProjectCommon common_of(const ss_splats* s, const Layout& L, void* ws) {
 }
 
 ss_status fill_raster(RasterParams& rp, const ss_splats* s, const Layout& L, const ss_raster_opts* o,
-                      const ss_target_io* io, const float* color, void* ws, bool bwd) {
+                      const ss_target_io* io, void* ws, bool bwd) {
   std::memset(&rp, 0, sizeof(rp));
   if (!io) return SS_ERR_INVALID_ARG;
   for (int t = 0; t < L.T; ++t) {
@@ -242,7 +242,6 @@ ss_status fill_raster(RasterParams& rp, const ss_splats* s, const Layout& L, con
   rp.items = nullptr;
   rp.status = at<StatusBlock>(ws, L.status);
   rp.grad = at<float>(ws, L.grad);
-  rp.color = color;
   rp.n_pad = s->n_pad;
   rp.n_targets = (int32_t)L.T;
   rp.total_tiles = (int32_t)L.total_tiles;
@@ -264,7 +263,7 @@ ss_status check_grads(const ss_splats* s, const ss_splat_grads* g) {
 }
 
 ss_status run_project_bwd(const ss_splats* splats, const Layout& L, const ss_raster_opts* opts,
-                          const ss_splat_grads* grads, float* d_dF, void* ws, cudaStream_t st) {
+                          const ss_splat_grads* grads, float* d_dF, float* d_color, void* ws, cudaStream_t st) {
   ProjectBwdParams pb;
   pb.c = common_of(splats, L, ws);
   pb.rect = at<uint4>(ws, L.rect);
@@ -276,6 +275,7 @@ ss_status run_project_bwd(const ss_splats* splats, const Layout& L, const ss_ras
   pb.g.rgb = grads->rgb;
   pb.g.n_pad = grads->n_pad;
   pb.d_dF = d_dF;
+  pb.d_color = d_color;
   pb.amin = opts->alpha_min;
   pb.det_eps = opts->det_eps;
   SS_CUDA_TRY(launch_project_bwd(pb, splats->dtype, st));
@@ -324,7 +324,8 @@ ss_status ss_workspace_size(const ss_splats* splats, const ss_camera* cams, int3
 }
 
 ss_status ss_project_splats(const ss_splats* splats, const ss_camera* cams, int32_t n_cams, int32_t passes,
-                            const float* dF, const ss_raster_opts* opts, void* ws, size_t ws_bytes,
+                            const float* dF, const float* color, const ss_raster_opts* opts, void* ws,
+                            size_t ws_bytes,
                             int64_t capacity, ss_stream_t stream) {
   Layout L;
   ss_status e = make_layout(splats, cams, n_cams, passes, opts, capacity, &L);
@@ -344,6 +345,7 @@ ss_status ss_project_splats(const ss_splats* splats, const ss_camera* cams, int3
   for (int t = 0; t < L.T; ++t) ap.tg[t] = L.tg[t];
   ap.n_targets = (int32_t)L.T;
   ap.dF = dF;
+  ap.color = color;
   ap.out = at<TargetCam>(ws, L.tcams);
   SS_CUDA_TRY(launch_assemble(ap, st));
   ProjectParams pp;
@@ -425,14 +427,14 @@ ss_status ss_bin_and_sort(const ss_splats* splats, const ss_camera* cams, int32_
 }
 
 ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams, int32_t passes,
-                           const float* color, const ss_raster_opts* opts, const ss_target_io* io, void* ws,
+                           const ss_raster_opts* opts, const ss_target_io* io, void* ws,
                            size_t ws_bytes, int64_t capacity, ss_stream_t stream) {
   Layout L;
   ss_status e = make_layout(splats, cams, n_cams, passes, opts, capacity, &L);
   if (e != SS_OK) return e;
   if ((e = check_ws(L, ws, ws_bytes)) != SS_OK) return e;
   RasterParams* rp = new RasterParams;
-  e = fill_raster(*rp, splats, L, opts, io, color, ws, false);
+  e = fill_raster(*rp, splats, L, opts, io, ws, false);
   if (e != SS_OK) {
     delete rp;
     return e;
@@ -449,17 +451,16 @@ ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32
 }
 
 ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams, int32_t passes,
-                           const float* dF, const float* color, const ss_raster_opts* opts,
-                           const ss_target_io* io, const ss_splat_grads* grads, float* d_dF, float* d_color,
+                           const ss_raster_opts* opts, const ss_target_io* io, const ss_splat_grads* grads,
+                           float* d_dF, float* d_color,
                            void* ws, size_t ws_bytes, int64_t capacity, ss_stream_t stream) {
-  (void)dF;
   Layout L;
   ss_status e = make_layout(splats, cams, n_cams, passes, opts, capacity, &L);
   if (e != SS_OK) return e;
   if ((e = check_ws(L, ws, ws_bytes)) != SS_OK) return e;
   if (grads && (e = check_grads(splats, grads)) != SS_OK) return e;
   RasterParams* rp = new RasterParams;
-  e = fill_raster(*rp, splats, L, opts, io, color, ws, true);
+  e = fill_raster(*rp, splats, L, opts, io, ws, true);
   if (e != SS_OK) {
     delete rp;
     return e;
@@ -475,28 +476,30 @@ ss_status ss_rasterize_bwd(const ss_splats* splats, const ss_camera* cams, int32
   delete rp;
   if (ce != cudaSuccess) return SS_ERR_CUDA;
   if (!grads) return SS_OK;
-  return run_project_bwd(splats, L, opts, grads, d_dF, ws, st);
+  return run_project_bwd(splats, L, opts, grads, d_dF, d_color, ws, st);
 }
 
 ss_status ss_project_bwd(const ss_splats* splats, const ss_camera* cams, int32_t n_cams, int32_t passes,
-                         const ss_raster_opts* opts, const ss_splat_grads* grads, float* d_dF, void* ws,
+                         const ss_raster_opts* opts, const ss_splat_grads* grads, float* d_dF, float* d_color,
+                         void* ws,
                          size_t ws_bytes, int64_t capacity, ss_stream_t stream) {
   Layout L;
   ss_status e = make_layout(splats, cams, n_cams, passes, opts, capacity, &L);
   if (e != SS_OK) return e;
   if ((e = check_ws(L, ws, ws_bytes)) != SS_OK) return e;
   if ((e = check_grads(splats, grads)) != SS_OK) return e;
-  return run_project_bwd(splats, L, opts, grads, d_dF, ws, reinterpret_cast<cudaStream_t>(stream));
+  return run_project_bwd(splats, L, opts, grads, d_dF, d_color, ws, reinterpret_cast<cudaStream_t>(stream));
 }
 
 ss_status ss_shadow_depth(const ss_splats* splats, const ss_camera* cams, int32_t n_cams, const float* dF,
                           const ss_raster_opts* opts, const ss_target_io* io, void* ws, size_t ws_bytes,
                           int64_t capacity, int64_t* needed, ss_stream_t stream) {
-  ss_status e = ss_project_splats(splats, cams, n_cams, SS_PASS_SUN, dF, opts, ws, ws_bytes, capacity, stream);
+  ss_status e =
+      ss_project_splats(splats, cams, n_cams, SS_PASS_SUN, dF, nullptr, opts, ws, ws_bytes, capacity, stream);
   if (e != SS_OK) return e;
   e = ss_bin_and_sort(splats, cams, n_cams, SS_PASS_SUN, opts, ws, ws_bytes, capacity, needed, stream);
   if (e != SS_OK) return e;
-  return ss_rasterize_fwd(splats, cams, n_cams, SS_PASS_SUN, nullptr, opts, io, ws, ws_bytes, capacity, stream);
+  return ss_rasterize_fwd(splats, cams, n_cams, SS_PASS_SUN, opts, io, ws, ws_bytes, capacity, stream);
 }
 
 ss_status ss_frame_status(const void* ws, size_t ws_bytes, int64_t* needed, int64_t* nonfinite, int64_t* walked,

@@ -62,6 +62,7 @@ struct __align__(16) TargetCam {
   int32_t W, H, tiles_x, tiles_y;
   int32_t tile_base;
   int32_t cam, sun, pad;
+  float C[12];      // colour correction [C | c] row-major (identity for sun views)
 };
 
 // Host-known static part of a target.
@@ -170,17 +171,51 @@ __device__ __forceinline__ PairEval eval_pair(const float4 g0, const float4 g1, 
   }
   e.uwin = pu >= ps;
   const float p = e.uwin ? pu : ps;
-  const float lp = __fadd_rn(p, g2.x);  // ln(o G^)
-  e.clamped = false;
-  e.contrib = false;
-  e.alpha = 0.0f;
-  if (lp >= k.ln_amin_slack) {
-    const float og = __expf(lp);
-    e.clamped = og > k.amax;
-    e.alpha = e.clamped ? k.amax : og;
-    e.contrib = e.alpha >= k.amin;
-  }
+  const float lp = __fadd_rn(p, g2.x);  // ln(o G^) <= ln(o) <= 0
+  // branch free (the forward and backward evaluate both pixels of a lane side by side); below
+  // ln(alpha_min) - 1e-3 the exponential is below alpha_min, so the decisions are those of
+  // skipping it there
+  const float og = __expf(fmaxf(lp, k.ln_amin_slack - 4.0f));
+  e.clamped = og > k.amax;
+  e.alpha = e.clamped ? k.amax : og;
+  e.contrib = (lp >= k.ln_amin_slack) && (e.alpha >= k.amin);
   return e;
+}
+
+// ---------------------------------------------------------------- warp reductions
+// Transposed warp reduction of 16 values: lanes 2f and 2f + 1 end with the warp sum of field f
+// (16 shuffles instead of 80 for 16 separate reductions).
+__device__ __forceinline__ float warp_reduce16_transposed(float v[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool up = lane & 16;
+    const float send = up ? v[i] : v[i + 8];
+    const float keep = up ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool up = lane & 8;
+    const float send = up ? v[i] : v[i + 4];
+    const float keep = up ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool up = lane & 4;
+    const float send = up ? v[i] : v[i + 2];
+    const float keep = up ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool up = lane & 2;
+    const float send = up ? v[0] : v[1];
+    const float keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
 }
 
 // ---------------------------------------------------------------- footprint culling

@@ -9,7 +9,8 @@ struct AssembleParams {
   CamRaw cams[kMaxCams];
   TargetStatic tg[kMaxTargets];
   int32_t n_targets;
-  const float* dF;  // [n_cams][8] or null
+  const float* dF;     // [n_cams][8] or null
+  const float* color;  // [n_cams][12] or null (identity)
   TargetCam* out;
 };
 
@@ -51,6 +52,7 @@ struct ProjectBwdParams {
   const float* grad;  // [T][n_pad][16]
   GradOut g;
   float* d_dF;        // [n_cams][8] or null
+  float* d_color;     // [n_cams][12] or null: the 3x3 block C
   float amin, det_eps;
 };
 
@@ -79,8 +81,7 @@ struct RasterParams {
   const uint32_t* items;   // optional work order of global tile ids (persistent)
   StatusBlock* status;
   float* grad;             // [T][n_pad][16] (backward)
-  const float* color;      // [n_cams][12] or null
-  float* d_color;          // [n_cams][12] or null
+  float* d_color;          // [n_cams][12] or null: the offset column c receives sum d(rgb_out)
   int64_t n_pad;
   int32_t n_targets, total_tiles;
   EvalConsts k;

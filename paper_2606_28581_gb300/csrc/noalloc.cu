@@ -67,13 +67,14 @@ ss_status ss_render_fwd_noalloc(const ss_splats* splats, const ss_camera* cam, c
   void* ws = nullptr;
   if ((e = scratch_for_current_device(&ws)) != SS_OK) return e;
   // projection clears the status block; binning clears the per-tile ranges
-  e = ss_project_splats(splats, cam, 1, SS_PASS_MAIN, dF, opts, ws, kNoAllocScratchBytes, capacity, stream);
+  e = ss_project_splats(splats, cam, 1, SS_PASS_MAIN, dF, color, opts, ws, kNoAllocScratchBytes, capacity,
+                        stream);
   if (e != SS_OK) return e;
   int64_t need = 0;
   e = ss_bin_and_sort(splats, cam, 1, SS_PASS_MAIN, opts, ws, kNoAllocScratchBytes, capacity, &need, stream);
   if (needed) *needed = need;
   if (e != SS_OK) return e;
-  return ss_rasterize_fwd(splats, cam, 1, SS_PASS_MAIN, color, opts, io, ws, kNoAllocScratchBytes, capacity,
+  return ss_rasterize_fwd(splats, cam, 1, SS_PASS_MAIN, opts, io, ws, kNoAllocScratchBytes, capacity,
                           stream);
 }
 

@@ -54,6 +54,12 @@ __global__ void assemble_kernel(AssembleParams p) {
   tc.cam = st.cam;
   tc.sun = st.sun;
   tc.pad = 0;
+  // colour correction [C | c] of main views (Sec. 3.1 Eq. image_formation); sun views carry none
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const float id = (i % 4 == i / 4) ? 1.0f : 0.0f;
+    tc.C[i] = (!st.sun && p.color) ? p.color[st.cam * 12 + i] : id;
+  }
   p.out[t] = tc;
 }
 
@@ -261,7 +267,11 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectParams p) {
           g[2] = g2;
           float4* f = p.feat + rec * 2;
           f[0] = make_float4(-s.su * s.R[2][0], -s.sv * s.R[2][1], sp.flip * s.R[0][2], sp.flip * s.R[1][2]);
-          f[1] = make_float4(sp.flip * s.R[2][2], s.rgb[0], s.rgb[1], s.rgb[2]);
+          // C (sum w rgb) = sum w (C rgb): main views composite the corrected splat colour
+          const float* C = cam.C;
+          f[1] = make_float4(sp.flip * s.R[2][2], C[0] * s.rgb[0] + C[1] * s.rgb[1] + C[2] * s.rgb[2],
+                             C[4] * s.rgb[0] + C[5] * s.rgb[1] + C[6] * s.rgb[2],
+                             C[8] * s.rgb[0] + C[9] * s.rgb[1] + C[10] * s.rgb[2]);
           float4* gz = p.grad + rec * 4;
           const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
           gz[0] = z4;
@@ -278,38 +288,10 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectParams p) {
 // ------------------------------------------------------------------------------------------
 // K5: chain the per-(target, splat) gradient records through the projection
 // ------------------------------------------------------------------------------------------
-// Transposed warp reduction of 8 values: lane l ends with the warp sum of field (l >> 2).
-__device__ __forceinline__ float warp_reduce8_transposed(float v[8]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const bool up = lane & 16;
-    float send = up ? v[i] : v[i + 4];
-    float keep = up ? v[i + 4] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool up = lane & 8;
-    float send = up ? v[i] : v[i + 2];
-    float keep = up ? v[i + 2] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  {
-    const bool up = lane & 4;
-    float send = up ? v[0] : v[1];
-    float keep = up ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-  return v[0];
-}
-
 template <typename Tst>
 __global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdParams p) {
   __shared__ TargetCam scam[kMaxTargets];
-  __shared__ float red[8][8];
+  __shared__ float red[8][17];
   for (int t = threadIdx.x; t < p.c.n_targets; t += blockDim.x) scam[t] = p.c.tcams[t];
   __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -323,7 +305,9 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdParams p) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = 0; t < p.c.n_targets; ++t) {
     const TargetCam& cam = scam[t];
-    float dBp[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // d/d[B' | b'] of this target's camera
+    // per target: d/d[B' | b'] (8) and d/dC of the colour correction's 3x3 block (9)
+    float dBp[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    float dC22 = 0.0f;
     const int64_t rec = (int64_t)t * np + k;
     bool live = false;
     if (alive) {
@@ -401,19 +385,43 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdParams p) {
       dR[1][2] += sp.flip * g[GF_NY];
       dR[2][2] += sp.flip * g[GF_NZ];
       dlno += g[GF_LNO];
-      drgb[0] += g[GF_R];
-      drgb[1] += g[GF_G];
-      drgb[2] += g[GF_B];
+      if (!cam.sun) {
+        // the record holds H = sum_px w d(rgb_out): the splat composited C rgb, so
+        // d rgb = C^T H and dC = H rgb^T (Sec. 3.1 Eq. image_formation)
+        const float H[3] = {g[GF_R], g[GF_G], g[GF_B]};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) drgb[j] += cam.C[j] * H[0] + cam.C[4 + j] * H[1] + cam.C[8 + j] * H[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            if (3 * i + j < 8) dBp[8 + 3 * i + j] = H[i] * s.rgb[j];
+          }
+        dC22 = H[2] * s.rgb[2];
+      }
     }
-    // camera-delta gradient of this target: block reduction, one atomic per field
-    if (p.d_dF != nullptr) {
-      const float tot = warp_reduce8_transposed(dBp);
-      if ((lane & 3) == 0) red[warp][lane >> 2] = tot;
+    // camera-delta and colour gradients of this target: block reduction, one atomic per field
+    const bool want_dF = p.d_dF != nullptr, want_dC = p.d_color != nullptr && !cam.sun;
+    if (want_dF || want_dC) {
+      const float tot = warp_reduce16_transposed(dBp);
+      float t22 = dC22;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t22 += __shfl_xor_sync(0xffffffffu, t22, o);
+      if (!(lane & 1)) red[warp][lane >> 1] = tot;
+      if (lane == 0) red[warp][16] = t22;
       __syncthreads();
-      if (threadIdx.x < 8) {
+      if (threadIdx.x < 17) {
         float acc = 0.0f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
-        if (acc != 0.0f) atomicAdd(p.d_dF + cam.cam * 8 + threadIdx.x, acc);
+        const int f = threadIdx.x;
+        if (acc != 0.0f) {
+          if (f < 8) {
+            if (want_dF) atomicAdd(p.d_dF + cam.cam * 8 + f, acc);
+          } else if (want_dC) {
+            const int ij = f - 8, i = ij / 3, j = ij % 3;  // dC[i][j], row-major [C | c]
+            atomicAdd(p.d_color + cam.cam * 12 + 4 * i + j, acc);
+          }
+        }
       }
       __syncthreads();
     }

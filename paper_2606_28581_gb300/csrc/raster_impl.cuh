@@ -62,40 +62,6 @@ __device__ __forceinline__ void group_reduce16(float v[16]) {
   }
 }
 
-// Transposed warp reduction of 16 values: lanes 2f and 2f + 1 end with the warp sum of field f.
-__device__ __forceinline__ float warp_reduce16_transposed(float v[16]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const bool up = lane & 16;
-    const float send = up ? v[i] : v[i + 8];
-    const float keep = up ? v[i + 8] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const bool up = lane & 8;
-    const float send = up ? v[i] : v[i + 4];
-    const float keep = up ? v[i + 4] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool up = lane & 4;
-    const float send = up ? v[i] : v[i + 2];
-    const float keep = up ? v[i + 2] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  {
-    const bool up = lane & 2;
-    const float send = up ? v[0] : v[1];
-    const float keep = up ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-  return v[0];
-}
-
 template <bool PERSIST>
 __device__ __forceinline__ bool next_item(const RasterParams& p, unsigned int* counter, int& tile, int& s_item) {
   if (!PERSIST) {
@@ -190,6 +156,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_fwd_kernel(const __grid_co
       last[k] = range.x;
       done[k] = !(lg.px < cam.W && lg.py0 + 2 * k < cam.H);
     }
+    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (uint32_t b0 = range.x; b0 < range.y; b0 += BATCH) {
       const int nb = min((int)(range.y - b0), BATCH);
       __syncthreads();
@@ -201,7 +168,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_fwd_kernel(const __grid_co
         sg[i][1] = g[1];
         sg[i][2] = g[2];
         sf[i][0] = f[0];
-        if (!sun) sf[i][1] = f[1];
+        sf[i][1] = sun ? zero4 : f[1];
       }
       const bool all_done = done[0] && done[1];
       if (__syncthreads_and(all_done)) break;
@@ -213,51 +180,48 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_fwd_kernel(const __grid_co
           const int j = c0 + __ffs(m) - 1;
           m &= m - 1;
           const float4 g0 = sg[j][0], g1 = sg[j][1], g2 = sg[j][2];
+          // both pixels side by side (independent chains)
+          const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
+          const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
+          const bool c0p = !done[0] && e0.contrib, c1p = !done[1] && e1.contrib;
+          if (!(c0p || c1p)) continue;
+          walked += (uint32_t)c0p + (uint32_t)c1p;
+          const float4 f0 = sf[j][0], f1 = sf[j][1];
+          const uint32_t pos = b0 + (uint32_t)j + 1u;
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
-            if (done[k]) continue;
-            const PairEval e = eval_pair(g0, g1, g2, x, y[k], p.k);
-            if (!e.contrib) continue;
-            ++walked;
+            const PairEval& e = k == 0 ? e0 : e1;
+            const bool ck = k == 0 ? c0p : c1p;
             const float Tn = T[k] * (1.0f - e.alpha);
-            if (Tn < p.t_min) {
-              done[k] = true;
-              continue;
-            }
-            const float w = e.alpha * T[k];
-            const float4 f0 = sf[j][0];
+            const bool stop = ck && Tn < p.t_min;  // this splat ends the walk and is not composited
+            const bool take = ck && !stop;
+            const float w = take ? e.alpha * T[k] : 0.0f;
             D[k] += w * (g2.w + f0.x * e.u + f0.y * e.v);
-            if (!sun) {
-              const float4 f1 = sf[j][1];
-              A0[k] += w * f1.y;
-              A1[k] += w * f1.z;
-              A2[k] += w * f1.w;
-              N0[k] += w * f0.z;
-              N1[k] += w * f0.w;
-              N2[k] += w * f1.x;
-            }
-            T[k] = Tn;
-            last[k] = b0 + (uint32_t)j + 1u;
+            A0[k] += w * f1.y;
+            A1[k] += w * f1.z;
+            A2[k] += w * f1.w;
+            N0[k] += w * f0.z;
+            N1[k] += w * f0.w;
+            N2[k] += w * f1.x;
+            T[k] = take ? Tn : T[k];
+            last[k] = take ? pos : last[k];
+            done[k] = done[k] || stop;
           }
         }
       }
     }
     const TargetIO io = p.io[t];
     const int64_t hw = (int64_t)cam.W * cam.H;
-    float C[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
-    if (io.rgb && p.color) {
-#pragma unroll
-      for (int i = 0; i < 12; ++i) C[i] = p.color[cam.cam * 12 + i];
-    }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int py = lg.py0 + 2 * k;
       if (!(lg.px < cam.W && py < cam.H)) continue;
       const int64_t pix = (int64_t)py * cam.W + lg.px;
       if (io.rgb) {
-        io.rgb[pix] = C[0] * A0[k] + C[1] * A1[k] + C[2] * A2[k] + C[3];
-        io.rgb[hw + pix] = C[4] * A0[k] + C[5] * A1[k] + C[6] * A2[k] + C[7];
-        io.rgb[2 * hw + pix] = C[8] * A0[k] + C[9] * A1[k] + C[10] * A2[k] + C[11];
+        // the splats carry C rgb; the offset c completes C A + c (Sec. 3.1 Eq. image_formation)
+        io.rgb[pix] = A0[k] + cam.C[3];
+        io.rgb[hw + pix] = A1[k] + cam.C[7];
+        io.rgb[2 * hw + pix] = A2[k] + cam.C[11];
       }
       if (io.depth) io.depth[pix] = D[k];
       if (io.normal) {
@@ -287,7 +251,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
   __shared__ float4 sf[BATCH][2];
   __shared__ uint32_t sk[BATCH];
   __shared__ float sacc[BATCH][kSaccStride];
-  __shared__ float scol[NW][16];
+  __shared__ float scol[NW][4];
   __shared__ int s_item;
   __shared__ unsigned int s_hi;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gl = lane & 7;
@@ -306,10 +270,9 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
     const int64_t recbase = (int64_t)t * p.n_pad;
     const TargetIO io = p.io[t];
     const int64_t hw = (int64_t)cam.W * cam.H;
-    const float* Cm = p.color ? p.color + cam.cam * 12 : nullptr;
 
-    float T[2], Tfin[2], y[2], Sg[2], gD[2], gAl[2];
-    float gA[2][3], gN[2][3], gR[2][3], Aacc[2][3];
+    // per pixel: T (recovered backwards), the composite behind (as g . S), the upstream
+    float T[2], Tfin[2], y[2], Sg[2], gD[2], gAl[2], gR[2][3], gN[2][3];
     uint32_t lastp[2];
     if (tid == 0) s_hi = range.x;
     __syncthreads();
@@ -322,7 +285,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
       Sg[k] = gD[k] = gAl[k] = 0.0f;
       lastp[k] = range.x;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) gA[k][c] = gN[k][c] = gR[k][c] = Aacc[k][c] = 0.0f;
+      for (int c = 0; c < 3; ++c) gR[k][c] = gN[k][c] = 0.0f;
       if (inside) {
         const int64_t pix = (int64_t)py * cam.W + lg.px;
         T[k] = io.T_final[pix];
@@ -330,16 +293,10 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         // the saved end of the walk, clamped to this tile's list
         lastp[k] = min(max(io.last[pix], range.x), range.y);
         if (!sun && io.d_rgb) {
+          // the splats carry C rgb, so d(rgb_out) multiplies their colour directly
           gR[k][0] = io.d_rgb[pix];
           gR[k][1] = io.d_rgb[hw + pix];
           gR[k][2] = io.d_rgb[2 * hw + pix];
-          // rgb_out = C A + c  ->  dA = C^T d(rgb_out)
-          if (Cm) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) gA[k][j] = Cm[j] * gR[k][0] + Cm[4 + j] * gR[k][1] + Cm[8 + j] * gR[k][2];
-          } else {
-            gA[k][0] = gR[k][0]; gA[k][1] = gR[k][1]; gA[k][2] = gR[k][2];
-          }
         }
         if (!sun && io.d_normal) {
           gN[k][0] = io.d_normal[pix];
@@ -354,6 +311,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
     __syncthreads();
     const uint32_t hi_all = s_hi;
     const float two_inv2s2 = 2.0f * p.k.inv2s2;
+    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (uint32_t hi = hi_all; hi > range.x;) {
       const uint32_t b0 = (hi - range.x > (uint32_t)BATCH) ? hi - BATCH : range.x;
       const int nb = (int)(hi - b0);
@@ -368,7 +326,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         sg[i][1] = g[1];
         sg[i][2] = g[2];
         sf[i][0] = f[0];
-        if (!sun) sf[i][1] = f[1];
+        sf[i][1] = sun ? zero4 : f[1];
       }
       for (int i = tid; i < nb * kSaccStride; i += NT) (&sacc[0][0])[i] = 0.0f;
       __syncthreads();
@@ -390,64 +348,51 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
           if (jj >= 0) {
             const uint32_t j = b0 + (uint32_t)jj;
             const float4 g0 = sg[jj][0], g1 = sg[jj][1], g2 = sg[jj][2];
-            const bool deg = g2.y < 0.0f;
+            const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
+            const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
+            const bool c0p = j < lastp[0] && e0.contrib, c1p = j < lastp[1] && e1.contrib;
+            any = c0p || c1p;
+            if (any) {
+              const bool deg = g2.y < 0.0f;
+              const float4 f0 = sf[jj][0], f1 = sf[jj][1];
+              // both pixels side by side; a pixel that the splat does not reach adds zeros
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-              if (j >= lastp[k]) continue;
-              const PairEval e = eval_pair(g0, g1, g2, x, y[k], p.k);
-              if (!e.contrib) continue;
-              any = true;
-              const float4 f0 = sf[jj][0];
-              const float om = 1.0f - e.alpha;
-              const float rom = __fdividef(1.0f, om);  // om >= 1 - alpha_max
-              const float Ti = T[k] * rom;
-              const float w = e.alpha * Ti;
-              const float z = g2.w + f0.x * e.u + f0.y * e.v;
-              float gf = gD[k] * z;
-              float4 f1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-              if (!sun) {
-                f1 = sf[jj][1];
-                gf += gA[k][0] * f1.y + gA[k][1] * f1.z + gA[k][2] * f1.w + gN[k][0] * f0.z + gN[k][1] * f0.w +
-                      gN[k][2] * f1.x;
-              }
-              const float dal = Ti * (gf - Sg[k]) + gAl[k] * Tfin[k] * rom;
-              Sg[k] = e.alpha * gf + om * Sg[k];
-              T[k] = Ti;
-              if (!sun) {
-                Aacc[k][0] += w * f1.y;
-                Aacc[k][1] += w * f1.z;
-                Aacc[k][2] += w * f1.w;
-                G[GF_R] += w * gA[k][0];
-                G[GF_G] += w * gA[k][1];
-                G[GF_B] += w * gA[k][2];
+              for (int k = 0; k < 2; ++k) {
+                const PairEval& e = k == 0 ? e0 : e1;
+                const bool ck = k == 0 ? c0p : c1p;
+                const float om = 1.0f - e.alpha;
+                const float rom = __fdividef(1.0f, om);  // om >= 1 - alpha_max
+                const float Ti = T[k] * rom;
+                const float z = g2.w + f0.x * e.u + f0.y * e.v;
+                const float gf = gD[k] * z + gR[k][0] * f1.y + gR[k][1] * f1.z + gR[k][2] * f1.w +
+                                 gN[k][0] * f0.z + gN[k][1] * f0.w + gN[k][2] * f1.x;
+                const float dal = Ti * (gf - Sg[k]) + gAl[k] * Tfin[k] * rom;
+                const float Sn = e.alpha * gf + om * Sg[k];
+                const float w = ck ? e.alpha * Ti : 0.0f;
+                T[k] = ck ? Ti : T[k];
+                Sg[k] = ck ? Sn : Sg[k];
+                G[GF_R] += w * gR[k][0];
+                G[GF_G] += w * gR[k][1];
+                G[GF_B] += w * gR[k][2];
                 G[GF_NX] += w * gN[k][0];
                 G[GF_NY] += w * gN[k][1];
                 G[GF_NZ] += w * gN[k][2];
-              }
-              const float dz = w * gD[k];
-              G[GF_ZC] += dz;
-              G[GF_DZDU] += dz * e.u;
-              G[GF_DZDV] += dz * e.v;
-              float du = deg ? 0.0f : dz * f0.x;
-              float dv = deg ? 0.0f : dz * f0.y;
-              if (!e.clamped) {
-                const float dpw = dal * e.alpha;  // d / d ln(o G^)
+                const float dz = w * gD[k];
+                G[GF_ZC] += dz;
+                G[GF_DZDU] += dz * e.u;
+                G[GF_DZDV] += dz * e.v;
+                // d / d ln(o G^); zero when clamped (the exact adjoint of the clamp)
+                const float dpw = (ck && !e.clamped) ? dal * e.alpha : 0.0f;
                 G[GF_LNO] += dpw;
-                if (e.uwin) {
-                  du -= dpw * e.u;
-                  dv -= dpw * e.v;
-                } else {
-                  G[GF_CX] += dpw * e.dx * two_inv2s2;
-                  G[GF_CY] += dpw * e.dy * two_inv2s2;
-                }
-              }
-              if (!deg) {
+                const float dpu = e.uwin ? dpw : 0.0f, dps = e.uwin ? 0.0f : dpw * two_inv2s2;
+                const float du = (deg ? 0.0f : dz * f0.x) - dpu * e.u;
+                const float dv = (deg ? 0.0f : dz * f0.y) - dpu * e.v;
                 G[GF_Q00] += du * e.dx;
                 G[GF_Q01] += du * e.dy;
                 G[GF_Q10] += dv * e.dx;
                 G[GF_Q11] += dv * e.dy;
-                G[GF_CX] -= g1.x * du + g1.z * dv;
-                G[GF_CY] -= g1.y * du + g1.w * dv;
+                G[GF_CX] += dps * e.dx - (g1.x * du + g1.z * dv);
+                G[GF_CY] += dps * e.dy - (g1.y * du + g1.w * dv);
               }
             }
           }
@@ -468,29 +413,27 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
       }
       hi = b0;
     }
-    // colour correction gradient of this target: dC = sum g A^T, dc = sum g
+    // gradient of the colour offset c of this target: the sum of d(rgb_out) over its pixels
+    // (the 3x3 block C is chained per splat in the projection adjoint)
     if (!sun && p.d_color && io.d_rgb) {
-      float cv[16];
+      float s3[3];
 #pragma unroll
-      for (int a = 0; a < 16; ++a) cv[a] = 0.0f;
+      for (int c = 0; c < 3; ++c) {
+        s3[c] = gR[0][c] + gR[1][c];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          cv[4 * a + 0] += gR[k][a] * Aacc[k][0];
-          cv[4 * a + 1] += gR[k][a] * Aacc[k][1];
-          cv[4 * a + 2] += gR[k][a] * Aacc[k][2];
-          cv[4 * a + 3] += gR[k][a];
-        }
+        for (int o = 16; o > 0; o >>= 1) s3[c] += __shfl_xor_sync(0xffffffffu, s3[c], o);
       }
-      const float r = warp_reduce16_transposed(cv);
-      if (!(lane & 1)) scol[warp][lane >> 1] = r;
+      if (lane == 0) {
+        scol[warp][0] = s3[0];
+        scol[warp][1] = s3[1];
+        scol[warp][2] = s3[2];
+      }
       __syncthreads();
-      if (tid < 12) {
+      if (tid < 3) {
         float s = 0.0f;
 #pragma unroll
         for (int w2 = 0; w2 < NW; ++w2) s += scol[w2][tid];
-        if (s != 0.0f) atomicAdd(p.d_color + cam.cam * 12 + tid, s);
+        if (s != 0.0f) atomicAdd(p.d_color + cam.cam * 12 + 4 * tid + 3, s);
       }
     }
   }

@@ -110,14 +110,14 @@ class Frame:
         return int(min(2 ** 31 - 1, max(1 << 16, 6 * n * len(self.targets), 600 * tiles)))
 
     # -------------------------------------------------------------- passes
-    def project_and_bin(self, splats: L.ss_splats, dF: Optional[torch.Tensor], sync: bool = True,
+    def project_and_bin(self, splats: L.ss_splats, dF: Optional[torch.Tensor], color=None, sync: bool = True,
                         stream=None) -> int:
         """Project, bin and sort.  With ``sync`` the intersection count is read back and the
         workspace grown and the frame re-run when it did not fit; returns the count."""
         cap = self.capacity if self.capacity is not None else self.default_capacity(int(splats.n))
         for _ in range(3):
             self.ensure_workspace(splats, cap)
-            L.project_splats(splats, self.cams, self.n_cams, self.passes, dF, self.opts, self.ws,
+            L.project_splats(splats, self.cams, self.n_cams, self.passes, dF, color, self.opts, self.ws,
                              self.ws_bytes, self.capacity, stream)
             st, needed = L.bin_and_sort(splats, self.cams, self.n_cams, self.passes, self.opts, self.ws,
                                         self.ws_bytes, self.capacity, sync_needed=sync, stream=stream)
@@ -131,37 +131,37 @@ class Frame:
 
     def forward(self, splats: L.ss_splats, dF=None, color=None, out: Optional[Outputs] = None,
                 sync: bool = True, stream=None) -> Outputs:
-        self.project_and_bin(splats, dF, sync=sync, stream=stream)
+        self.project_and_bin(splats, dF, color, sync=sync, stream=stream)
         out = out if out is not None else Outputs(self.targets, self.device)
         io = out.io_array()
-        L.rasterize_fwd(splats, self.cams, self.n_cams, self.passes, color, self.opts, io, self.ws,
+        L.rasterize_fwd(splats, self.cams, self.n_cams, self.passes, self.opts, io, self.ws,
                         self.ws_bytes, self.capacity, stream)
         return out
 
-    def rasterize(self, splats: L.ss_splats, color, out: Outputs, stream=None):
+    def rasterize(self, splats: L.ss_splats, out: Outputs, stream=None):
         io = out.io_array()
-        L.rasterize_fwd(splats, self.cams, self.n_cams, self.passes, color, self.opts, io, self.ws,
+        L.rasterize_fwd(splats, self.cams, self.n_cams, self.passes, self.opts, io, self.ws,
                         self.ws_bytes, self.capacity, stream)
 
     def backward(self, splats: L.ss_splats, out: Outputs, upstream: Sequence[dict], grads: dict,
-                 dF=None, color=None, d_dF=None, d_color=None, stream=None):
+                 d_dF=None, d_color=None, stream=None):
         """Accumulate gradients into ``grads`` (dict of fp32 [C, n_pad] tensors: means,
         scales, quats, opacity, rgb) and into d_dF [V,2,4] / d_color [V,3,4]."""
         io = out.io_array(upstream)
         g = grads_struct(grads)
-        L.rasterize_bwd(splats, self.cams, self.n_cams, self.passes, dF, color, self.opts, io, g, d_dF,
+        L.rasterize_bwd(splats, self.cams, self.n_cams, self.passes, self.opts, io, g, d_dF,
                         d_color, self.ws, self.ws_bytes, self.capacity, stream)
 
-    def backward_pixels(self, splats: L.ss_splats, out: Outputs, upstream: Sequence[dict], color=None,
-                        d_color=None, stream=None):
+    def backward_pixels(self, splats: L.ss_splats, out: Outputs, upstream: Sequence[dict], d_color=None,
+                        stream=None):
         """Per-pixel adjoint only (K4); finish with :meth:`backward_project`."""
         io = out.io_array(upstream)
-        L.rasterize_bwd(splats, self.cams, self.n_cams, self.passes, None, color, self.opts, io, None, None,
+        L.rasterize_bwd(splats, self.cams, self.n_cams, self.passes, self.opts, io, None, None,
                         d_color, self.ws, self.ws_bytes, self.capacity, stream)
 
-    def backward_project(self, splats: L.ss_splats, grads: dict, d_dF=None, stream=None):
+    def backward_project(self, splats: L.ss_splats, grads: dict, d_dF=None, d_color=None, stream=None):
         """Projection adjoint (K5) of the records left by :meth:`backward_pixels`."""
-        L.project_bwd(splats, self.cams, self.n_cams, self.passes, self.opts, grads_struct(grads), d_dF,
+        L.project_bwd(splats, self.cams, self.n_cams, self.passes, self.opts, grads_struct(grads), d_dF, d_color,
                       self.ws, self.ws_bytes, self.capacity, stream)
 
     def status(self, stream=None):

@@ -104,7 +104,7 @@ def test_backward_parity(name, passes):
     grads = zero_grads(ds.n_pad, "cuda")
     d_dF = torch.zeros(1, 2, 4, device="cuda")
     d_col = torch.zeros(1, 3, 4, device="cuda")
-    frame.backward(ds.splats, out, ups, grads, dF=ds.dF, color=ds.color, d_dF=d_dF, d_color=d_col)
+    frame.backward(ds.splats, out, ups, grads, d_dF=d_dF, d_color=d_col)
     torch.cuda.synchronize()
     ref = None
     for t, u in zip(frame.targets, ups_np):
@@ -147,7 +147,7 @@ def test_bf16_backward_parity():
     ups, ups_np = _upstream(scene, frame, 9, [(ora["margin_bwd"] >= MARGIN).astype(np.float64)])
     grads = zero_grads(ds.n_pad, "cuda")
     d_dF = torch.zeros(1, 2, 4, device="cuda")
-    frame.backward(ds.splats, out, ups, grads, dF=ds.dF, color=ds.color, d_dF=d_dF)
+    frame.backward(ds.splats, out, ups, grads, d_dF=d_dF)
     ref = oracle.backward(s64, cam, ups_np[0], color=cam.color)
     for k in ("means", "scales", "quats", "opacity", "rgb"):
         g = grads[k][:, : ds.n].cpu().numpy().astype(np.float64)
@@ -194,7 +194,7 @@ def test_capacity_overflow_is_reported_and_recovered():
     ds = DeviceScene(scene)
     frame = Frame(scene.cameras, L.SS_PASS_MAIN, capacity=100)
     frame.ensure_workspace(ds.splats, 100)
-    L.project_splats(ds.splats, frame.cams, 1, 1, ds.dF, frame.opts, frame.ws, frame.ws_bytes, 100)
+    L.project_splats(ds.splats, frame.cams, 1, 1, ds.dF, ds.color, frame.opts, frame.ws, frame.ws_bytes, 100)
     st, needed = L.bin_and_sort(ds.splats, frame.cams, 1, 1, frame.opts, frame.ws, frame.ws_bytes, 100)
     assert st == L.SS_ERR_CAPACITY and needed > 100
     st2, needed2, _, _, flags = frame.status()
@@ -213,22 +213,22 @@ def test_invalid_arguments_are_rejected():
     lib = L.load()
     import ctypes
     bad = L.default_opts(tile_w=12)
-    st = lib.ss_project_splats(ctypes.byref(ds.splats), frame.cams, 1, 1, None, ctypes.byref(bad),
+    st = lib.ss_project_splats(ctypes.byref(ds.splats), frame.cams, 1, 1, None, None, ctypes.byref(bad),
                                L.ptr(frame.ws), frame.ws_bytes, frame.capacity, None)
     assert st == L.SS_ERR_INVALID_ARG
-    st = lib.ss_project_splats(ctypes.byref(ds.splats), frame.cams, 1, 1, None, ctypes.byref(frame.opts),
+    st = lib.ss_project_splats(ctypes.byref(ds.splats), frame.cams, 1, 1, None, None, ctypes.byref(frame.opts),
                                L.ptr(frame.ws), 16, frame.capacity, None)
     assert st == L.SS_ERR_INVALID_ARG
-    st = lib.ss_project_splats(ctypes.byref(ds.splats), frame.cams, 0, 1, None, ctypes.byref(frame.opts),
+    st = lib.ss_project_splats(ctypes.byref(ds.splats), frame.cams, 0, 1, None, None, ctypes.byref(frame.opts),
                                L.ptr(frame.ws), frame.ws_bytes, frame.capacity, None)
     assert st == L.SS_ERR_INVALID_ARG
     s2 = L.make_splats(ds.means, ds.scales, ds.quats, ds.opacity, ds.rgb, ds.n)
     s2.n_pad = ds.n_pad + 3
-    st = lib.ss_project_splats(ctypes.byref(s2), frame.cams, 1, 1, None, ctypes.byref(frame.opts),
+    st = lib.ss_project_splats(ctypes.byref(s2), frame.cams, 1, 1, None, None, ctypes.byref(frame.opts),
                                L.ptr(frame.ws), frame.ws_bytes, frame.capacity, None)
     assert st == L.SS_ERR_INVALID_ARG
     io = (L.ss_target_io * 1)()  # T_final / last missing
-    st = lib.ss_rasterize_fwd(ctypes.byref(ds.splats), frame.cams, 1, 1, None, ctypes.byref(frame.opts), io,
+    st = lib.ss_rasterize_fwd(ctypes.byref(ds.splats), frame.cams, 1, 1, ctypes.byref(frame.opts), io,
                               L.ptr(frame.ws), frame.ws_bytes, frame.capacity, None)
     assert st == L.SS_ERR_INVALID_ARG
 
