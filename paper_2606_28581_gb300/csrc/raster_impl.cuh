@@ -124,7 +124,7 @@ __device__ __forceinline__ uint32_t group_mask(const float4 (*sg)[3], int c0, in
 // K3 forward
 // ------------------------------------------------------------------------------------------
 template <int TW, int TH, int BATCH, bool PERSIST>
-__global__ void __launch_bounds__(TW * TH / 2) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
+__global__ void __launch_bounds__(TW * TH / 2, 8) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
   constexpr int NT = TW * TH / 2;
   static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are whole 8 x 8 warp blocks");
   __shared__ float4 sg[BATCH][3];
@@ -176,37 +176,47 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_fwd_kernel(const __grid_co
       for (int c0 = 0; c0 < nb; c0 += 32) {
         uint32_t m = group_mask(sg, c0, nb, lg, p.cull);
         if (all_done) continue;
+        // two splats per step: their four pair evaluations are independent; only the
+        // compositing runs in order (splat a, then splat b) for each pixel
+        auto composite = [&](const PairEval& e, bool ck, int k, const float4& g2, const float4& f0,
+                             const float4& f1, uint32_t pos) {
+          const float Tn = T[k] * (1.0f - e.alpha);
+          const bool stop = ck && Tn < p.t_min;  // this splat ends the walk and is not composited
+          const bool take = ck && !stop;
+          const float w = take ? e.alpha * T[k] : 0.0f;
+          D[k] += w * (g2.w + f0.x * e.u + f0.y * e.v);
+          A0[k] += w * f1.y;
+          A1[k] += w * f1.z;
+          A2[k] += w * f1.w;
+          N0[k] += w * f0.z;
+          N1[k] += w * f0.w;
+          N2[k] += w * f1.x;
+          T[k] = take ? Tn : T[k];
+          last[k] = take ? pos : last[k];
+          done[k] = done[k] || stop;
+        };
         while (m) {
-          const int j = c0 + __ffs(m) - 1;
+          const int ja = c0 + __ffs(m) - 1;
           m &= m - 1;
-          const float4 g0 = sg[j][0], g1 = sg[j][1], g2 = sg[j][2];
-          // both pixels side by side (independent chains)
-          const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
-          const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
-          const bool c0p = !done[0] && e0.contrib, c1p = !done[1] && e1.contrib;
-          if (!(c0p || c1p)) continue;
-          walked += (uint32_t)c0p + (uint32_t)c1p;
-          const float4 f0 = sf[j][0], f1 = sf[j][1];
-          const uint32_t pos = b0 + (uint32_t)j + 1u;
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const PairEval& e = k == 0 ? e0 : e1;
-            const bool ck = k == 0 ? c0p : c1p;
-            const float Tn = T[k] * (1.0f - e.alpha);
-            const bool stop = ck && Tn < p.t_min;  // this splat ends the walk and is not composited
-            const bool take = ck && !stop;
-            const float w = take ? e.alpha * T[k] : 0.0f;
-            D[k] += w * (g2.w + f0.x * e.u + f0.y * e.v);
-            A0[k] += w * f1.y;
-            A1[k] += w * f1.z;
-            A2[k] += w * f1.w;
-            N0[k] += w * f0.z;
-            N1[k] += w * f0.w;
-            N2[k] += w * f1.x;
-            T[k] = take ? Tn : T[k];
-            last[k] = take ? pos : last[k];
-            done[k] = done[k] || stop;
-          }
+          const bool has_b = m != 0u;
+          const int jb = has_b ? c0 + __ffs(m) - 1 : ja;
+          m = has_b ? (m & (m - 1)) : m;
+          const float4 ga0 = sg[ja][0], ga1 = sg[ja][1], ga2 = sg[ja][2];
+          const float4 gb0 = sg[jb][0], gb1 = sg[jb][1], gb2 = sg[jb][2];
+          const PairEval ea0 = eval_pair(ga0, ga1, ga2, x, y[0], p.k);
+          const PairEval ea1 = eval_pair(ga0, ga1, ga2, x, y[1], p.k);
+          const PairEval eb0 = eval_pair(gb0, gb1, gb2, x, y[0], p.k);
+          const PairEval eb1 = eval_pair(gb0, gb1, gb2, x, y[1], p.k);
+          const float4 fa0 = sf[ja][0], fa1 = sf[ja][1], fb0 = sf[jb][0], fb1 = sf[jb][1];
+          const uint32_t pa = b0 + (uint32_t)ja + 1u, pb = b0 + (uint32_t)jb + 1u;
+          const bool ca0 = !done[0] && ea0.contrib, ca1 = !done[1] && ea1.contrib;
+          walked += (uint32_t)ca0 + (uint32_t)ca1;
+          composite(ea0, ca0, 0, ga2, fa0, fa1, pa);
+          composite(ea1, ca1, 1, ga2, fa0, fa1, pa);
+          const bool cb0 = has_b && !done[0] && eb0.contrib, cb1 = has_b && !done[1] && eb1.contrib;
+          walked += (uint32_t)cb0 + (uint32_t)cb1;
+          composite(eb0, cb0, 0, gb2, fb0, fb1, pb);
+          composite(eb1, cb1, 1, gb2, fb0, fb1, pb);
         }
       }
     }
@@ -330,7 +340,21 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
       }
       for (int i = tid; i < nb * kSaccStride; i += NT) (&sacc[0][0])[i] = 0.0f;
       __syncthreads();
-      // chunks in reverse list order; within a chunk each group walks its own splats backwards
+      // chunks in reverse list order; within a chunk each group walks its own splats backwards.
+      // The group reduction of one splat's 16 sums is issued in the next step, beside the next
+      // splat's arithmetic (software pipelining); Gp / jp hold the pending sums.
+      float Gp[16];
+#pragma unroll
+      for (int f = 0; f < 16; ++f) Gp[f] = 0.0f;
+      int jp = -1;
+      bool pend = false;  // some lane of the warp has pending sums
+      auto flush = [&]() {
+        group_reduce16(Gp);
+        if (jp >= 0) {
+          if (Gp[0] != 0.0f) atomicAdd(&sacc[jp][2 * gl], Gp[0]);
+          if (Gp[1] != 0.0f) atomicAdd(&sacc[jp][2 * gl + 1], Gp[1]);
+        }
+      };
 #pragma unroll 1
       for (int c0 = ((nb - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
         uint32_t m = group_mask(sg, c0, nb, lg, p.cull);
@@ -345,16 +369,20 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
 #pragma unroll
           for (int f = 0; f < 16; ++f) G[f] = 0.0f;
           bool any = false;
-          if (jj >= 0) {
-            const uint32_t j = b0 + (uint32_t)jj;
-            const float4 g0 = sg[jj][0], g1 = sg[jj][1], g2 = sg[jj][2];
+          {
+            // lanes whose group has no splat left evaluate a stand-in and add nothing
+            const int js = jj >= 0 ? jj : c0;
+            const uint32_t j = b0 + (uint32_t)js;
+            const float4 g0 = sg[js][0], g1 = sg[js][1], g2 = sg[js][2];
             const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
             const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
-            const bool c0p = j < lastp[0] && e0.contrib, c1p = j < lastp[1] && e1.contrib;
+            const bool c0p = jj >= 0 && j < lastp[0] && e0.contrib, c1p = jj >= 0 && j < lastp[1] && e1.contrib;
             any = c0p || c1p;
-            if (any) {
+            // the previous splat's group reduction overlaps this splat's arithmetic
+            if (pend) flush();
+            {
               const bool deg = g2.y < 0.0f;
-              const float4 f0 = sf[jj][0], f1 = sf[jj][1];
+              const float4 f0 = sf[js][0], f1 = sf[js][1];
               // both pixels side by side; a pixel that the splat does not reach adds zeros
 #pragma unroll
               for (int k = 0; k < 2; ++k) {
@@ -396,15 +424,13 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
               }
             }
           }
-          if (__any_sync(0xffffffffu, any)) {
-            group_reduce16(G);
-            if (jj >= 0) {
-              if (G[0] != 0.0f) atomicAdd(&sacc[jj][2 * gl], G[0]);
-              if (G[1] != 0.0f) atomicAdd(&sacc[jj][2 * gl + 1], G[1]);
-            }
-          }
+#pragma unroll
+          for (int f = 0; f < 16; ++f) Gp[f] = G[f];
+          jp = jj;
+          pend = __any_sync(0xffffffffu, any);
         }
       }
+      if (pend) flush();
       __syncthreads();
       for (int i = tid; i < nb * kGradFields; i += NT) {
         const int s = i >> 4, f = i & 15;
