@@ -249,7 +249,6 @@ ss_status fill_raster(RasterParams& rp, const ss_splats* s, const Layout& L, con
   rp.k.inv2s2 = 1.0f / (2.0f * sig * sig);
   rp.k.amin = o->alpha_min;
   rp.k.amax = o->alpha_max;
-  rp.k.ln_amin_slack = logf(o->alpha_min) - 1e-3f;
   rp.cull.ln_amin = logf(o->alpha_min);
   rp.cull.sigma2 = sig * sig;
   rp.t_min = o->t_min;

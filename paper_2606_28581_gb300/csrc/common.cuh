@@ -3,7 +3,8 @@
 // Data layout in HBM (one frame = one workspace):
 //   TargetCam   [T]                 assembled camera of every render target
 //   geom        [T][n_pad] 3 x f4   cx, cy, cx_lo, cy_lo | Q00 Q01 Q10 Q11 | lno, ex(sign=degenerate), ey, zc
-//   feat        [T][n_pad] 2 x f4   dzdu, dzdv, nx, ny | nz, r, g, b
+//   feat        [T][n_pad] 2 x f4   dzdu, dzdv, nx, ny | nz, C rgb
+//               (degenerate splats: Q = kDegenerateQ I, dzdu = dzdv = 0)
 //   rect        [T][n_pad] 4 x u16  tile rectangle x0, y0, x1, y1 (empty: x0 > x1)
 //   grad        [T][n_pad] 16 f32   d(loss)/d of the projected quantities (see GradField)
 //   lists       capacity x (tile key u32, splat index u32), sorted by tile, then front to back
@@ -139,9 +140,17 @@ __device__ __forceinline__ uint32_t float_order(float x) {
 // ---------------------------------------------------------------- per-pixel evaluation
 // The one definition of a splat's alpha at a pixel, shared by the forward and the
 // backward kernels so that both take every threshold decision identically.
+//
+// A degenerate splat (|det M| below det_eps) is drawn by the screen-space term alone.  Its
+// projected record carries Q = kDegenerateQ I and zero depth slopes instead of a flag: then
+// |Q (x - c)|^2 is at least 10^36 |x - c|^2 (or +inf), so the uv term never exceeds the
+// screen term, and at x = c, where both are 0, either choice gives the same alpha.  u and v
+// stay finite (|x - c| is bounded by the splat's extent), so w * u never forms inf * 0.
+constexpr float kDegenerateQ = 1e18f;
+
 struct PairEval {
   float dx, dy;   // x - c
-  float u, v;     // uv coordinates (0 for degenerate splats)
+  float u, v;     // uv coordinates (finite but meaningless for degenerate splats)
   float alpha;    // min(alpha_max, o G^)
   bool uwin;      // the uv Gaussian won the max (ties: uv)
   bool clamped;   // alpha_max reached
@@ -151,7 +160,6 @@ struct PairEval {
 struct EvalConsts {
   float inv2s2;   // 1 / (2 sigma^2)
   float amin, amax;
-  float ln_amin_slack;  // ln(alpha_min) - slack: below it no exp is evaluated
 };
 
 __device__ __forceinline__ PairEval eval_pair(const float4 g0, const float4 g1, const float4 g2,
@@ -159,26 +167,19 @@ __device__ __forceinline__ PairEval eval_pair(const float4 g0, const float4 g1, 
   PairEval e;
   e.dx = __fsub_rn(__fsub_rn(x, g0.x), g0.z);
   e.dy = __fsub_rn(__fsub_rn(y, g0.y), g0.w);
-  const bool deg = g2.y < 0.0f;
   e.u = __fmaf_rn(g1.y, e.dy, __fmul_rn(g1.x, e.dx));
   e.v = __fmaf_rn(g1.w, e.dy, __fmul_rn(g1.z, e.dx));
-  float pu = __fmul_rn(-0.5f, __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v)));
-  float ps = __fmul_rn(-__fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)), k.inv2s2);
-  if (deg) {
-    pu = -INFINITY;
-    e.u = 0.0f;
-    e.v = 0.0f;
-  }
-  e.uwin = pu >= ps;
-  const float p = e.uwin ? pu : ps;
-  const float lp = __fadd_rn(p, g2.x);  // ln(o G^) <= ln(o) <= 0
-  // branch free (the forward and backward evaluate both pixels of a lane side by side); below
-  // ln(alpha_min) - 1e-3 the exponential is below alpha_min, so the decisions are those of
-  // skipping it there
-  const float og = __expf(fmaxf(lp, k.ln_amin_slack - 4.0f));
-  e.clamped = og > k.amax;
-  e.alpha = e.clamped ? k.amax : og;
-  e.contrib = (lp >= k.ln_amin_slack) && (e.alpha >= k.amin);
+  const float pu = __fmul_rn(-0.5f, __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v)));
+  const float ps = __fmul_rn(-__fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)), k.inv2s2);
+  e.uwin = pu >= ps;  // only the backward reads it
+  const float lp = __fadd_rn(fmaxf(pu, ps), g2.x);  // ln(o G^) <= ln(o) <= 0
+  // branch free: the kernels evaluate several pairs side by side.  __expf is accurate to a
+  // few ulp, so alpha >= alpha_min decides the same as ln(o G^) >= ln(alpha_min) except within
+  // that error of the threshold, and both kernels take the decision from this same value.
+  const float og = __expf(lp);
+  e.clamped = og > k.amax;  // only the backward reads it
+  e.alpha = fminf(og, k.amax);
+  e.contrib = e.alpha >= k.amin;
   return e;
 }
 

@@ -187,7 +187,9 @@ __device__ __forceinline__ SplatProj project_one(const SplatIn& s, const TargetC
     r.Q[1][0] = -r.M[1][0] * id;
     r.Q[1][1] = r.M[0][0] * id;
   } else {
-    r.Q[0][0] = r.Q[0][1] = r.Q[1][0] = r.Q[1][1] = 0.0f;
+    // drawn by the screen-space term alone (see kDegenerateQ)
+    r.Q[0][0] = r.Q[1][1] = kDegenerateQ;
+    r.Q[0][1] = r.Q[1][0] = 0.0f;
   }
   const float nd = s.R[0][2] * cam.vs[0] + s.R[1][2] * cam.vs[1] + s.R[2][2] * cam.vs[2];
   r.flip = nd < 0.0f ? -1.0f : 1.0f;
@@ -266,7 +268,9 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectParams p) {
           g[1] = g1;
           g[2] = g2;
           float4* f = p.feat + rec * 2;
-          f[0] = make_float4(-s.su * s.R[2][0], -s.sv * s.R[2][1], sp.flip * s.R[0][2], sp.flip * s.R[1][2]);
+          // a degenerate splat's depth is zc at every pixel (u = v = 0 in the per-pixel definition)
+          f[0] = make_float4(sp.deg ? 0.0f : -s.su * s.R[2][0], sp.deg ? 0.0f : -s.sv * s.R[2][1],
+                             sp.flip * s.R[0][2], sp.flip * s.R[1][2]);
           // C (sum w rgb) = sum w (C rgb): main views composite the corrected splat colour
           const float* C = cam.C;
           f[1] = make_float4(sp.flip * s.R[2][2], C[0] * s.rgb[0] + C[1] * s.rgb[1] + C[2] * s.rgb[2],
@@ -370,8 +374,10 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdParams p) {
       }
       // depth at the centre zc = max_alt - p_z and its slopes dzdu = -s_u R20, dzdv = -s_v R21
       dp[2] -= g[GF_ZC];
-      dRS[2][0] -= g[GF_DZDU];
-      dRS[2][1] -= g[GF_DZDV];
+      if (!sp.deg) {  // a degenerate splat's depth has no slope term (its u, v fields are meaningless)
+        dRS[2][0] -= g[GF_DZDU];
+        dRS[2][1] -= g[GF_DZDV];
+      }
       // RS' = [s_u R[:,0], s_v R[:,1]]
 #pragma unroll
       for (int j = 0; j < 3; ++j) {

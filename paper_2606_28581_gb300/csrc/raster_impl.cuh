@@ -120,11 +120,50 @@ __device__ __forceinline__ uint32_t group_mask(const float4 (*sg)[3], int c0, in
   return m;
 }
 
+// Candidate masks of a whole staged batch: lane gl of a group ends with the group's mask of
+// chunk gl (staged splats [32 gl, 32 gl + 32)).  Holding every chunk at once lets a group walk
+// its candidates across chunk boundaries, so the groups of a warp stay busy until the warp's
+// total work, not each chunk's largest group, is done.
+template <int BATCH>
+__device__ __forceinline__ uint32_t batch_masks(const float4 (*sg)[3], int nb, const LaneGeom& lg,
+                                                const CullConsts& cc) {
+  static_assert(BATCH % 32 == 0 && BATCH / 32 <= 8, "one chunk per lane of a group");
+  const int gl = threadIdx.x & 7;
+  uint32_t mk = 0;
+#pragma unroll 1
+  for (int c0 = 0; c0 < nb; c0 += 32) {
+    const uint32_t m = group_mask(sg, c0, nb, lg, cc);
+    mk = (gl == (c0 >> 5)) ? m : mk;
+  }
+  return mk;
+}
+
+// Bits (one per chunk) of a group's non-empty chunk masks.
+__device__ __forceinline__ uint32_t chunk_bits(uint32_t mk, bool keep) {
+  const int lane = threadIdx.x & 31;
+  return (__ballot_sync(0xffffffffu, keep && mk != 0u) >> (lane & 24)) & 0xffu;
+}
+
+// Moves a group to its next non-empty chunk once the current mask m is used up: in list order
+// (REV false) or in reverse list order.  Every lane of the warp takes part (one shuffle).
+template <bool REV>
+__device__ __forceinline__ void next_chunk(uint32_t& m, int& cb, uint32_t& chunks, uint32_t mk) {
+  const int lane = threadIdx.x & 31;
+  const bool need = m == 0u && chunks != 0u;
+  const int ci = need ? (REV ? 31 - __clz(chunks) : __ffs(chunks) - 1) : 0;
+  const uint32_t got = __shfl_sync(0xffffffffu, mk, (lane & 24) | ci);
+  if (need) {
+    m = got;
+    cb = ci << 5;
+    chunks &= ~(1u << ci);
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // K3 forward
 // ------------------------------------------------------------------------------------------
 template <int TW, int TH, int BATCH, bool PERSIST>
-__global__ void __launch_bounds__(TW * TH / 2, 8) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
+__global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
   constexpr int NT = TW * TH / 2;
   static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are whole 8 x 8 warp blocks");
   __shared__ float4 sg[BATCH][3];
@@ -172,52 +211,58 @@ __global__ void __launch_bounds__(TW * TH / 2, 8) raster_fwd_kernel(const __grid
       }
       const bool all_done = done[0] && done[1];
       if (__syncthreads_and(all_done)) break;
-#pragma unroll 1
-      for (int c0 = 0; c0 < nb; c0 += 32) {
-        uint32_t m = group_mask(sg, c0, nb, lg, p.cull);
-        if (all_done) continue;
-        // two splats per step: their four pair evaluations are independent; only the
-        // compositing runs in order (splat a, then splat b) for each pixel
-        auto composite = [&](const PairEval& e, bool ck, int k, const float4& g2, const float4& f0,
-                             const float4& f1, uint32_t pos) {
-          const float Tn = T[k] * (1.0f - e.alpha);
-          const bool stop = ck && Tn < p.t_min;  // this splat ends the walk and is not composited
-          const bool take = ck && !stop;
-          const float w = take ? e.alpha * T[k] : 0.0f;
-          D[k] += w * (g2.w + f0.x * e.u + f0.y * e.v);
-          A0[k] += w * f1.y;
-          A1[k] += w * f1.z;
-          A2[k] += w * f1.w;
-          N0[k] += w * f0.z;
-          N1[k] += w * f0.w;
-          N2[k] += w * f1.x;
-          T[k] = take ? Tn : T[k];
-          last[k] = take ? pos : last[k];
-          done[k] = done[k] || stop;
-        };
-        while (m) {
-          const int ja = c0 + __ffs(m) - 1;
-          m &= m - 1;
-          const bool has_b = m != 0u;
-          const int jb = has_b ? c0 + __ffs(m) - 1 : ja;
-          m = has_b ? (m & (m - 1)) : m;
-          const float4 ga0 = sg[ja][0], ga1 = sg[ja][1], ga2 = sg[ja][2];
-          const float4 gb0 = sg[jb][0], gb1 = sg[jb][1], gb2 = sg[jb][2];
-          const PairEval ea0 = eval_pair(ga0, ga1, ga2, x, y[0], p.k);
-          const PairEval ea1 = eval_pair(ga0, ga1, ga2, x, y[1], p.k);
-          const PairEval eb0 = eval_pair(gb0, gb1, gb2, x, y[0], p.k);
-          const PairEval eb1 = eval_pair(gb0, gb1, gb2, x, y[1], p.k);
-          const float4 fa0 = sf[ja][0], fa1 = sf[ja][1], fb0 = sf[jb][0], fb1 = sf[jb][1];
-          const uint32_t pa = b0 + (uint32_t)ja + 1u, pb = b0 + (uint32_t)jb + 1u;
-          const bool ca0 = !done[0] && ea0.contrib, ca1 = !done[1] && ea1.contrib;
-          walked += (uint32_t)ca0 + (uint32_t)ca1;
-          composite(ea0, ca0, 0, ga2, fa0, fa1, pa);
-          composite(ea1, ca1, 1, ga2, fa0, fa1, pa);
-          const bool cb0 = has_b && !done[0] && eb0.contrib, cb1 = has_b && !done[1] && eb1.contrib;
-          walked += (uint32_t)cb0 + (uint32_t)cb1;
-          composite(eb0, cb0, 0, gb2, fb0, fb1, pb);
-          composite(eb1, cb1, 1, gb2, fb0, fb1, pb);
-        }
+      const uint32_t mk = batch_masks<BATCH>(sg, nb, lg, p.cull);
+      // a group whose 16 pixels have all stopped walks nothing
+      const bool gdone = ((__ballot_sync(0xffffffffu, all_done) >> (lane & 24)) & 0xffu) == 0xffu;
+      uint32_t chunks = chunk_bits(mk, !gdone);
+      // two splats per step: their four pair evaluations are independent; only the
+      // compositing runs in order (splat a, then splat b) for each pixel
+      auto composite = [&](const PairEval& e, bool ck, int k, const float4& g2, const float4& f0,
+                           const float4& f1, uint32_t pos) {
+        const float Tn = T[k] * (1.0f - e.alpha);
+        const bool stop = ck && Tn < p.t_min;  // this splat ends the walk and is not composited
+        const bool take = ck && !stop;
+        const float w = take ? e.alpha * T[k] : 0.0f;
+        D[k] += w * (g2.w + f0.x * e.u + f0.y * e.v);
+        A0[k] += w * f1.y;
+        A1[k] += w * f1.z;
+        A2[k] += w * f1.w;
+        N0[k] += w * f0.z;
+        N1[k] += w * f0.w;
+        N2[k] += w * f1.x;
+        T[k] = take ? Tn : T[k];
+        last[k] = take ? pos : last[k];
+        done[k] = done[k] || stop;
+      };
+      uint32_t m = 0;
+      int cb = 0;
+      while (true) {
+        next_chunk<false>(m, cb, chunks, mk);
+        if (!__any_sync(0xffffffffu, m != 0u)) break;
+        // lanes whose group has nothing left evaluate a stand-in and composite nothing
+        const bool has_a = m != 0u;
+        const int ja = has_a ? cb + __ffs(m) - 1 : 0;
+        m &= m - 1;
+        next_chunk<false>(m, cb, chunks, mk);
+        const bool has_b = m != 0u;
+        const int jb = has_b ? cb + __ffs(m) - 1 : ja;
+        m &= m - 1;
+        const float4 ga0 = sg[ja][0], ga1 = sg[ja][1], ga2 = sg[ja][2];
+        const float4 gb0 = sg[jb][0], gb1 = sg[jb][1], gb2 = sg[jb][2];
+        const PairEval ea0 = eval_pair(ga0, ga1, ga2, x, y[0], p.k);
+        const PairEval ea1 = eval_pair(ga0, ga1, ga2, x, y[1], p.k);
+        const PairEval eb0 = eval_pair(gb0, gb1, gb2, x, y[0], p.k);
+        const PairEval eb1 = eval_pair(gb0, gb1, gb2, x, y[1], p.k);
+        const float4 fa0 = sf[ja][0], fa1 = sf[ja][1], fb0 = sf[jb][0], fb1 = sf[jb][1];
+        const uint32_t pa = b0 + (uint32_t)ja + 1u, pb = b0 + (uint32_t)jb + 1u;
+        const bool ca0 = has_a && !done[0] && ea0.contrib, ca1 = has_a && !done[1] && ea1.contrib;
+        walked += (uint32_t)ca0 + (uint32_t)ca1;
+        composite(ea0, ca0, 0, ga2, fa0, fa1, pa);
+        composite(ea1, ca1, 1, ga2, fa0, fa1, pa);
+        const bool cb0 = has_b && !done[0] && eb0.contrib, cb1 = has_b && !done[1] && eb1.contrib;
+        walked += (uint32_t)cb0 + (uint32_t)cb1;
+        composite(eb0, cb0, 0, gb2, fb0, fb1, pb);
+        composite(eb1, cb1, 1, gb2, fb0, fb1, pb);
       }
     }
     const TargetIO io = p.io[t];
@@ -282,7 +327,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
     const int64_t hw = (int64_t)cam.W * cam.H;
 
     // per pixel: T (recovered backwards), the composite behind (as g . S), the upstream
-    float T[2], Tfin[2], y[2], Sg[2], gD[2], gAl[2], gR[2][3], gN[2][3];
+    float T[2], y[2], Sg[2], gD[2], gAlT[2], gR[2][3], gN[2][3];  // gAlT: d(alpha_out) T_final
     uint32_t lastp[2];
     if (tid == 0) s_hi = range.x;
     __syncthreads();
@@ -291,15 +336,14 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
       const int py = lg.py0 + 2 * k;
       const bool inside = lg.px < cam.W && py < cam.H;
       y[k] = (float)py + 0.5f;
-      T[k] = Tfin[k] = 1.0f;
-      Sg[k] = gD[k] = gAl[k] = 0.0f;
+      T[k] = 1.0f;
+      Sg[k] = gD[k] = gAlT[k] = 0.0f;
       lastp[k] = range.x;
 #pragma unroll
       for (int c = 0; c < 3; ++c) gR[k][c] = gN[k][c] = 0.0f;
       if (inside) {
         const int64_t pix = (int64_t)py * cam.W + lg.px;
         T[k] = io.T_final[pix];
-        Tfin[k] = T[k];
         // the saved end of the walk, clamped to this tile's list
         lastp[k] = min(max(io.last[pix], range.x), range.y);
         if (!sun && io.d_rgb) {
@@ -314,10 +358,15 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
           gN[k][2] = io.d_normal[2 * hw + pix];
         }
         if (io.d_depth) gD[k] = io.d_depth[pix];
-        if (io.d_alpha) gAl[k] = io.d_alpha[pix];
+        if (io.d_alpha) gAlT[k] = io.d_alpha[pix] * T[k];
         if (lastp[k] > range.x) atomicMax(&s_hi, lastp[k]);
       }
     }
+    // the group's last walked position (exclusive): its walk ends there
+    uint32_t glast = max(lastp[0], lastp[1]);
+    glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 1));
+    glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 2));
+    glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 4));
     __syncthreads();
     const uint32_t hi_all = s_hi;
     const float two_inv2s2 = 2.0f * p.k.inv2s2;
@@ -340,9 +389,15 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
       }
       for (int i = tid; i < nb * kSaccStride; i += NT) (&sacc[0][0])[i] = 0.0f;
       __syncthreads();
-      // chunks in reverse list order; within a chunk each group walks its own splats backwards.
+      // each group walks its candidates in reverse list order, up to its last walked splat.
       // The group reduction of one splat's 16 sums is issued in the next step, beside the next
       // splat's arithmetic (software pipelining); Gp / jp hold the pending sums.
+      uint32_t mk = batch_masks<BATCH>(sg, nb, lg, p.cull);
+      {
+        const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - (gl << 5);
+        mk = lim <= 0 ? 0u : (lim >= 32 ? mk : mk & ((1u << lim) - 1u));
+      }
+      uint32_t chunks = chunk_bits(mk, true);
       float Gp[16];
 #pragma unroll
       for (int f = 0; f < 16; ++f) Gp[f] = 0.0f;
@@ -355,15 +410,17 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
           if (Gp[1] != 0.0f) atomicAdd(&sacc[jp][2 * gl + 1], Gp[1]);
         }
       };
-#pragma unroll 1
-      for (int c0 = ((nb - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
-        uint32_t m = group_mask(sg, c0, nb, lg, p.cull);
-        while (__any_sync(0xffffffffu, m != 0u)) {
+      uint32_t m = 0;
+      int cb = 0;
+      {
+        while (true) {
+          next_chunk<true>(m, cb, chunks, mk);
+          if (!__any_sync(0xffffffffu, m != 0u)) break;
           int jj = -1;
           if (m) {
             const int bit = 31 - __clz(m);
             m &= ~(1u << bit);
-            jj = c0 + bit;
+            jj = cb + bit;
           }
           float G[16];
 #pragma unroll
@@ -371,7 +428,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
           bool any = false;
           {
             // lanes whose group has no splat left evaluate a stand-in and add nothing
-            const int js = jj >= 0 ? jj : c0;
+            const int js = jj >= 0 ? jj : 0;
             const uint32_t j = b0 + (uint32_t)js;
             const float4 g0 = sg[js][0], g1 = sg[js][1], g2 = sg[js][2];
             const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
@@ -381,9 +438,11 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
             // the previous splat's group reduction overlaps this splat's arithmetic
             if (pend) flush();
             {
-              const bool deg = g2.y < 0.0f;
               const float4 f0 = sf[js][0], f1 = sf[js][1];
-              // both pixels side by side; a pixel that the splat does not reach adds zeros
+              // both pixels side by side; a pixel that the splat does not reach adds zeros.  The
+              // two pixels share their column (e0.dx == e1.dx), so the terms linear in dx and
+              // the centre's chain through Q are summed over the lane before they are formed.
+              float du[2], dv[2], dps[2];
 #pragma unroll
               for (int k = 0; k < 2; ++k) {
                 const PairEval& e = k == 0 ? e0 : e1;
@@ -394,7 +453,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
                 const float z = g2.w + f0.x * e.u + f0.y * e.v;
                 const float gf = gD[k] * z + gR[k][0] * f1.y + gR[k][1] * f1.z + gR[k][2] * f1.w +
                                  gN[k][0] * f0.z + gN[k][1] * f0.w + gN[k][2] * f1.x;
-                const float dal = Ti * (gf - Sg[k]) + gAl[k] * Tfin[k] * rom;
+                const float dal = Ti * (gf - Sg[k]) + gAlT[k] * rom;
                 const float Sn = e.alpha * gf + om * Sg[k];
                 const float w = ck ? e.alpha * Ti : 0.0f;
                 T[k] = ck ? Ti : T[k];
@@ -412,16 +471,19 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
                 // d / d ln(o G^); zero when clamped (the exact adjoint of the clamp)
                 const float dpw = (ck && !e.clamped) ? dal * e.alpha : 0.0f;
                 G[GF_LNO] += dpw;
-                const float dpu = e.uwin ? dpw : 0.0f, dps = e.uwin ? 0.0f : dpw * two_inv2s2;
-                const float du = (deg ? 0.0f : dz * f0.x) - dpu * e.u;
-                const float dv = (deg ? 0.0f : dz * f0.y) - dpu * e.v;
-                G[GF_Q00] += du * e.dx;
-                G[GF_Q01] += du * e.dy;
-                G[GF_Q10] += dv * e.dx;
-                G[GF_Q11] += dv * e.dy;
-                G[GF_CX] += dps * e.dx - (g1.x * du + g1.z * dv);
-                G[GF_CY] += dps * e.dy - (g1.y * du + g1.w * dv);
+                const float dpu = e.uwin ? dpw : 0.0f;
+                dps[k] = e.uwin ? 0.0f : dpw * two_inv2s2;
+                // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
+                du[k] = dz * f0.x - dpu * e.u;
+                dv[k] = dz * f0.y - dpu * e.v;
               }
+              const float sdu = du[0] + du[1], sdv = dv[0] + dv[1];
+              G[GF_Q00] = sdu * e0.dx;
+              G[GF_Q01] = du[0] * e0.dy + du[1] * e1.dy;
+              G[GF_Q10] = sdv * e0.dx;
+              G[GF_Q11] = dv[0] * e0.dy + dv[1] * e1.dy;
+              G[GF_CX] = (dps[0] + dps[1]) * e0.dx - (g1.x * sdu + g1.z * sdv);
+              G[GF_CY] = dps[0] * e0.dy + dps[1] * e1.dy - (g1.y * sdu + g1.w * sdv);
             }
           }
 #pragma unroll
