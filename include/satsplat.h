@@ -118,7 +118,11 @@ typedef struct {
   int32_t pixels_per_thread; /* [2], the only value: each lane owns two pixels of a 4 x 4
                                 sub-block.  Tile shape, batch and persistence never change an
                                 output. */
-  int32_t reserved[2];
+  int32_t subblock_cull;  /* [1] each group of lanes walks only the staged splats whose support
+                             can reach its 4 x 4 sub-block; 0 walks every staged splat in every
+                             sub-block.  The outputs are identical (the test is conservative);
+                             0 is slower and serves to check that. */
+  int32_t reserved;
 } ss_raster_opts;
 
 /* Per render target I/O (device pointers; row-major [H][W] planes of the

@@ -41,7 +41,8 @@ class ss_raster_opts(ctypes.Structure):
                 ("persistent", ctypes.c_int32), ("sigma_px", ctypes.c_float),
                 ("det_eps", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
-                ("pixels_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("pixels_per_thread", ctypes.c_int32), ("subblock_cull", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ss_target_io(ctypes.Structure):

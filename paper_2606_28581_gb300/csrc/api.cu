@@ -46,6 +46,7 @@ ss_status check_opts(const ss_raster_opts* o) {
   if (o->batch != 128 && o->batch != 256) return SS_ERR_INVALID_ARG;
   if (o->pixels_per_thread != 2) return SS_ERR_INVALID_ARG;
   if (o->persistent != 0 && o->persistent != 1) return SS_ERR_INVALID_ARG;
+  if (o->subblock_cull != 0 && o->subblock_cull != 1) return SS_ERR_INVALID_ARG;
   if (!finite(o->sigma_px) || !(o->sigma_px > 0.0f)) return SS_ERR_INVALID_ARG;
   if (!finite(o->det_eps) || !(o->det_eps >= 0.0f)) return SS_ERR_INVALID_ARG;
   if (!finite(o->alpha_min) || !finite(o->alpha_max) || !(o->alpha_min > 0.0f) ||
@@ -252,6 +253,7 @@ ss_status fill_raster(RasterParams& rp, const ss_splats* s, const Layout& L, con
   rp.cull.ln_amin = logf(o->alpha_min);
   rp.cull.sigma2 = sig * sig;
   rp.t_min = o->t_min;
+  rp.subblock_cull = o->subblock_cull;
   return SS_OK;
 }
 
@@ -298,6 +300,7 @@ void ss_default_opts(ss_raster_opts* o) {
   o->alpha_max = 0.99f;
   o->t_min = 1e-4f;
   o->pixels_per_thread = 2;
+  o->subblock_cull = 1;
 }
 
 const char* ss_status_string(ss_status s) {

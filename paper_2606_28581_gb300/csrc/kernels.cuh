@@ -87,6 +87,7 @@ struct RasterParams {
   EvalConsts k;
   CullConsts cull;
   float t_min;
+  int32_t subblock_cull;   // 0: every staged splat is a candidate of every sub-block
   TargetIO io[kMaxTargets];
 };
 

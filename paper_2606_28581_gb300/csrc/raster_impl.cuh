@@ -3,9 +3,9 @@
 // One block renders one screen tile of one target and stages the tile's sorted splat list,
 // batch by batch, in shared memory.  Each warp owns an 8 x 8 pixel block made of four 4 x 4
 // sub-blocks; the 8 lanes of a group own one sub-block, two pixels per lane (rows r, r + 2).
-// For every 32 staged splats each group tests which of them can reach its sub-block (exact
-// footprint test, `may_touch`) and walks only those, in list order (forward) or reverse list
-// order (backward), independently of the other groups.  A pixel's walk is therefore exactly
+// The thread that stages a splat also forms the set of the tile's 16 sub-blocks its support can
+// reach (`subblock_mask`); each group walks only the staged splats that reach its sub-block, in
+// list order (forward) or reverse list order (backward), independently of the other groups.  A pixel's walk is therefore exactly
 // the per-pixel definition, whatever the tile shape or schedule.  With PERSIST one launch
 // sized to the GPU pulls (target, tile) items from a queue, so views of uneven size and sun
 // views share a single launch.
@@ -77,11 +77,11 @@ __device__ __forceinline__ bool next_item(const RasterParams& p, unsigned int* c
   return true;
 }
 
-// Pixels of this lane and the rectangle of its group's 4 x 4 sub-block.
+// Pixels of this lane, and the tile's origin.
 struct LaneGeom {
-  int px;                // pixel column
-  int py0;               // first pixel row; the second is py0 + 2
-  float xa, xb, ya, yb;  // the sub-block's pixel-centre rectangle
+  int px;        // pixel column
+  int py0;       // first pixel row; the second is py0 + 2
+  float x0, y0;  // the tile's first pixel column and row
 };
 
 template <int TW, int TH>
@@ -96,44 +96,91 @@ __device__ __forceinline__ LaneGeom lane_geom(const TargetCam& cam, int tile) {
   LaneGeom g;
   g.px = sbx + (gl & 3);
   g.py0 = sby + (gl >> 2);
-  g.xa = (float)sbx + 0.5f;
-  g.xb = (float)sbx + 3.5f;
-  g.ya = (float)sby + 0.5f;
-  g.yb = (float)sby + 3.5f;
+  g.x0 = (float)(tx * TW);
+  g.y0 = (float)(ty * TH);
   return g;
 }
 
-// The 32 bits of this lane's group: which of the chunk's staged splats [c0, c0 + 32) can reach
-// the group's sub-block (bit b <-> splat c0 + b).  Every lane tests 4 splats.
-__device__ __forceinline__ uint32_t group_mask(const float4 (*sg)[3], int c0, int nb, const LaneGeom& lg,
-                                               const CullConsts& cc) {
-  const int lane = threadIdx.x & 31;
-  const int grp = lane >> 3, gl = lane & 7;
-  uint32_t m = 0;
+// The 4 x 4 sub-blocks of a tile that a splat can reach: bit (row * TW / 4 + col) is set when the
+// support {alpha >= alpha_min} can contain a pixel centre of sub-block (col, row).  The support is
+// the ellipse |Q d|^2 <= r2 united with the disc |d|^2 <= sigma^2 r2 (d = x - c,
+// r2 = 2 (ln o - ln alpha_min)).  A convex set meets a rectangle exactly when its slice through
+// the rectangle's rows meets the rectangle's columns, so per row of sub-blocks the x-range of
+// each slice is formed and compared with the columns: exact for the ellipse and for the disc,
+// their union bounded by the hull of the two ranges.  On the ellipse's boundary at height y,
+// x = (-A01 y +- sqrt(A00 r2 - det(Q)^2 y^2)) / A00 with A = Q^T Q, extreme at y = -+A01 X / A11.
+// Conservative: r2 is inflated by 0.2 % (far above the FP32 error of the slice formulas and of
+// eval_pair) and the rectangles are padded by 2e-3 px (the centre's low part is ignored).
+// Degenerate splats (record ex < 0) have the disc only.
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t subblock_mask(const float4 g0, const float4 g1, const float4 g2, float x0,
+                                                  float y0, const CullConsts& cc) {
+  constexpr int SBX = TW / 4, SBY = TH / 4;
+  constexpr float kPad = 2e-3f;
+  const float r2 = fmaxf(2.0f * (g2.x - cc.ln_amin), 0.0f) * 1.002f + 1e-4f;
+  const float rd2 = r2 * cc.sigma2;
+  const bool ell = g2.y >= 0.0f;
+  const float Q00 = g1.x, Q01 = g1.y, Q10 = g1.z, Q11 = g1.w;
+  const float A00 = Q00 * Q00 + Q10 * Q10, A11 = Q01 * Q01 + Q11 * Q11, A01 = Q00 * Q01 + Q10 * Q11;
+  const float dq = fabsf(det2(Q00, Q01, Q10, Q11));
+  const float dA = dq * dq;
+  const float Ar2 = A00 * r2;
+  const float Xe = sqrtf(r2 * A11) / dq;  // x half-extent of the ellipse
+  const float Ye = sqrtf(Ar2) / dq;       // y half-extent
+  const float yr = -A01 * Xe / A11;       // height of the rightmost point (leftmost: -yr)
+  const float iA00 = 1.0f / A00;
+  // tile-relative offsets: pixel centre (x0 + i + 0.5) - cx
+  const float ox = x0 + 0.5f - g0.x, oy = y0 + 0.5f - g0.y;
+  uint32_t mask = 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int j = c0 + gl + 8 * i;
-    const bool keep = j < nb && may_touch(sg[j][0], sg[j][1], sg[j][2], lg.xa, lg.xb, lg.ya, lg.yb, cc);
-    const uint32_t b = __ballot_sync(0xffffffffu, keep);
-    m |= ((b >> (8 * grp)) & 0xffu) << (8 * i);
+  for (int b = 0; b < SBY; ++b) {
+    const float yl = oy + (float)(4 * b) - kPad, yh = oy + (float)(4 * b + 3) + kPad;
+    float lo = INFINITY, hi = -INFINITY;
+    if (ell && yh >= -Ye && yl <= Ye) {
+      const float er = fminf(fmaxf(yr, yl), yh), el = fminf(fmaxf(-yr, yl), yh);
+      const float hr = sqrtf(fmaxf(Ar2 - dA * er * er, 0.0f)), hl = sqrtf(fmaxf(Ar2 - dA * el * el, 0.0f));
+      hi = er == yr ? Xe : (hr - A01 * er) * iA00;
+      lo = el == -yr ? -Xe : (-hl - A01 * el) * iA00;
+    }
+    const float dy = fminf(fmaxf(0.0f, yl), yh);
+    if (dy * dy <= rd2) {
+      const float hw = sqrtf(rd2 - dy * dy);
+      lo = fminf(lo, -hw);
+      hi = fmaxf(hi, hw);
+    }
+    // columns c with [ox + 4c, ox + 4c + 3] (padded) meeting [lo, hi]
+    const float cl = fmaxf(ceilf((lo - ox - 3.0f - kPad) * 0.25f), 0.0f);
+    const float ch = fminf(floorf((hi - ox + kPad) * 0.25f), (float)(SBX - 1));
+    if (cl <= ch) {
+      const int a = (int)cl, z = (int)ch;
+      mask |= ((2u << z) - (1u << a)) << (b * SBX);
+    }
   }
-  return m;
+  return mask;
 }
 
-// Candidate masks of a whole staged batch: lane gl of a group ends with the group's mask of
-// chunk gl (staged splats [32 gl, 32 gl + 32)).  Holding every chunk at once lets a group walk
-// its candidates across chunk boundaries, so the groups of a warp stay busy until the warp's
-// total work, not each chunk's largest group, is done.
-template <int BATCH>
-__device__ __forceinline__ uint32_t batch_masks(const float4 (*sg)[3], int nb, const LaneGeom& lg,
-                                                const CullConsts& cc) {
+// Candidate masks of a whole staged batch from the per-splat sub-block masks: lane gl of a
+// group ends with the group's mask of chunk gl (staged splats [32 gl, 32 gl + 32)).  Holding
+// every chunk at once lets a group walk its candidates across chunk boundaries, so the groups
+// of a warp stay busy until the warp's total work, not each chunk's largest group, is done.
+template <int TW, int BATCH>
+__device__ __forceinline__ uint32_t batch_masks(const uint32_t* smask, int nb) {
   static_assert(BATCH % 32 == 0 && BATCH / 32 <= 8, "one chunk per lane of a group");
-  const int gl = threadIdx.x & 7;
+  constexpr int WBX = TW / 8, SBX = TW / 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, gl = lane & 7;
+  // bit of this warp's first sub-block; its groups add 0, 1, SBX, SBX + 1
+  const int base = (warp / WBX) * 2 * SBX + (warp % WBX) * 2;
   uint32_t mk = 0;
 #pragma unroll 1
   for (int c0 = 0; c0 < nb; c0 += 32) {
-    const uint32_t m = group_mask(sg, c0, nb, lg, cc);
-    mk = (gl == (c0 >> 5)) ? m : mk;
+    const int i = c0 + lane;
+    const uint32_t v = i < nb ? smask[i] >> base : 0u;
+    const uint32_t m0 = __ballot_sync(0xffffffffu, v & 1u);
+    const uint32_t m1 = __ballot_sync(0xffffffffu, (v >> 1) & 1u);
+    const uint32_t m2 = __ballot_sync(0xffffffffu, (v >> SBX) & 1u);
+    const uint32_t m3 = __ballot_sync(0xffffffffu, (v >> (SBX + 1)) & 1u);
+    const uint32_t mine = grp == 0 ? m0 : grp == 1 ? m1 : grp == 2 ? m2 : m3;
+    mk = (gl == (c0 >> 5)) ? mine : mk;
   }
   return mk;
 }
@@ -168,6 +215,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
   static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are whole 8 x 8 warp blocks");
   __shared__ float4 sg[BATCH][3];
   __shared__ float4 sf[BATCH][2];
+  __shared__ uint32_t smask[BATCH];
   __shared__ int s_item;
   const int tid = threadIdx.x, lane = tid & 31;
   int tile;
@@ -203,15 +251,17 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
         const int64_t rec = recbase + p.vals[b0 + i];
         const float4* g = p.geom + rec * 3;
         const float4* f = p.feat + rec * 2;
-        sg[i][0] = g[0];
-        sg[i][1] = g[1];
-        sg[i][2] = g[2];
+        const float4 g0 = g[0], g1 = g[1], g2 = g[2];
+        sg[i][0] = g0;
+        sg[i][1] = g1;
+        sg[i][2] = g2;
         sf[i][0] = f[0];
         sf[i][1] = sun ? zero4 : f[1];
+        smask[i] = p.subblock_cull ? subblock_mask<TW, TH>(g0, g1, g2, lg.x0, lg.y0, p.cull) : 0xffffu;
       }
       const bool all_done = done[0] && done[1];
       if (__syncthreads_and(all_done)) break;
-      const uint32_t mk = batch_masks<BATCH>(sg, nb, lg, p.cull);
+      const uint32_t mk = batch_masks<TW, BATCH>(smask, nb);
       // a group whose 16 pixels have all stopped walks nothing
       const bool gdone = ((__ballot_sync(0xffffffffu, all_done) >> (lane & 24)) & 0xffu) == 0xffu;
       uint32_t chunks = chunk_bits(mk, !gdone);
@@ -305,6 +355,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
   __shared__ float4 sg[BATCH][3];
   __shared__ float4 sf[BATCH][2];
   __shared__ uint32_t sk[BATCH];
+  __shared__ uint32_t smask[BATCH];
   __shared__ float sacc[BATCH][kSaccStride];
   __shared__ float scol[NW][4];
   __shared__ int s_item;
@@ -380,19 +431,21 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         const int64_t rec = recbase + kk;
         const float4* g = p.geom + rec * 3;
         const float4* f = p.feat + rec * 2;
+        const float4 g0 = g[0], g1 = g[1], g2 = g[2];
         sk[i] = kk;
-        sg[i][0] = g[0];
-        sg[i][1] = g[1];
-        sg[i][2] = g[2];
+        sg[i][0] = g0;
+        sg[i][1] = g1;
+        sg[i][2] = g2;
         sf[i][0] = f[0];
         sf[i][1] = sun ? zero4 : f[1];
+        smask[i] = p.subblock_cull ? subblock_mask<TW, TH>(g0, g1, g2, lg.x0, lg.y0, p.cull) : 0xffffu;
       }
       for (int i = tid; i < nb * kSaccStride; i += NT) (&sacc[0][0])[i] = 0.0f;
       __syncthreads();
       // each group walks its candidates in reverse list order, up to its last walked splat.
       // The group reduction of one splat's 16 sums is issued in the next step, beside the next
       // splat's arithmetic (software pipelining); Gp / jp hold the pending sums.
-      uint32_t mk = batch_masks<BATCH>(sg, nb, lg, p.cull);
+      uint32_t mk = batch_masks<TW, BATCH>(smask, nb);
       {
         const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - (gl << 5);
         mk = lim <= 0 ? 0u : (lim >= 32 ? mk : mk & ((1u << lim) - 1u));
