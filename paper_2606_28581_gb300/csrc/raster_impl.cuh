@@ -444,108 +444,108 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
       __syncthreads();
       // each group walks its candidates in reverse list order, up to its last walked splat.
       // The group reduction of one splat's 16 sums is issued in the next step, beside the next
-      // splat's arithmetic (software pipelining); Gp / jp hold the pending sums.
+      // splat's arithmetic (software pipelining); the sums alternate between GA and GB so that
+      // the pending ones are never copied.
       uint32_t mk = batch_masks<TW, BATCH>(smask, nb);
       {
         const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - (gl << 5);
         mk = lim <= 0 ? 0u : (lim >= 32 ? mk : mk & ((1u << lim) - 1u));
       }
       uint32_t chunks = chunk_bits(mk, true);
-      float Gp[16];
-#pragma unroll
-      for (int f = 0; f < 16; ++f) Gp[f] = 0.0f;
-      int jp = -1;
-      bool pend = false;  // some lane of the warp has pending sums
-      auto flush = [&]() {
-        group_reduce16(Gp);
-        if (jp >= 0) {
-          if (Gp[0] != 0.0f) atomicAdd(&sacc[jp][2 * gl], Gp[0]);
-          if (Gp[1] != 0.0f) atomicAdd(&sacc[jp][2 * gl + 1], Gp[1]);
-        }
-      };
       uint32_t m = 0;
       int cb = 0;
-      {
-        while (true) {
-          next_chunk<true>(m, cb, chunks, mk);
-          if (!__any_sync(0xffffffffu, m != 0u)) break;
-          int jj = -1;
-          if (m) {
-            const int bit = 31 - __clz(m);
-            m &= ~(1u << bit);
-            jj = cb + bit;
-          }
-          float G[16];
-#pragma unroll
-          for (int f = 0; f < 16; ++f) G[f] = 0.0f;
-          bool any = false;
-          {
-            // lanes whose group has no splat left evaluate a stand-in and add nothing
-            const int js = jj >= 0 ? jj : 0;
-            const uint32_t j = b0 + (uint32_t)js;
-            const float4 g0 = sg[js][0], g1 = sg[js][1], g2 = sg[js][2];
-            const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
-            const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
-            const bool c0p = jj >= 0 && j < lastp[0] && e0.contrib, c1p = jj >= 0 && j < lastp[1] && e1.contrib;
-            any = c0p || c1p;
-            // the previous splat's group reduction overlaps this splat's arithmetic
-            if (pend) flush();
-            {
-              const float4 f0 = sf[js][0], f1 = sf[js][1];
-              // both pixels side by side; a pixel that the splat does not reach adds zeros.  The
-              // two pixels share their column (e0.dx == e1.dx), so the terms linear in dx and
-              // the centre's chain through Q are summed over the lane before they are formed.
-              float du[2], dv[2], dps[2];
-#pragma unroll
-              for (int k = 0; k < 2; ++k) {
-                const PairEval& e = k == 0 ? e0 : e1;
-                const bool ck = k == 0 ? c0p : c1p;
-                const float om = 1.0f - e.alpha;
-                const float rom = __fdividef(1.0f, om);  // om >= 1 - alpha_max
-                const float Ti = T[k] * rom;
-                const float z = g2.w + f0.x * e.u + f0.y * e.v;
-                const float gf = gD[k] * z + gR[k][0] * f1.y + gR[k][1] * f1.z + gR[k][2] * f1.w +
-                                 gN[k][0] * f0.z + gN[k][1] * f0.w + gN[k][2] * f1.x;
-                const float dal = Ti * (gf - Sg[k]) + gAlT[k] * rom;
-                const float Sn = e.alpha * gf + om * Sg[k];
-                const float w = ck ? e.alpha * Ti : 0.0f;
-                T[k] = ck ? Ti : T[k];
-                Sg[k] = ck ? Sn : Sg[k];
-                G[GF_R] += w * gR[k][0];
-                G[GF_G] += w * gR[k][1];
-                G[GF_B] += w * gR[k][2];
-                G[GF_NX] += w * gN[k][0];
-                G[GF_NY] += w * gN[k][1];
-                G[GF_NZ] += w * gN[k][2];
-                const float dz = w * gD[k];
-                G[GF_ZC] += dz;
-                G[GF_DZDU] += dz * e.u;
-                G[GF_DZDV] += dz * e.v;
-                // d / d ln(o G^); zero when clamped (the exact adjoint of the clamp)
-                const float dpw = (ck && !e.clamped) ? dal * e.alpha : 0.0f;
-                G[GF_LNO] += dpw;
-                const float dpu = e.uwin ? dpw : 0.0f;
-                dps[k] = e.uwin ? 0.0f : dpw * two_inv2s2;
-                // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
-                du[k] = dz * f0.x - dpu * e.u;
-                dv[k] = dz * f0.y - dpu * e.v;
-              }
-              const float sdu = du[0] + du[1], sdv = dv[0] + dv[1];
-              G[GF_Q00] = sdu * e0.dx;
-              G[GF_Q01] = du[0] * e0.dy + du[1] * e1.dy;
-              G[GF_Q10] = sdv * e0.dx;
-              G[GF_Q11] = dv[0] * e0.dy + dv[1] * e1.dy;
-              G[GF_CX] = (dps[0] + dps[1]) * e0.dx - (g1.x * sdu + g1.z * sdv);
-              G[GF_CY] = dps[0] * e0.dy + dps[1] * e1.dy - (g1.y * sdu + g1.w * sdv);
-            }
-          }
-#pragma unroll
-          for (int f = 0; f < 16; ++f) Gp[f] = G[f];
-          jp = jj;
-          pend = __any_sync(0xffffffffu, any);
+      // group sums of splat jq, one atomic per field into the block's accumulator
+      auto flush = [&](float (&Gq)[16], const int jq) {
+        group_reduce16(Gq);
+        if (jq >= 0) {
+          if (Gq[0] != 0.0f) atomicAdd(&sacc[jq][2 * gl], Gq[0]);
+          if (Gq[1] != 0.0f) atomicAdd(&sacc[jq][2 * gl + 1], Gq[1]);
         }
+      };
+      float GA[16], GB[16];
+      int jA = -1, jB = -1;
+      bool pA = false, pB = false;  // some lane of the warp has pending sums in GA / GB
+      // one step: the next splat of this lane's group into Gc, the reduction of the pending Gq
+      auto step = [&](float (&Gc)[16], int& jc, bool& pc, float (&Gq)[16], const int jq, const bool pq) -> bool {
+        next_chunk<true>(m, cb, chunks, mk);
+        if (!__any_sync(0xffffffffu, m != 0u)) return false;
+        int jj = -1;
+        if (m) {
+          const int bit = 31 - __clz(m);
+          m &= ~(1u << bit);
+          jj = cb + bit;
+        }
+        // lanes whose group has no splat left evaluate a stand-in and add nothing
+        const int js = jj >= 0 ? jj : 0;
+        const uint32_t j = b0 + (uint32_t)js;
+        const float4 g0 = sg[js][0], g1 = sg[js][1], g2 = sg[js][2];
+        const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
+        const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
+        const bool c0p = jj >= 0 && j < lastp[0] && e0.contrib, c1p = jj >= 0 && j < lastp[1] && e1.contrib;
+        // the previous splat's group reduction overlaps this splat's arithmetic
+        if (pq) flush(Gq, jq);
+        const float4 f0 = sf[js][0], f1 = sf[js][1];
+        // both pixels side by side.  A pair that does not contribute runs with alpha = 0, which
+        // leaves T and S unchanged and adds zeros.  The two pixels share their column
+        // (e0.dx == e1.dx), so the terms linear in dx and the centre's chain through Q are
+        // summed over the lane before they are formed.
+        float du[2], dv[2], dps[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const PairEval& e = k == 0 ? e0 : e1;
+          const bool ck = k == 0 ? c0p : c1p;
+          const float a = ck ? e.alpha : 0.0f;
+          const float om = 1.0f - a;
+          const float rom = __fdividef(1.0f, om);  // om >= 1 - alpha_max
+          const float Ti = T[k] * rom;             // T in front of the splat
+          const float z = g2.w + f0.x * e.u + f0.y * e.v;
+          const float gf = gD[k] * z + gR[k][0] * f1.y + gR[k][1] * f1.z + gR[k][2] * f1.w +
+                           gN[k][0] * f0.z + gN[k][1] * f0.w + gN[k][2] * f1.x;
+          const float gs = gf - Sg[k];
+          const float w = a * Ti;
+          T[k] = Ti;
+          Sg[k] = Sg[k] + a * gs;  // composite from this splat on: a f + (1 - a) S
+          Gc[GF_R] = (k == 0 ? 0.0f : Gc[GF_R]) + w * gR[k][0];
+          Gc[GF_G] = (k == 0 ? 0.0f : Gc[GF_G]) + w * gR[k][1];
+          Gc[GF_B] = (k == 0 ? 0.0f : Gc[GF_B]) + w * gR[k][2];
+          Gc[GF_NX] = (k == 0 ? 0.0f : Gc[GF_NX]) + w * gN[k][0];
+          Gc[GF_NY] = (k == 0 ? 0.0f : Gc[GF_NY]) + w * gN[k][1];
+          Gc[GF_NZ] = (k == 0 ? 0.0f : Gc[GF_NZ]) + w * gN[k][2];
+          const float dz = w * gD[k];
+          Gc[GF_ZC] = (k == 0 ? 0.0f : Gc[GF_ZC]) + dz;
+          Gc[GF_DZDU] = (k == 0 ? 0.0f : Gc[GF_DZDU]) + dz * e.u;
+          Gc[GF_DZDV] = (k == 0 ? 0.0f : Gc[GF_DZDV]) + dz * e.v;
+          // d / d ln(o G^) = alpha dL/dalpha, dL/dalpha = T_i (f - S) + d(alpha_out) T_final / (1 - alpha);
+          // zero when clamped (the exact adjoint of the clamp)
+          const float dal = Ti * gs + gAlT[k] * rom;
+          const float dpw = e.clamped ? 0.0f : dal * a;
+          Gc[GF_LNO] = (k == 0 ? 0.0f : Gc[GF_LNO]) + dpw;
+          const float dpu = e.uwin ? dpw : 0.0f;
+          dps[k] = e.uwin ? 0.0f : dpw * two_inv2s2;
+          // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
+          du[k] = dz * f0.x - dpu * e.u;
+          dv[k] = dz * f0.y - dpu * e.v;
+        }
+        const float sdu = du[0] + du[1], sdv = dv[0] + dv[1];
+        Gc[GF_Q00] = sdu * e0.dx;
+        Gc[GF_Q01] = du[0] * e0.dy + du[1] * e1.dy;
+        Gc[GF_Q10] = sdv * e0.dx;
+        Gc[GF_Q11] = dv[0] * e0.dy + dv[1] * e1.dy;
+        Gc[GF_CX] = (dps[0] + dps[1]) * e0.dx - (g1.x * sdu + g1.z * sdv);
+        Gc[GF_CY] = dps[0] * e0.dy + dps[1] * e1.dy - (g1.y * sdu + g1.w * sdv);
+        jc = jj;
+        pc = __any_sync(0xffffffffu, c0p || c1p);
+        return true;
+      };
+      bool lastA = false;  // the last step that found a splat wrote GA (else GB)
+      while (true) {
+        if (!step(GA, jA, pA, GB, jB, pB)) break;
+        lastA = true;
+        if (!step(GB, jB, pB, GA, jA, pA)) break;
+        lastA = false;
       }
-      if (pend) flush();
+      // the sums of the last step are still pending
+      if (lastA ? pA : pB) flush(lastA ? GA : GB, lastA ? jA : jB);
       __syncthreads();
       for (int i = tid; i < nb * kGradFields; i += NT) {
         const int s = i >> 4, f = i & 15;
