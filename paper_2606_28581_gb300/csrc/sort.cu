@@ -168,29 +168,35 @@ __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(const uint
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter of one block's tile: ranks within the block (warps own consecutive
+// sub-chunks, equal digits ranked in element order with warp match masks), the tile reordered
+// by digit in shared memory, then written out in runs that are contiguous in the output.
 __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n_host, const uint32_t* n_dev, int shift, uint32_t mask,
     const uint32_t* hist_off, int64_t nblocks) {
   constexpr int kWarps = kRadixThreads / 32;
   __shared__ uint32_t whist[kWarps][256];
-  __shared__ uint32_t dbase[256];
+  __shared__ uint32_t dbase[256];   // output position of the block's first element of each digit
+  __shared__ uint32_t dstart[256];  // block-local position of the first element of each digit
+  __shared__ uint32_t sk[kRadixTile], sv[kRadixTile];
   const int64_t n = radix_count(n_host, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
   if (base >= n) return;
+  const int count = (int)min((int64_t)kRadixTile, n - base);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * 256; i += kRadixThreads) (&whist[0][0])[i] = 0;
   dbase[threadIdx.x] = hist_off[(int64_t)threadIdx.x * nblocks + blockIdx.x];
   __syncthreads();
   const uint32_t lt = (1u << lane) - 1u;
-  const int64_t wbase = base + (int64_t)warp * (kRadixItems * 32);
+  const int wbase = warp * (kRadixItems * 32);
   uint32_t k[kRadixItems], v[kRadixItems], rk[kRadixItems];
 #pragma unroll
   for (int i = 0; i < kRadixItems; ++i) {
-    const int64_t idx = wbase + i * 32 + lane;
-    const bool valid = idx < n;
-    k[i] = valid ? keys_in[idx] : 0u;
-    v[i] = valid ? vals_in[idx] : 0u;
+    const int idx = wbase + i * 32 + lane;
+    const bool valid = idx < count;
+    k[i] = valid ? keys_in[base + idx] : 0u;
+    v[i] = valid ? vals_in[base + idx] : 0u;
     const uint32_t d = valid ? ((k[i] >> shift) & mask) : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
   }
   __syncthreads();
   {
-    // exclusive scan of each digit's count over the warps (warps own consecutive sub-chunks)
+    // per digit: exclusive scan of the warps' counts, then over the digits
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
@@ -210,17 +216,27 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
       whist[w][threadIdx.x] = run;
       run += c;
     }
+    unsigned long long tot;
+    dstart[threadIdx.x] = (uint32_t)block_exclusive_scan((unsigned long long)run, &tot);
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kRadixItems; ++i) {
-    const int64_t idx = wbase + i * 32 + lane;
-    if (idx < n) {
+    const int idx = wbase + i * 32 + lane;
+    if (idx < count) {
       const uint32_t d = (k[i] >> shift) & mask;
-      const uint32_t pos = dbase[d] + whist[warp][d] + rk[i];
-      keys_out[pos] = k[i];
-      vals_out[pos] = v[i];
+      const uint32_t lp = dstart[d] + whist[warp][d] + rk[i];
+      sk[lp] = k[i];
+      sv[lp] = v[i];
     }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < count; j += kRadixThreads) {
+    const uint32_t kk = sk[j];
+    const uint32_t d = (kk >> shift) & mask;
+    const uint32_t pos = dbase[d] + (uint32_t)j - dstart[d];
+    keys_out[pos] = kk;
+    vals_out[pos] = sv[j];
   }
 }
 
