@@ -463,6 +463,8 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         }
       };
       float GA[16], GB[16];
+#pragma unroll
+      for (int f = 0; f < 16; ++f) GA[f] = GB[f] = 0.0f;
       int jA = -1, jB = -1;
       bool pA = false, pB = false;  // some lane of the warp has pending sums in GA / GB
       // one step: the next splat of this lane's group into Gc, the reduction of the pending Gq
@@ -482,8 +484,10 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
         const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
         const bool c0p = jj >= 0 && j < lastp[0] && e0.contrib, c1p = jj >= 0 && j < lastp[1] && e1.contrib;
-        // the previous splat's group reduction overlaps this splat's arithmetic
-        if (pq) flush(Gq, jq);
+        // the previous splat's group reduction overlaps this splat's arithmetic; it runs
+        // unconditionally (sums that nothing wrote are zeros) so that it stays branch free
+        (void)pq;
+        flush(Gq, jq);
         const float4 f0 = sf[js][0], f1 = sf[js][1];
         // both pixels side by side.  A pair that does not contribute runs with alpha = 0, which
         // leaves T and S unchanged and adds zeros.  The two pixels share their column
