@@ -107,7 +107,8 @@ typedef struct {
 /* Rasterizer options.  ss_default_opts() fills the defaults in brackets. */
 typedef struct {
   int32_t tile_w, tile_h; /* screen tile [16 x 16]; also 32 x 8 and 8 x 32 */
-  int32_t batch;          /* splats staged per block in shared memory [256]; 128 or 256 */
+  int32_t batch;          /* splats staged per block in shared memory [256]; 128 or 256 (the
+                             backward stages 224 when 256 is asked) */
   int32_t persistent;     /* [0] one block per tile; 1: one persistent launch that pulls
                              (target, tile) work items from a queue */
   float sigma_px;         /* screen-space low-pass sigma, pixels [1/sqrt(2)] */

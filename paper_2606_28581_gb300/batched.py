@@ -1,12 +1,14 @@
-"""Batched multi-view training step in one CUDA graph (training form b).
+"""Batched multi-view training step in CUDA graphs (training form b).
 
 All views and their sun views form one frame.  One step is: camera assembly +
 projection (K1), one shared height sort + binning of every target (K2), ONE
 persistent forward launch over every (target, tile) item (K3), ONE persistent
 backward launch (K4) and the projection adjoint (K5).  The step is captured once
-in a CUDA graph and replayed; the intersection capacity is fixed at capture and
-an overflow is reported through the workspace status block, which the host
-reads after a replay (``check``).
+as two CUDA graphs (forward part, backward part) and replayed; the intersection
+capacity is fixed at capture and an overflow is reported through the workspace
+status block, which the host reads after a replay (``check``).  From host
+buffers (``replay_from_host``) the upstream gradients are copied on a side
+stream while the forward part runs, and only the backward part waits for them.
 
 The autotuner times the candidate tile shapes and per-block splat batches on
 the actual workload and caches the winner per (GPU, workload) in a JSON file.
@@ -62,6 +64,7 @@ class BatchedStep:
         self._io_b = self.out.io_array(self.upstream)
         self._g = grads_struct(self.grads)
         self.graph = None
+        self._copy_stream = None
         # size the intersection capacity with one synchronised eager run
         needed = self.frame.project_and_bin(self.splats, self.dF, self.color, sync=True)
         cap = capacity if capacity is not None else max(1 << 16, int(needed * capacity_slack) + 4096)
@@ -101,34 +104,77 @@ class BatchedStep:
         self.d_dF.zero_()
         self.d_color.zero_()
 
-    def step_eager(self, stream=None):
-        self.zero_grads()
+    def forward_part(self, stream=None):
         self.project(stream)
         self.bin(stream)
         self.forward(stream)
+
+    def backward_part(self, stream=None):
+        self.zero_grads()
         self.backward_pixels(stream)
         self.backward_project(stream)
 
+    def step_eager(self, stream=None):
+        self.forward_part(stream)
+        self.backward_part(stream)
+
     # ------------------------------------------------------------------ graph
     def capture(self):
-        """Capture one step in a CUDA graph (after an eager warm-up run)."""
+        """Capture one step as two CUDA graphs (after an eager warm-up run): the forward part
+        (projection, binning, forward) and the backward part (gradient zeroing, backward,
+        projection adjoint)."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             self.step_eager()
         torch.cuda.current_stream().wait_stream(s)
         torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            self.step_eager()
+        gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gf):
+            self.forward_part()
+        with torch.cuda.graph(gb, pool=gf.pool()):
+            self.backward_part()
         torch.cuda.synchronize()
-        self.graph = g
-        return g
+        self.graph = (gf, gb)
+        return self.graph
 
     def replay(self):
         if self.graph is None:
             self.capture()
-        self.graph.replay()
+        self.graph[0].replay()
+        self.graph[1].replay()
+
+    def replay_from_host(self, h_splats: dict, h_dF, h_color, h_upstream: Sequence[dict], h_grads: dict,
+                         h_d_dF=None, h_d_color=None):
+        """One step from pinned host buffers: splats, camera deltas and colour corrections are
+        copied in, the upstream gradient planes follow on a side stream while the forward part
+        runs, the backward part waits for them, and the gradients are copied out (into
+        ``h_grads`` and the optional ``h_d_dF`` / ``h_d_color``).  Asynchronous: synchronise the
+        current stream before reading the host results."""
+        if self.graph is None:
+            self.capture()
+        cur = torch.cuda.current_stream()
+        if self._copy_stream is None:
+            self._copy_stream = torch.cuda.Stream()
+        side = self._copy_stream
+        for k, t in self.tensors.items():
+            t.copy_(h_splats[k], non_blocking=True)
+        self.dF.copy_(h_dF, non_blocking=True)
+        self.color.copy_(h_color, non_blocking=True)
+        side.wait_stream(cur)  # the previous step's backward has read the upstream planes
+        with torch.cuda.stream(side):
+            for du, hu in zip(self.upstream, h_upstream):
+                for k in du:
+                    du[k].copy_(hu[k], non_blocking=True)
+        self.graph[0].replay()
+        cur.wait_stream(side)
+        self.graph[1].replay()
+        for k, v in self.grads.items():
+            h_grads[k].copy_(v, non_blocking=True)
+        if h_d_dF is not None:
+            h_d_dF.copy_(self.d_dF, non_blocking=True)
+        if h_d_color is not None:
+            h_d_color.copy_(self.d_color, non_blocking=True)
 
     def check(self):
         """Synchronise and read the status block: (status, needed, walked, flags)."""
