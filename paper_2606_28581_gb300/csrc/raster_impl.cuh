@@ -185,25 +185,29 @@ __device__ __forceinline__ uint32_t batch_masks(const uint32_t* smask, int nb) {
   return mk;
 }
 
-// Bits (one per chunk) of a group's non-empty chunk masks.
-__device__ __forceinline__ uint32_t chunk_bits(uint32_t mk, bool keep) {
-  const int lane = threadIdx.x & 31;
-  return (__ballot_sync(0xffffffffu, keep && mk != 0u) >> (lane & 24)) & 0xffu;
-}
-
-// Moves a group to its next non-empty chunk once the current mask m is used up: in list order
-// (REV false) or in reverse list order.  Every lane of the warp takes part (one shuffle).
-template <bool REV>
-__device__ __forceinline__ void next_chunk(uint32_t& m, int& cb, uint32_t& chunks, uint32_t mk) {
-  const int lane = threadIdx.x & 31;
-  const bool need = m == 0u && chunks != 0u;
-  const int ci = need ? (REV ? 31 - __clz(chunks) : __ffs(chunks) - 1) : 0;
-  const uint32_t got = __shfl_sync(0xffffffffu, mk, (lane & 24) | ci);
-  if (need) {
-    m = got;
-    cb = ci << 5;
-    chunks &= ~(1u << ci);
+// Writes a group's candidates (the set bits of its chunk masks, lane gl holding chunk gl) to the
+// group's list of staged-splat indices, in list order, and returns their number.  The walk then
+// reads its next splat from the list at a position that depends on the step count alone, so no
+// step waits on the previous one to find its splat.  Every lane of the warp takes part.
+__device__ __forceinline__ int compact_candidates(uint32_t mk, uint8_t* list) {
+  const int gl = threadIdx.x & 7;
+  const int c = __popc(mk);
+  int inc = c;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o, 8);
+    if (gl >= o) inc += t;
   }
+  const int total = __shfl_sync(0xffffffffu, inc, 7, 8);
+  int pos = inc - c;
+  uint32_t mm = mk;
+  while (mm) {
+    const int bit = __ffs(mm) - 1;
+    mm &= mm - 1;
+    list[pos++] = (uint8_t)(gl * 32 + bit);
+  }
+  __syncwarp();
+  return total;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -216,6 +220,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
   __shared__ float4 sg[BATCH][3];
   __shared__ float4 sf[BATCH][2];
   __shared__ uint32_t smask[BATCH];
+  __shared__ uint8_t slist[NT / 8][BATCH];  // candidates of each group
   __shared__ int s_item;
   const int tid = threadIdx.x, lane = tid & 31;
   int tile;
@@ -264,7 +269,9 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
       const uint32_t mk = batch_masks<TW, BATCH>(smask, nb);
       // a group whose 16 pixels have all stopped walks nothing
       const bool gdone = ((__ballot_sync(0xffffffffu, all_done) >> (lane & 24)) & 0xffu) == 0xffu;
-      uint32_t chunks = chunk_bits(mk, !gdone);
+      const uint8_t* list = slist[tid >> 3];
+      const int total = compact_candidates(gdone ? 0u : mk, slist[tid >> 3]);
+      const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
       // two splats per step: their four pair evaluations are independent; only the
       // compositing runs in order (splat a, then splat b) for each pixel
       auto composite = [&](const PairEval& e, bool ck, int k, const float4& g2, const float4& f0,
@@ -284,19 +291,11 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
         last[k] = take ? pos : last[k];
         done[k] = done[k] || stop;
       };
-      uint32_t m = 0;
-      int cb = 0;
-      while (true) {
-        next_chunk<false>(m, cb, chunks, mk);
-        if (!__any_sync(0xffffffffu, m != 0u)) break;
+      for (int st = 0; st < nsteps; st += 2) {
         // lanes whose group has nothing left evaluate a stand-in and composite nothing
-        const bool has_a = m != 0u;
-        const int ja = has_a ? cb + __ffs(m) - 1 : 0;
-        m &= m - 1;
-        next_chunk<false>(m, cb, chunks, mk);
-        const bool has_b = m != 0u;
-        const int jb = has_b ? cb + __ffs(m) - 1 : ja;
-        m &= m - 1;
+        const bool has_a = st < total, has_b = st + 1 < total;
+        const int ja = has_a ? list[st] : 0;
+        const int jb = has_b ? list[st + 1] : ja;
         const float4 ga0 = sg[ja][0], ga1 = sg[ja][1], ga2 = sg[ja][2];
         const float4 gb0 = sg[jb][0], gb1 = sg[jb][1], gb2 = sg[jb][2];
         const PairEval ea0 = eval_pair(ga0, ga1, ga2, x, y[0], p.k);
@@ -356,6 +355,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
   __shared__ float4 sf[BATCH][2];
   __shared__ uint32_t sk[BATCH];
   __shared__ uint32_t smask[BATCH];
+  __shared__ uint8_t slist[NT / 8][BATCH];  // candidates of each group
   __shared__ float sacc[BATCH][kSaccStride];
   __shared__ float scol[NW][4];
   __shared__ int s_item;
@@ -451,9 +451,9 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - (gl << 5);
         mk = lim <= 0 ? 0u : (lim >= 32 ? mk : mk & ((1u << lim) - 1u));
       }
-      uint32_t chunks = chunk_bits(mk, true);
-      uint32_t m = 0;
-      int cb = 0;
+      const uint8_t* list = slist[tid >> 3];
+      const int total = compact_candidates(mk, slist[tid >> 3]);
+      const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
       // group sums of splat jq, one atomic per field into the block's accumulator
       auto flush = [&](float (&Gq)[16], const int jq) {
         group_reduce16(Gq);
@@ -466,17 +466,11 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
 #pragma unroll
       for (int f = 0; f < 16; ++f) GA[f] = GB[f] = 0.0f;
       int jA = -1, jB = -1;
-      bool pA = false, pB = false;  // some lane of the warp has pending sums in GA / GB
-      // one step: the next splat of this lane's group into Gc, the reduction of the pending Gq
-      auto step = [&](float (&Gc)[16], int& jc, bool& pc, float (&Gq)[16], const int jq, const bool pq) -> bool {
-        next_chunk<true>(m, cb, chunks, mk);
-        if (!__any_sync(0xffffffffu, m != 0u)) return false;
-        int jj = -1;
-        if (m) {
-          const int bit = 31 - __clz(m);
-          m &= ~(1u << bit);
-          jj = cb + bit;
-        }
+      // step st: the group's candidate total - 1 - st (reverse list order) into Gc, and the
+      // reduction of the pending Gq
+      auto step = [&](float (&Gc)[16], int& jc, float (&Gq)[16], const int jq, const int st) {
+        const int pos = total - 1 - st;
+        const int jj = pos >= 0 ? (int)list[pos] : -1;
         // lanes whose group has no splat left evaluate a stand-in and add nothing
         const int js = jj >= 0 ? jj : 0;
         const uint32_t j = b0 + (uint32_t)js;
@@ -486,7 +480,6 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         const bool c0p = jj >= 0 && j < lastp[0] && e0.contrib, c1p = jj >= 0 && j < lastp[1] && e1.contrib;
         // the previous splat's group reduction overlaps this splat's arithmetic; it runs
         // unconditionally (sums that nothing wrote are zeros) so that it stays branch free
-        (void)pq;
         flush(Gq, jq);
         const float4 f0 = sf[js][0], f1 = sf[js][1];
         // both pixels side by side.  A pair that does not contribute runs with alpha = 0, which
@@ -538,18 +531,17 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         Gc[GF_CX] = (dps[0] + dps[1]) * e0.dx - (g1.x * sdu + g1.z * sdv);
         Gc[GF_CY] = dps[0] * e0.dy + dps[1] * e1.dy - (g1.y * sdu + g1.w * sdv);
         jc = jj;
-        pc = __any_sync(0xffffffffu, c0p || c1p);
-        return true;
       };
-      bool lastA = false;  // the last step that found a splat wrote GA (else GB)
-      while (true) {
-        if (!step(GA, jA, pA, GB, jB, pB)) break;
+      bool lastA = false;  // the last step wrote GA (else GB)
+      for (int st = 0; st < nsteps; st += 2) {
+        step(GA, jA, GB, jB, st);
         lastA = true;
-        if (!step(GB, jB, pB, GA, jA, pA)) break;
+        if (st + 1 >= nsteps) break;
+        step(GB, jB, GA, jA, st + 1);
         lastA = false;
       }
       // the sums of the last step are still pending
-      if (lastA ? pA : pB) flush(lastA ? GA : GB, lastA ? jA : jB);
+      if (lastA) flush(GA, jA); else flush(GB, jB);
       __syncthreads();
       for (int i = tid; i < nb * kGradFields; i += NT) {
         const int s = i >> 4, f = i & 15;
