@@ -20,6 +20,8 @@
 // field) leaves the block.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace ss {
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
   __shared__ float4 sg[BATCH][3];
   __shared__ float4 sf[BATCH][2];
   __shared__ uint32_t smask[BATCH];
-  __shared__ uint8_t slist[NT / 8][BATCH];  // candidates of each group
+  __shared__ uint8_t slist[NT / 8][BATCH + 4];  // candidates of each group (rows padded: the 4 groups of a warp read at one position from different banks)
   __shared__ int s_item;
   const int tid = threadIdx.x, lane = tid & 31;
   int tile;
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
         sg[i][1] = g1;
         sg[i][2] = g2;
         sf[i][0] = f[0];
-        sf[i][1] = sun ? zero4 : f[1];
+        if (!sun) sf[i][1] = f[1];  // a sun view composites depth alone
         smask[i] = p.subblock_cull ? subblock_mask<TW, TH>(g0, g1, g2, lg.x0, lg.y0, p.cull) : 0xffffu;
       }
       const bool all_done = done[0] && done[1];
@@ -273,46 +275,54 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
       const int total = compact_candidates(gdone ? 0u : mk, slist[tid >> 3]);
       const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
       // two splats per step: their four pair evaluations are independent; only the
-      // compositing runs in order (splat a, then splat b) for each pixel
-      auto composite = [&](const PairEval& e, bool ck, int k, const float4& g2, const float4& f0,
-                           const float4& f1, uint32_t pos) {
-        const float Tn = T[k] * (1.0f - e.alpha);
-        const bool stop = ck && Tn < p.t_min;  // this splat ends the walk and is not composited
-        const bool take = ck && !stop;
-        const float w = take ? e.alpha * T[k] : 0.0f;
-        D[k] += w * (g2.w + f0.x * e.u + f0.y * e.v);
-        A0[k] += w * f1.y;
-        A1[k] += w * f1.z;
-        A2[k] += w * f1.w;
-        N0[k] += w * f0.z;
-        N1[k] += w * f0.w;
-        N2[k] += w * f1.x;
-        T[k] = take ? Tn : T[k];
-        last[k] = take ? pos : last[k];
-        done[k] = done[k] || stop;
+      // compositing runs in order (splat a, then splat b) for each pixel.  A sun view
+      // (SUN) composites depth alone: it has no colour or normal output.
+      auto walk = [&](auto sun_c) {
+        constexpr bool SUN = decltype(sun_c)::value;
+        auto composite = [&](const PairEval& e, bool ck, int k, const float4& g2, const float4& f0,
+                             const float4& f1, uint32_t pos) {
+          const float Tn = T[k] * (1.0f - e.alpha);
+          const bool stop = ck && Tn < p.t_min;  // this splat ends the walk and is not composited
+          const bool take = ck && !stop;
+          const float w = take ? e.alpha * T[k] : 0.0f;
+          D[k] += w * (g2.w + f0.x * e.u + f0.y * e.v);
+          if (!SUN) {
+            A0[k] += w * f1.y;
+            A1[k] += w * f1.z;
+            A2[k] += w * f1.w;
+            N0[k] += w * f0.z;
+            N1[k] += w * f0.w;
+            N2[k] += w * f1.x;
+          }
+          T[k] = take ? Tn : T[k];
+          last[k] = take ? pos : last[k];
+          done[k] = done[k] || stop;
+        };
+        for (int st = 0; st < nsteps; st += 2) {
+          // lanes whose group has nothing left evaluate a stand-in and composite nothing
+          const bool has_a = st < total, has_b = st + 1 < total;
+          const int ja = has_a ? list[st] : 0;
+          const int jb = has_b ? list[st + 1] : ja;
+          const float4 ga0 = sg[ja][0], ga1 = sg[ja][1], ga2 = sg[ja][2];
+          const float4 gb0 = sg[jb][0], gb1 = sg[jb][1], gb2 = sg[jb][2];
+          const PairEval ea0 = eval_pair(ga0, ga1, ga2, x, y[0], p.k);
+          const PairEval ea1 = eval_pair(ga0, ga1, ga2, x, y[1], p.k);
+          const PairEval eb0 = eval_pair(gb0, gb1, gb2, x, y[0], p.k);
+          const PairEval eb1 = eval_pair(gb0, gb1, gb2, x, y[1], p.k);
+          const float4 fa0 = sf[ja][0], fb0 = sf[jb][0];
+          const float4 fa1 = SUN ? zero4 : sf[ja][1], fb1 = SUN ? zero4 : sf[jb][1];
+          const uint32_t pa = b0 + (uint32_t)ja + 1u, pb = b0 + (uint32_t)jb + 1u;
+          const bool ca0 = has_a && !done[0] && ea0.contrib, ca1 = has_a && !done[1] && ea1.contrib;
+          walked += (uint32_t)ca0 + (uint32_t)ca1;
+          composite(ea0, ca0, 0, ga2, fa0, fa1, pa);
+          composite(ea1, ca1, 1, ga2, fa0, fa1, pa);
+          const bool cb0 = has_b && !done[0] && eb0.contrib, cb1 = has_b && !done[1] && eb1.contrib;
+          walked += (uint32_t)cb0 + (uint32_t)cb1;
+          composite(eb0, cb0, 0, gb2, fb0, fb1, pb);
+          composite(eb1, cb1, 1, gb2, fb0, fb1, pb);
+        }
       };
-      for (int st = 0; st < nsteps; st += 2) {
-        // lanes whose group has nothing left evaluate a stand-in and composite nothing
-        const bool has_a = st < total, has_b = st + 1 < total;
-        const int ja = has_a ? list[st] : 0;
-        const int jb = has_b ? list[st + 1] : ja;
-        const float4 ga0 = sg[ja][0], ga1 = sg[ja][1], ga2 = sg[ja][2];
-        const float4 gb0 = sg[jb][0], gb1 = sg[jb][1], gb2 = sg[jb][2];
-        const PairEval ea0 = eval_pair(ga0, ga1, ga2, x, y[0], p.k);
-        const PairEval ea1 = eval_pair(ga0, ga1, ga2, x, y[1], p.k);
-        const PairEval eb0 = eval_pair(gb0, gb1, gb2, x, y[0], p.k);
-        const PairEval eb1 = eval_pair(gb0, gb1, gb2, x, y[1], p.k);
-        const float4 fa0 = sf[ja][0], fa1 = sf[ja][1], fb0 = sf[jb][0], fb1 = sf[jb][1];
-        const uint32_t pa = b0 + (uint32_t)ja + 1u, pb = b0 + (uint32_t)jb + 1u;
-        const bool ca0 = has_a && !done[0] && ea0.contrib, ca1 = has_a && !done[1] && ea1.contrib;
-        walked += (uint32_t)ca0 + (uint32_t)ca1;
-        composite(ea0, ca0, 0, ga2, fa0, fa1, pa);
-        composite(ea1, ca1, 1, ga2, fa0, fa1, pa);
-        const bool cb0 = has_b && !done[0] && eb0.contrib, cb1 = has_b && !done[1] && eb1.contrib;
-        walked += (uint32_t)cb0 + (uint32_t)cb1;
-        composite(eb0, cb0, 0, gb2, fb0, fb1, pb);
-        composite(eb1, cb1, 1, gb2, fb0, fb1, pb);
-      }
+      if (sun) walk(std::true_type{}); else walk(std::false_type{});
     }
     const TargetIO io = p.io[t];
     const int64_t hw = (int64_t)cam.W * cam.H;
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
   __shared__ float4 sf[BATCH][2];
   __shared__ uint32_t sk[BATCH];
   __shared__ uint32_t smask[BATCH];
-  __shared__ uint8_t slist[NT / 8][BATCH];  // candidates of each group
+  __shared__ uint8_t slist[NT / 8][BATCH + 4];  // candidates of each group (rows padded: the 4 groups of a warp read at one position from different banks)
   __shared__ float sacc[BATCH][kSaccStride];
   __shared__ float scol[NW][4];
   __shared__ int s_item;
@@ -421,7 +431,6 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
     __syncthreads();
     const uint32_t hi_all = s_hi;
     const float two_inv2s2 = 2.0f * p.k.inv2s2;
-    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (uint32_t hi = hi_all; hi > range.x;) {
       const uint32_t b0 = (hi - range.x > (uint32_t)BATCH) ? hi - BATCH : range.x;
       const int nb = (int)(hi - b0);
@@ -437,7 +446,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         sg[i][1] = g1;
         sg[i][2] = g2;
         sf[i][0] = f[0];
-        sf[i][1] = sun ? zero4 : f[1];
+        if (!sun) sf[i][1] = f[1];  // a sun view has no colour or normal terms
         smask[i] = p.subblock_cull ? subblock_mask<TW, TH>(g0, g1, g2, lg.x0, lg.y0, p.cull) : 0xffffu;
       }
       for (int i = tid; i < nb * kSaccStride; i += NT) (&sacc[0][0])[i] = 0.0f;
@@ -466,82 +475,94 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
 #pragma unroll
       for (int f = 0; f < 16; ++f) GA[f] = GB[f] = 0.0f;
       int jA = -1, jB = -1;
-      // step st: the group's candidate total - 1 - st (reverse list order) into Gc, and the
-      // reduction of the pending Gq
-      auto step = [&](float (&Gc)[16], int& jc, float (&Gq)[16], const int jq, const int st) {
-        const int pos = total - 1 - st;
-        const int jj = pos >= 0 ? (int)list[pos] : -1;
-        // lanes whose group has no splat left evaluate a stand-in and add nothing
-        const int js = jj >= 0 ? jj : 0;
-        const uint32_t j = b0 + (uint32_t)js;
-        const float4 g0 = sg[js][0], g1 = sg[js][1], g2 = sg[js][2];
-        const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
-        const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
-        const bool c0p = jj >= 0 && j < lastp[0] && e0.contrib, c1p = jj >= 0 && j < lastp[1] && e1.contrib;
-        // the previous splat's group reduction overlaps this splat's arithmetic; it runs
-        // unconditionally (sums that nothing wrote are zeros) so that it stays branch free
-        flush(Gq, jq);
-        const float4 f0 = sf[js][0], f1 = sf[js][1];
-        // both pixels side by side.  A pair that does not contribute runs with alpha = 0, which
-        // leaves T and S unchanged and adds zeros.  The two pixels share their column
-        // (e0.dx == e1.dx), so the terms linear in dx and the centre's chain through Q are
-        // summed over the lane before they are formed.
-        float du[2], dv[2], dps[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const PairEval& e = k == 0 ? e0 : e1;
-          const bool ck = k == 0 ? c0p : c1p;
-          const float a = ck ? e.alpha : 0.0f;
-          const float om = 1.0f - a;
-          const float rom = __fdividef(1.0f, om);  // om >= 1 - alpha_max
-          const float Ti = T[k] * rom;             // T in front of the splat
-          const float z = g2.w + f0.x * e.u + f0.y * e.v;
-          const float gf = gD[k] * z + gR[k][0] * f1.y + gR[k][1] * f1.z + gR[k][2] * f1.w +
-                           gN[k][0] * f0.z + gN[k][1] * f0.w + gN[k][2] * f1.x;
-          const float gs = gf - Sg[k];
-          const float w = a * Ti;
-          T[k] = Ti;
-          Sg[k] = Sg[k] + a * gs;  // composite from this splat on: a f + (1 - a) S
-          Gc[GF_R] = (k == 0 ? 0.0f : Gc[GF_R]) + w * gR[k][0];
-          Gc[GF_G] = (k == 0 ? 0.0f : Gc[GF_G]) + w * gR[k][1];
-          Gc[GF_B] = (k == 0 ? 0.0f : Gc[GF_B]) + w * gR[k][2];
-          Gc[GF_NX] = (k == 0 ? 0.0f : Gc[GF_NX]) + w * gN[k][0];
-          Gc[GF_NY] = (k == 0 ? 0.0f : Gc[GF_NY]) + w * gN[k][1];
-          Gc[GF_NZ] = (k == 0 ? 0.0f : Gc[GF_NZ]) + w * gN[k][2];
-          const float dz = w * gD[k];
-          Gc[GF_ZC] = (k == 0 ? 0.0f : Gc[GF_ZC]) + dz;
-          Gc[GF_DZDU] = (k == 0 ? 0.0f : Gc[GF_DZDU]) + dz * e.u;
-          Gc[GF_DZDV] = (k == 0 ? 0.0f : Gc[GF_DZDV]) + dz * e.v;
-          // d / d ln(o G^) = alpha dL/dalpha, dL/dalpha = T_i (f - S) + d(alpha_out) T_final / (1 - alpha);
-          // zero when clamped (the exact adjoint of the clamp)
-          const float dal = Ti * gs + gAlT[k] * rom;
-          const float dpw = e.clamped ? 0.0f : dal * a;
-          Gc[GF_LNO] = (k == 0 ? 0.0f : Gc[GF_LNO]) + dpw;
-          const float dpu = e.uwin ? dpw : 0.0f;
-          dps[k] = e.uwin ? 0.0f : dpw * two_inv2s2;
-          // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
-          du[k] = dz * f0.x - dpu * e.u;
-          dv[k] = dz * f0.y - dpu * e.v;
+      // A sun view (SUN) has depth and alpha upstream only: its colour and normal terms are
+      // zero and are not formed.
+      auto walk = [&](auto sun_c) {
+        constexpr bool SUN = decltype(sun_c)::value;
+        // step st: the group's candidate total - 1 - st (reverse list order) into Gc, and the
+        // reduction of the pending Gq
+        auto step = [&](float (&Gc)[16], int& jc, float (&Gq)[16], const int jq, const int st) {
+          const int pos = total - 1 - st;
+          const int jj = pos >= 0 ? (int)list[pos] : -1;
+          // lanes whose group has no splat left evaluate a stand-in and add nothing
+          const int js = jj >= 0 ? jj : 0;
+          const uint32_t j = b0 + (uint32_t)js;
+          const float4 g0 = sg[js][0], g1 = sg[js][1], g2 = sg[js][2];
+          const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
+          const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
+          const bool c0p = jj >= 0 && j < lastp[0] && e0.contrib, c1p = jj >= 0 && j < lastp[1] && e1.contrib;
+          // the previous splat's group reduction overlaps this splat's arithmetic; it runs
+          // unconditionally (sums that nothing wrote are zeros) so that it stays branch free
+          flush(Gq, jq);
+          const float4 f0 = sf[js][0];
+          const float4 f1 = SUN ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : sf[js][1];
+          // both pixels side by side.  A pair that does not contribute runs with alpha = 0, which
+          // leaves T and S unchanged and adds zeros.  The two pixels share their column
+          // (e0.dx == e1.dx), so the terms linear in dx and the centre's chain through Q are
+          // summed over the lane before they are formed.
+          float du[2], dv[2], dps[2];
+  #pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const PairEval& e = k == 0 ? e0 : e1;
+            const bool ck = k == 0 ? c0p : c1p;
+            const float a = ck ? e.alpha : 0.0f;
+            const float om = 1.0f - a;
+            const float rom = __fdividef(1.0f, om);  // om >= 1 - alpha_max
+            const float Ti = T[k] * rom;             // T in front of the splat
+            const float z = g2.w + f0.x * e.u + f0.y * e.v;
+            const float gf = SUN ? gD[k] * z
+                                 : gD[k] * z + gR[k][0] * f1.y + gR[k][1] * f1.z + gR[k][2] * f1.w +
+                                       gN[k][0] * f0.z + gN[k][1] * f0.w + gN[k][2] * f1.x;
+            const float gs = gf - Sg[k];
+            const float w = a * Ti;
+            T[k] = Ti;
+            Sg[k] = Sg[k] + a * gs;  // composite from this splat on: a f + (1 - a) S
+            if (SUN) {
+              Gc[GF_R] = Gc[GF_G] = Gc[GF_B] = Gc[GF_NX] = Gc[GF_NY] = Gc[GF_NZ] = 0.0f;
+            } else {
+              Gc[GF_R] = (k == 0 ? 0.0f : Gc[GF_R]) + w * gR[k][0];
+              Gc[GF_G] = (k == 0 ? 0.0f : Gc[GF_G]) + w * gR[k][1];
+              Gc[GF_B] = (k == 0 ? 0.0f : Gc[GF_B]) + w * gR[k][2];
+              Gc[GF_NX] = (k == 0 ? 0.0f : Gc[GF_NX]) + w * gN[k][0];
+              Gc[GF_NY] = (k == 0 ? 0.0f : Gc[GF_NY]) + w * gN[k][1];
+              Gc[GF_NZ] = (k == 0 ? 0.0f : Gc[GF_NZ]) + w * gN[k][2];
+            }
+            const float dz = w * gD[k];
+            Gc[GF_ZC] = (k == 0 ? 0.0f : Gc[GF_ZC]) + dz;
+            Gc[GF_DZDU] = (k == 0 ? 0.0f : Gc[GF_DZDU]) + dz * e.u;
+            Gc[GF_DZDV] = (k == 0 ? 0.0f : Gc[GF_DZDV]) + dz * e.v;
+            // d / d ln(o G^) = alpha dL/dalpha, dL/dalpha = T_i (f - S) + d(alpha_out) T_final / (1 - alpha);
+            // zero when clamped (the exact adjoint of the clamp)
+            const float dal = Ti * gs + gAlT[k] * rom;
+            const float dpw = e.clamped ? 0.0f : dal * a;
+            Gc[GF_LNO] = (k == 0 ? 0.0f : Gc[GF_LNO]) + dpw;
+            const float dpu = e.uwin ? dpw : 0.0f;
+            dps[k] = e.uwin ? 0.0f : dpw * two_inv2s2;
+            // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
+            du[k] = dz * f0.x - dpu * e.u;
+            dv[k] = dz * f0.y - dpu * e.v;
+          }
+          const float sdu = du[0] + du[1], sdv = dv[0] + dv[1];
+          Gc[GF_Q00] = sdu * e0.dx;
+          Gc[GF_Q01] = du[0] * e0.dy + du[1] * e1.dy;
+          Gc[GF_Q10] = sdv * e0.dx;
+          Gc[GF_Q11] = dv[0] * e0.dy + dv[1] * e1.dy;
+          Gc[GF_CX] = (dps[0] + dps[1]) * e0.dx - (g1.x * sdu + g1.z * sdv);
+          Gc[GF_CY] = dps[0] * e0.dy + dps[1] * e1.dy - (g1.y * sdu + g1.w * sdv);
+          jc = jj;
+        };
+        bool lastA = false;  // the last step wrote GA (else GB)
+        for (int st = 0; st < nsteps; st += 2) {
+          step(GA, jA, GB, jB, st);
+          lastA = true;
+          if (st + 1 >= nsteps) break;
+          step(GB, jB, GA, jA, st + 1);
+          lastA = false;
         }
-        const float sdu = du[0] + du[1], sdv = dv[0] + dv[1];
-        Gc[GF_Q00] = sdu * e0.dx;
-        Gc[GF_Q01] = du[0] * e0.dy + du[1] * e1.dy;
-        Gc[GF_Q10] = sdv * e0.dx;
-        Gc[GF_Q11] = dv[0] * e0.dy + dv[1] * e1.dy;
-        Gc[GF_CX] = (dps[0] + dps[1]) * e0.dx - (g1.x * sdu + g1.z * sdv);
-        Gc[GF_CY] = dps[0] * e0.dy + dps[1] * e1.dy - (g1.y * sdu + g1.w * sdv);
-        jc = jj;
+        // the sums of the last step are still pending
+        if (lastA) flush(GA, jA); else flush(GB, jB);
       };
-      bool lastA = false;  // the last step wrote GA (else GB)
-      for (int st = 0; st < nsteps; st += 2) {
-        step(GA, jA, GB, jB, st);
-        lastA = true;
-        if (st + 1 >= nsteps) break;
-        step(GB, jB, GA, jA, st + 1);
-        lastA = false;
-      }
-      // the sums of the last step are still pending
-      if (lastA) flush(GA, jA); else flush(GB, jB);
+      if (sun) walk(std::true_type{}); else walk(std::false_type{});
       __syncthreads();
       for (int i = tid; i < nb * kGradFields; i += NT) {
         const int s = i >> 4, f = i & 15;
