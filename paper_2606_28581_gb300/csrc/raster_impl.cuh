@@ -64,6 +64,7 @@ __device__ __forceinline__ void group_reduce16(float v[16]) {
   }
 }
 
+// Work item of a block (forward): one block per tile, or the next item of the persistent queue.
 template <bool PERSIST>
 __device__ __forceinline__ bool next_item(const RasterParams& p, unsigned int* counter, int& tile, int& s_item) {
   if (!PERSIST) {
@@ -75,6 +76,27 @@ __device__ __forceinline__ bool next_item(const RasterParams& p, unsigned int* c
   __syncthreads();
   const int it = s_item;
   if (it >= p.total_tiles) return false;
+  tile = p.items ? (int)p.items[it] : it;
+  return true;
+}
+
+// Work items of a block (backward).  A persistent block claims its next (target, tile) item
+// while it works on the current one (s_item[cur ^ 1]), so claiming needs no barrier of its own:
+// the one barrier at the top of each iteration frees the shared buffers of the previous tile,
+// publishes the claim made during it, and orders the claim's overwrite after every read of the
+// slot.
+template <bool PERSIST>
+__device__ __forceinline__ bool begin_item(const RasterParams& p, unsigned int* counter, int* s_item, int& cur,
+                                           int iter, int& tile) {
+  __syncthreads();
+  if (!PERSIST) {
+    tile = blockIdx.x;
+    return iter == 0;
+  }
+  const int it = s_item[cur];
+  if (it >= p.total_tiles) return false;
+  if (threadIdx.x == 0) s_item[cur ^ 1] = (int)atomicAdd(counter, 1u);
+  cur ^= 1;
   tile = p.items ? (int)p.items[it] : it;
   return true;
 }
@@ -368,15 +390,18 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
   __shared__ uint8_t slist[NT / 8][BATCH + 4];  // candidates of each group (rows padded: the 4 groups of a warp read at one position from different banks)
   __shared__ float sacc[BATCH][kSaccStride];
   __shared__ float scol[NW][4];
-  __shared__ int s_item;
-  __shared__ unsigned int s_hi;
+  __shared__ int s_item[2];
+  __shared__ unsigned int s_hi[2];  // per iteration parity: the tile's largest walk end
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gl = lane & 7;
-  int tile;
-  bool first = true;
-  while (true) {
-    if (!PERSIST && !first) break;
-    first = false;
-    if (!next_item<PERSIST>(p, &p.status->work_bwd, tile, s_item)) break;
+  int cur = 0, tile;
+  if (tid == 0) {
+    if (PERSIST) s_item[0] = (int)atomicAdd(&p.status->work_bwd, 1u);
+    s_hi[0] = 0u;
+  }
+  for (int iter = 0;; ++iter) {
+    if (!begin_item<PERSIST>(p, &p.status->work_bwd, s_item, cur, iter, tile)) break;
+    const int hp = iter & 1;
+    if (tid == 0) s_hi[hp ^ 1] = 0u;  // reset for the next iteration (read in this one: s_hi[hp])
     const int t = find_target(p.tcams, p.n_targets, tile);
     const TargetCam& cam = p.tcams[t];
     const LaneGeom lg = lane_geom<TW, TH>(cam, tile);
@@ -390,8 +415,6 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
     // per pixel: T (recovered backwards), the composite behind (as g . S), the upstream
     float T[2], y[2], Sg[2], gD[2], gAlT[2], gR[2][3], gN[2][3];  // gAlT: d(alpha_out) T_final
     uint32_t lastp[2];
-    if (tid == 0) s_hi = range.x;
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int py = lg.py0 + 2 * k;
@@ -420,7 +443,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         }
         if (io.d_depth) gD[k] = io.d_depth[pix];
         if (io.d_alpha) gAlT[k] = io.d_alpha[pix] * T[k];
-        if (lastp[k] > range.x) atomicMax(&s_hi, lastp[k]);
+        if (lastp[k] > range.x) atomicMax(&s_hi[hp], lastp[k]);
       }
     }
     // the group's last walked position (exclusive): its walk ends there
@@ -429,12 +452,12 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
     glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 2));
     glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 4));
     __syncthreads();
-    const uint32_t hi_all = s_hi;
+    const uint32_t hi_all = s_hi[hp];  // 0 when no pixel walked: no batch
     const float two_inv2s2 = 2.0f * p.k.inv2s2;
     for (uint32_t hi = hi_all; hi > range.x;) {
       const uint32_t b0 = (hi - range.x > (uint32_t)BATCH) ? hi - BATCH : range.x;
       const int nb = (int)(hi - b0);
-      __syncthreads();
+      if (hi != hi_all) __syncthreads();  // the first batch follows the barrier after the upstream loads
       for (int i = tid; i < nb; i += NT) {
         const uint32_t kk = p.vals[b0 + i];
         const int64_t rec = recbase + kk;
