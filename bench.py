@@ -213,7 +213,8 @@ def time_loop(torch, fn, steps):
 
 def profiles_traffic(kernel: str):
     """Per-launch DRAM traffic of `kernel` from the committed ncu summary, if the summary was
-    taken on the current kernel source (fingerprint match); else None."""
+    taken on the current kernel sources (fingerprint of the listed files, concatenated); else
+    None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -222,11 +223,13 @@ def profiles_traffic(kernel: str):
         if ":" in ln:
             k, v = ln.split(":", 1)
             vals[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_2606_28581_gb300", "csrc", vals.get("source", "raster.cu"))
-    if not os.path.exists(src):
-        return None
-    fp = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if vals.get("source_sha256_16") != fp:
+    h = hashlib.sha256()
+    for name in vals.get("source", "raster_impl.cuh").split():
+        src = os.path.join(ROOT, "paper_2606_28581_gb300", "csrc", name)
+        if not os.path.exists(src):
+            return None
+        h.update(open(src, "rb").read())
+    if vals.get("source_sha256_16") != h.hexdigest()[:16]:
         return None
     try:
         return float(vals["bytes_per_launch_full"])
