@@ -200,7 +200,7 @@ __device__ __forceinline__ SplatProj project_one(const SplatIn& s, const TargetC
 // K1: projection of every splat into every target
 // ------------------------------------------------------------------------------------------
 template <typename Tst>
-__global__ void __launch_bounds__(256) project_kernel(ProjectParams p) {
+__global__ void __launch_bounds__(256, 3) project_kernel(ProjectParams p) {
   __shared__ TargetCam scam[kMaxTargets];
   for (int t = threadIdx.x; t < p.c.n_targets; t += blockDim.x) scam[t] = p.c.tcams[t];
   __syncthreads();
