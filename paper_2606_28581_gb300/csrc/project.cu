@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(ProjectParams p) {
 // K5: chain the per-(target, splat) gradient records through the projection
 // ------------------------------------------------------------------------------------------
 template <typename Tst>
-__global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdParams p) {
+__global__ void __launch_bounds__(256, 3) project_bwd_kernel(ProjectBwdParams p) {
   __shared__ TargetCam scam[kMaxTargets];
   __shared__ float red[8][17];
   for (int t = threadIdx.x; t < p.c.n_targets; t += blockDim.x) scam[t] = p.c.tcams[t];

@@ -345,19 +345,17 @@ __global__ void emit_kernel(BinParams p) {
 
 cudaError_t launch_counts(const BinParams& p, cudaStream_t st) {
   const int64_t m = (int64_t)p.n_targets * p.n;
-  if (m == 0) return cudaSuccess; {
+  if (m == 0) return cudaSuccess;
   count_launch();
   counts_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p);
-}
   return cudaGetLastError();
 }
 
 cudaError_t launch_emit(const BinParams& p, cudaStream_t st) {
   const int64_t m = (int64_t)p.n_targets * p.n;
-  if (m == 0) return cudaSuccess; {
+  if (m == 0) return cudaSuccess;
   count_launch();
   emit_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p);
-}
   return cudaGetLastError();
 }
 
@@ -375,21 +373,44 @@ cudaError_t launch_finish_count(StatusBlock* status, const uint32_t*, const uint
   return cudaGetLastError();
 }
 
+// [start, end) of every tile's run in the sorted keys.  Each thread reads four consecutive keys
+// (one 16-byte load) and takes its neighbours' boundary keys from the adjacent lanes; the
+// boundary lanes of a warp read them from memory.  Tiles without a run keep the zeros the
+// caller wrote.
 __global__ void ranges_kernel(const uint32_t* keys, const StatusBlock* status, uint2* ranges) {
   const int64_t n = status->n_isect32;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t key = keys[i];
-  if (i == 0 || keys[i - 1] != key) ranges[key].x = (uint32_t)i;
-  if (i == n - 1 || keys[i + 1] != key) ranges[key].y = (uint32_t)(i + 1);
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // quad index
+  const int64_t i0 = q * 4;
+  const int lane = threadIdx.x & 31;
+  uint32_t k[4];
+  if (i0 + 3 < n) {
+    const uint4 v = reinterpret_cast<const uint4*>(keys)[q];
+    k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? keys[i0 + j] : 0xffffffffu;
+  }
+  uint32_t prev = __shfl_up_sync(0xffffffffu, k[3], 1);
+  uint32_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
+  if (lane == 0) prev = (i0 > 0 && i0 - 1 < n) ? keys[i0 - 1] : 0xffffffffu;
+  if (lane == 31) next = i0 + 4 < n ? keys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t i = i0 + j;
+    if (i >= n) break;
+    const uint32_t before = j == 0 ? prev : k[j - 1];
+    const uint32_t after = (j == 3 || i + 1 >= n) ? (i + 1 >= n ? 0xffffffffu : next) : k[j + 1];
+    if (i == 0 || before != k[j]) ranges[k[j]].x = (uint32_t)i;
+    if (i + 1 == n || after != k[j]) ranges[k[j]].y = (uint32_t)(i + 1);
+  }
 }
 
 cudaError_t launch_ranges(const uint32_t* keys, const StatusBlock* status, uint2* ranges, int64_t capacity,
                           cudaStream_t st) {
-  if (capacity == 0) return cudaSuccess; {
+  if (capacity == 0) return cudaSuccess;
+  const int64_t quads = (capacity + 3) / 4;
   count_launch();
-  ranges_kernel<<<(unsigned)((capacity + 255) / 256), 256, 0, st>>>(keys, status, ranges);
-}
+  ranges_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, st>>>(keys, status, ranges);
   return cudaGetLastError();
 }
 
