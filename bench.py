@@ -340,6 +340,8 @@ def run_ours(args, dist):
         opts = L.default_opts(persistent=1)
     else:
         opts, tune = autotune(mk, workload_key(cams, scene.n, args.storage, passes), log=log)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
     step = mk(opts)
     n_before = L.kernel_launches()
     step.capture()
@@ -359,6 +361,8 @@ def run_ours(args, dist):
     clk.start()
     ms = time_loop(torch, step.replay, args.steps)
     clocks = clk.stop()
+    # device memory of the timed step: inputs, outputs, upstream planes, gradients, workspace
+    peak_hbm_gb = torch.cuda.max_memory_allocated() / 1e9
     dist.barrier()
     ms_max = dist.max(ms)
     total_px = dist.sum(main_px)
@@ -439,8 +443,8 @@ def run_ours(args, dist):
             if stf != L.SS_OK:
                 raise RuntimeError(f"plain frame status {L.status_string(stf)}")
         plain = {"value": main_px / (pms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": pms, "steps": p_steps,
-                 "storage": "fp32", "launch": "16 sequential single-view call sequences (eager, one block "
-                                               "per tile, 16x16 tiles)"}
+                 "storage": "fp32", "launch": f"{len(frames)} sequential single-view call sequences (eager, one "
+                                               "block per tile, 16x16 tiles)"}
         del frames, outs, ios, splats32
         torch.cuda.empty_cache()
 
@@ -499,6 +503,7 @@ def run_ours(args, dist):
                 "roofline": roofline, "cpu_baseline": cpu, "plain_fp32": plain,
                 "batched_over_plain": (value / dist.world) / plain["value"] if plain else None,
                 "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+                "steps_per_s": 1e3 / ms_max, "peak_hbm_gb": peak_hbm_gb,
                 "device": {"sms": sms, "arch": arch, "name": torch.cuda.get_device_name()}}
         print(json.dumps(line), flush=True)
     return 0
