@@ -261,6 +261,65 @@ ss_status ss_shadow_depth(const ss_splats* splats, const ss_camera* cams, int32_
                           void* ws, size_t ws_bytes, int64_t capacity, int64_t* needed,
                           ss_stream_t stream);
 
+/* Sun visibility and image formation (K7), Sec. 3.1 Eq. image_formation with the shadow
+ * mapping of Sec. 3.1 and Sec. 3.3.  Per main-view pixel x = (i + 0.5, j + 0.5):
+ *   z   = D / alpha                       receiver depth (alpha-normalised rendered depth)
+ *   h   = max_alt - z                     its height
+ *   u   = S (x - h B' s)                  where the sun ray through the receiver meets the
+ *                                         view's sun view (B' = F'[:, 0:3], s the sun
+ *                                         direction, S = shadow_scale; Supp. A)
+ *   z_o = bilinear sample of D_sun / alpha_sun at u (texel centres at +0.5)
+ *   V   = exp(-k max(z - z_o - bias, 0))  exponential shadow-map filter
+ *   I   = (C A + c) (V + (1 - V) L_a)     per channel, L_a the view's ambient light
+ * A pixel without a surface (alpha < alpha_eps), or whose sample needs a texel outside the sun
+ * view or without a surface, is lit (V = 1).  The paper takes the filter from earlier work
+ * without its constants: k, bias and alpha_eps are options. */
+typedef struct {
+  float esm_k;     /* filter sharpness per depth unit [2000] */
+  float esm_bias;  /* depth units [0] */
+  float alpha_eps; /* a pixel or texel with alpha below this has no surface [1e-3] */
+} ss_shade_opts;
+
+/* Per-view planes of the shading (device pointers, row-major, planar [3][H][W] for 3 channels):
+ *   rgb, depth, alpha          the main view's rasterize_fwd outputs (C A + c, D, alpha)
+ *   sun_depth, sun_alpha       the view's sun view [shadow_h][shadow_w]
+ *   image                      forward out: I [3][H][W]
+ *   vis                        forward out: V [H][W] (NULL = not written)
+ *   d_image                    backward in: dL/dI [3][H][W]
+ *   d_rgb, d_depth, d_alpha    backward: ADDED to (the main view's rasterizer upstream)
+ *   d_sun_depth, d_sun_alpha   backward: ADDED to (atomically; the sun view's upstream)
+ * Any backward output may be NULL (not written). */
+typedef struct {
+  const float* rgb;
+  const float* depth;
+  const float* alpha;
+  const float* sun_depth;
+  const float* sun_alpha;
+  float* image;
+  float* vis;
+  const float* d_image;
+  float* d_rgb;
+  float* d_depth;
+  float* d_alpha;
+  float* d_sun_depth;
+  float* d_sun_alpha;
+} ss_shade_io;
+
+void ss_default_shade_opts(ss_shade_opts* opts);
+
+/* Forward shading of n_cams views (one launch).  cams: HOST array; dF: DEVICE [n_cams][2][4]
+ * or NULL; La: DEVICE [n_cams][3]; io: HOST array of n_cams.  Errors: SS_ERR_INVALID_ARG. */
+ss_status ss_shade_fwd(const ss_camera* cams, int32_t n_cams, const float* dF, const float* La,
+                       const ss_shade_opts* opts, const ss_shade_io* io, ss_stream_t stream);
+
+/* Adjoint of ss_shade_fwd for io[v].d_image: adds into the io planes listed above, into d_La
+ * (DEVICE [n_cams][3], accumulated, or NULL) and into d_dF (DEVICE [n_cams][2][4], accumulated,
+ * or NULL: the sun position depends on B').  The derivative of V is zero where the filter is
+ * clamped at 1. */
+ss_status ss_shade_bwd(const ss_camera* cams, int32_t n_cams, const float* dF, const float* La,
+                       const ss_shade_opts* opts, const ss_shade_io* io, float* d_La, float* d_dF,
+                       ss_stream_t stream);
+
 /* Status block of a frame's workspace.  SYNCHRONISES the stream.
  *   needed:    intersections the last ss_bin_and_sort needed
  *   nonfinite: splats culled for non-finite values by the last projection

@@ -50,6 +50,16 @@ class ss_target_io(ctypes.Structure):
                 ("d_rgb", P), ("d_depth", P), ("d_normal", P), ("d_alpha", P)]
 
 
+class ss_shade_opts(ctypes.Structure):
+    _fields_ = [("esm_k", ctypes.c_float), ("esm_bias", ctypes.c_float), ("alpha_eps", ctypes.c_float)]
+
+
+class ss_shade_io(ctypes.Structure):
+    _fields_ = [("rgb", P), ("depth", P), ("alpha", P), ("sun_depth", P), ("sun_alpha", P), ("image", P),
+                ("vis", P), ("d_image", P), ("d_rgb", P), ("d_depth", P), ("d_alpha", P),
+                ("d_sun_depth", P), ("d_sun_alpha", P)]
+
+
 class ss_splat_grads(ctypes.Structure):
     _fields_ = [("means", P), ("scales", P), ("quats", P), ("opacity", P), ("rgb", P),
                 ("n_pad", ctypes.c_int64)]
@@ -58,7 +68,7 @@ class ss_splat_grads(ctypes.Structure):
 EXPORTS = ["ss_default_opts", "ss_status_string", "ss_workspace_size", "ss_project_splats",
            "ss_bin_and_sort", "ss_rasterize_fwd", "ss_rasterize_bwd", "ss_project_bwd", "ss_shadow_depth",
            "ss_frame_status", "ss_device_info", "ss_kernel_launches", "ss_render_fwd_noalloc",
-           "ss_noalloc_scratch_bytes"]
+           "ss_noalloc_scratch_bytes", "ss_default_shade_opts", "ss_shade_fwd", "ss_shade_bwd"]
 
 _lock = threading.Lock()
 _lib = None
@@ -104,9 +114,14 @@ def load(path: Optional[str] = None):
         L.ss_noalloc_scratch_bytes.restype = SZ
         L.ss_kernel_launches.argtypes = []
         L.ss_kernel_launches.restype = I64
+        PSO, PSI = ctypes.POINTER(ss_shade_opts), ctypes.POINTER(ss_shade_io)
+        L.ss_default_shade_opts.argtypes = [PSO]
+        L.ss_default_shade_opts.restype = None
+        L.ss_shade_fwd.argtypes = [PC, I32, P, P, PSO, PSI, P]
+        L.ss_shade_bwd.argtypes = [PC, I32, P, P, PSO, PSI, P, P, P]
         for name in EXPORTS:
             if name not in ("ss_default_opts", "ss_status_string", "ss_device_info", "ss_kernel_launches",
-                            "ss_noalloc_scratch_bytes"):
+                            "ss_noalloc_scratch_bytes", "ss_default_shade_opts"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -264,3 +279,31 @@ def device_info():
     sms, arch = ctypes.c_int32(0), ctypes.c_int32(0)
     load().ss_device_info(ctypes.byref(sms), ctypes.byref(arch))
     return int(sms.value), int(arch.value)
+
+
+# ------------------------------------------------------------------------------ shading (K7)
+def default_shade_opts(**overrides) -> ss_shade_opts:
+    o = ss_shade_opts()
+    load().ss_default_shade_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def shade_io_array(views: Sequence[dict]) -> ctypes.Array:
+    """ss_shade_io per view from dicts of tensors (keys as the struct's fields; missing = NULL)."""
+    arr = (ss_shade_io * len(views))()
+    for i, v in enumerate(views):
+        for name, _ in ss_shade_io._fields_:
+            setattr(arr[i], name, ptr(v.get(name)))
+    return arr
+
+
+def shade_fwd(cams, n_cams: int, dF, La, opts: ss_shade_opts, io, stream=None) -> None:
+    _check(load().ss_shade_fwd(cams, n_cams, ptr(dF), ptr(La), ctypes.byref(opts), io, stream_ptr(stream)),
+           "ss_shade_fwd")
+
+
+def shade_bwd(cams, n_cams: int, dF, La, opts: ss_shade_opts, io, d_La=None, d_dF=None, stream=None) -> None:
+    _check(load().ss_shade_bwd(cams, n_cams, ptr(dF), ptr(La), ctypes.byref(opts), io, ptr(d_La), ptr(d_dF),
+                               stream_ptr(stream)), "ss_shade_bwd")

@@ -1,0 +1,281 @@
+// Sun visibility and image formation (K7), Sec. 3.1 Eq. image_formation with the shadow mapping
+// of Sec. 3.1 / Sec. 3.3 (sun camera of Supp. A).
+//
+// One thread per main-view pixel, every view in one launch (blockIdx.y = view).  The receiver
+// (alpha-normalised rendered depth z, height h = max_alt - z) is moved along the sun ray into
+// the view's sun view at u = S (x - h B' s); the occluder depth z_o is the bilinear sample of
+// the sun view's alpha-normalised depth there; V = exp(-k max(z - z_o - bias, 0)) and
+// I = (C A + c) (V + (1 - V) L_a).  The pass is HBM-bound: per pixel it reads 5 planes (and
+// four sun texels, mostly from L2) and writes 3 or 4.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace ss {
+
+struct ShadeView {
+  float B[2][3];  // F_xy[:, 0:3] (host values; dF is added on the device)
+  float s[3];     // sun direction (cos phi / tan theta, sin phi / tan theta, 1)
+  float S, maxalt;
+  int32_t W, H, Ws, Hs;
+  ss_shade_io io;
+};
+
+struct ShadeParams {
+  ShadeView v[kMaxCams];
+  const float* dF;  // [V][8] or null
+  const float* La;  // [V][3]
+  float* d_La;      // [V][3] or null
+  float* d_dF;      // [V][8] or null
+  float k, bias, eps;
+};
+
+// The per-pixel geometry shared by the forward and the backward.
+struct ShadeGeom {
+  bool shadowed;        // a valid sample with z - z_o - bias > 0
+  float V;              // visibility
+  float z, h, a, D;     // receiver
+  float fx, fy;         // bilinear offsets
+  int64_t t00;          // first tap (row-major index into the sun planes)
+  float zs[4], as[4], Ds[4];  // taps (00, 10, 01, 11)
+  float Bs0, Bs1;       // B' s
+};
+
+__device__ __forceinline__ ShadeGeom shade_geom(const ShadeParams& p, const ShadeView& v, int cam, int px, int py,
+                                                int64_t pix) {
+  ShadeGeom g;
+  const float* dF = p.dF ? p.dF + 8 * cam : nullptr;
+  g.Bs0 = 0.0f;
+  g.Bs1 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float b0 = v.B[0][j] + (dF ? dF[j] : 0.0f);
+    const float b1 = v.B[1][j] + (dF ? dF[4 + j] : 0.0f);
+    g.Bs0 = fmaf(b0, v.s[j], g.Bs0);
+    g.Bs1 = fmaf(b1, v.s[j], g.Bs1);
+  }
+  g.shadowed = false;
+  g.V = 1.0f;
+  g.a = v.io.alpha[pix];
+  g.D = v.io.depth[pix];
+  g.z = 0.0f;
+  g.h = 0.0f;
+  g.fx = g.fy = 0.0f;
+  g.t00 = 0;
+  if (g.a >= p.eps) {
+    g.z = g.D / g.a;
+    g.h = v.maxalt - g.z;
+    const float tx = v.S * (((float)px + 0.5f) - g.h * g.Bs0) - 0.5f;
+    const float ty = v.S * (((float)py + 0.5f) - g.h * g.Bs1) - 0.5f;
+    if (tx >= 0.0f && tx < (float)(v.Ws - 1) && ty >= 0.0f && ty < (float)(v.Hs - 1)) {
+      const float fi = floorf(tx), fj = floorf(ty);
+      g.fx = tx - fi;
+      g.fy = ty - fj;
+      g.t00 = (int64_t)fj * v.Ws + (int64_t)fi;
+      const int64_t tap[4] = {g.t00, g.t00 + 1, g.t00 + v.Ws, g.t00 + v.Ws + 1};
+      bool ok = true;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        g.as[t] = v.io.sun_alpha[tap[t]];
+        g.Ds[t] = v.io.sun_depth[tap[t]];
+        ok = ok && g.as[t] >= p.eps;
+        g.zs[t] = g.as[t] >= p.eps ? g.Ds[t] / g.as[t] : 0.0f;
+      }
+      if (ok) {
+        const float zo = (1.0f - g.fx) * (1.0f - g.fy) * g.zs[0] + g.fx * (1.0f - g.fy) * g.zs[1] +
+                         (1.0f - g.fx) * g.fy * g.zs[2] + g.fx * g.fy * g.zs[3];
+        const float delta = g.z - zo - p.bias;
+        if (delta > 0.0f) {
+          g.shadowed = true;
+          g.V = expf(-p.k * delta);
+        }
+      }
+    }
+  }
+  return g;
+}
+
+__global__ void __launch_bounds__(256) shade_fwd_kernel(const __grid_constant__ ShadeParams p) {
+  const int cam = blockIdx.y;
+  const ShadeView& v = p.v[cam];
+  const int64_t hw = (int64_t)v.W * v.H;
+  const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= hw) return;
+  const int py = (int)(pix / v.W), px = (int)(pix - (int64_t)py * v.W);
+  const ShadeGeom g = shade_geom(p, v, cam, px, py, pix);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float La = p.La[3 * cam + c];
+    v.io.image[c * hw + pix] = v.io.rgb[c * hw + pix] * (La + g.V * (1.0f - La));
+  }
+  if (v.io.vis) v.io.vis[pix] = g.V;
+}
+
+__global__ void __launch_bounds__(256) shade_bwd_kernel(const __grid_constant__ ShadeParams p) {
+  __shared__ float red[8][10];
+  const int cam = blockIdx.y;
+  const ShadeView& v = p.v[cam];
+  const int64_t hw = (int64_t)v.W * v.H;
+  const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // per-view sums: d La (3) and d B'[:, 0:3] (6); threads past the view add zeros
+  float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (pix < hw) {
+    const int py = (int)(pix / v.W), px = (int)(pix - (int64_t)py * v.W);
+    const ShadeGeom g = shade_geom(p, v, cam, px, py, pix);
+    float dV = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float La = p.La[3 * cam + c];
+      const float dI = v.io.d_image[c * hw + pix];
+      const float R = v.io.rgb[c * hw + pix];
+      if (v.io.d_rgb) v.io.d_rgb[c * hw + pix] += dI * (La + g.V * (1.0f - La));
+      dV = fmaf(dI * R, 1.0f - La, dV);
+      acc[c] = dI * R * (1.0f - g.V);
+    }
+    if (g.shadowed) {
+      // V = exp(-k delta), delta = z - z_o - bias
+      const float d_delta = -p.k * g.V * dV;
+      const float dzo = -d_delta;
+      const float dzo_dux = (1.0f - g.fy) * (g.zs[1] - g.zs[0]) + g.fy * (g.zs[3] - g.zs[2]);
+      const float dzo_duy = (1.0f - g.fx) * (g.zs[2] - g.zs[0]) + g.fx * (g.zs[3] - g.zs[1]);
+      const float dux = dzo * dzo_dux, duy = dzo * dzo_duy;
+      const float w[4] = {(1.0f - g.fx) * (1.0f - g.fy), g.fx * (1.0f - g.fy), (1.0f - g.fx) * g.fy, g.fx * g.fy};
+      const int64_t tap[4] = {g.t00, g.t00 + 1, g.t00 + v.Ws, g.t00 + v.Ws + 1};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        // z_s = D_s / alpha_s
+        const float dzs = w[t] * dzo;
+        if (v.io.d_sun_depth) atomicAdd(v.io.d_sun_depth + tap[t], dzs / g.as[t]);
+        if (v.io.d_sun_alpha) atomicAdd(v.io.d_sun_alpha + tap[t], -dzs * g.Ds[t] / (g.as[t] * g.as[t]));
+      }
+      // u = S (x - h B' s): du/dh = -S B' s, du/dB'_ij = -S h s_j
+      const float dh = -v.S * (dux * g.Bs0 + duy * g.Bs1);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        acc[3 + j] = -v.S * g.h * v.s[j] * dux;
+        acc[6 + j] = -v.S * g.h * v.s[j] * duy;
+      }
+      // h = max_alt - z, z = D / alpha
+      const float dz = d_delta - dh;
+      if (v.io.d_depth) v.io.d_depth[pix] += dz / g.a;
+      if (v.io.d_alpha) v.io.d_alpha[pix] += -dz * g.D / (g.a * g.a);
+    }
+  }
+  // block sums, one atomic per field and block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < 9; ++f) {
+    float x = acc[f];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp][f] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    float s = 0.0f;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += red[w2][threadIdx.x];
+    const int f = threadIdx.x;
+    if (s != 0.0f) {
+      if (f < 3) {
+        if (p.d_La) atomicAdd(p.d_La + 3 * cam + f, s);
+      } else if (p.d_dF) {
+        const int i = (f - 3) / 3, j = (f - 3) % 3;
+        atomicAdd(p.d_dF + 8 * cam + 4 * i + j, s);
+      }
+    }
+  }
+}
+
+namespace {
+
+bool fin(float x) { return std::isfinite(x); }
+
+ss_status fill_shade(ShadeParams& p, const ss_camera* cams, int32_t n_cams, const float* dF, const float* La,
+                     const ss_shade_opts* o, const ss_shade_io* io, bool bwd) {
+  if (!cams || !io || !o || !La || n_cams < 1 || n_cams > kMaxCams) return SS_ERR_INVALID_ARG;
+  if (!fin(o->esm_k) || !(o->esm_k >= 0.0f) || !fin(o->esm_bias) || !fin(o->alpha_eps) || !(o->alpha_eps > 0.0f))
+    return SS_ERR_INVALID_ARG;
+  std::memset(&p, 0, sizeof(p));
+  for (int c = 0; c < n_cams; ++c) {
+    const ss_camera& k = cams[c];
+    const ss_shade_io& q = io[c];
+    if (k.width < 1 || k.height < 1 || k.width > 16384 || k.height > 16384) return SS_ERR_INVALID_ARG;
+    if (k.shadow_w < 2 || k.shadow_h < 2 || k.shadow_w > 16384 || k.shadow_h > 16384) return SS_ERR_INVALID_ARG;
+    if (!fin(k.sun_phi) || !fin(k.sun_theta) || !(k.sun_theta > 0.0f) || !(k.sun_theta <= 1.5707964f))
+      return SS_ERR_INVALID_ARG;
+    if (!fin(k.shadow_scale) || !(k.shadow_scale > 0.0f) || !fin(k.max_alt)) return SS_ERR_INVALID_ARG;
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 4; ++j)
+        if (!fin(k.F_xy[i][j])) return SS_ERR_INVALID_ARG;
+    if (!q.rgb || !q.depth || !q.alpha || !q.sun_depth || !q.sun_alpha) return SS_ERR_INVALID_ARG;
+    if (!bwd && !q.image) return SS_ERR_INVALID_ARG;
+    if (bwd && !q.d_image) return SS_ERR_INVALID_ARG;
+    ShadeView& v = p.v[c];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j) v.B[i][j] = k.F_xy[i][j];
+    const double ct = 1.0 / std::tan((double)k.sun_theta);
+    v.s[0] = (float)(std::cos((double)k.sun_phi) * ct);
+    v.s[1] = (float)(std::sin((double)k.sun_phi) * ct);
+    v.s[2] = 1.0f;
+    v.S = k.shadow_scale;
+    v.maxalt = k.max_alt;
+    v.W = k.width;
+    v.H = k.height;
+    v.Ws = k.shadow_w;
+    v.Hs = k.shadow_h;
+    v.io = q;
+  }
+  p.dF = dF;
+  p.La = La;
+  p.k = o->esm_k;
+  p.bias = o->esm_bias;
+  p.eps = o->alpha_eps;
+  return SS_OK;
+}
+
+dim3 shade_grid(const ss_camera* cams, int32_t n_cams) {
+  int64_t most = 0;
+  for (int c = 0; c < n_cams; ++c) most = std::max(most, (int64_t)cams[c].width * cams[c].height);
+  return dim3((unsigned)((most + 255) / 256), (unsigned)n_cams);
+}
+
+}  // namespace
+}  // namespace ss
+
+using namespace ss;
+
+extern "C" {
+
+void ss_default_shade_opts(ss_shade_opts* o) {
+  if (!o) return;
+  o->esm_k = 2000.0f;
+  o->esm_bias = 0.0f;
+  o->alpha_eps = 1e-3f;
+}
+
+ss_status ss_shade_fwd(const ss_camera* cams, int32_t n_cams, const float* dF, const float* La,
+                       const ss_shade_opts* opts, const ss_shade_io* io, ss_stream_t stream) {
+  ShadeParams p;
+  ss_status e = fill_shade(p, cams, n_cams, dF, La, opts, io, false);
+  if (e != SS_OK) return e;
+  count_launch();
+  shade_fwd_kernel<<<shade_grid(cams, n_cams), 256, 0, (cudaStream_t)stream>>>(p);
+  return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+}
+
+ss_status ss_shade_bwd(const ss_camera* cams, int32_t n_cams, const float* dF, const float* La,
+                       const ss_shade_opts* opts, const ss_shade_io* io, float* d_La, float* d_dF,
+                       ss_stream_t stream) {
+  ShadeParams p;
+  ss_status e = fill_shade(p, cams, n_cams, dF, La, opts, io, true);
+  if (e != SS_OK) return e;
+  p.d_La = d_La;
+  p.d_dF = d_dF;
+  count_launch();
+  shade_bwd_kernel<<<shade_grid(cams, n_cams), 256, 0, (cudaStream_t)stream>>>(p);
+  return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+"""Sun visibility and image formation (K7) against the FP64 shading oracle, through the C ABI.
+
+The rasterizer renders a view and its sun view on the GPU; the shading kernels and the oracle
+then take the same planes (widened exactly to float64 for the oracle), so the comparison isolates
+the shading arithmetic.  Pixels whose decisions sit within FP32 reach of a threshold are
+excluded (and counted)."""
+import numpy as np
+import pytest
+import torch
+
+import scenegen
+from oracle import shade as S
+from paper_2606_28581_gb300 import _lib as L
+from paper_2606_28581_gb300.frame import Frame
+from tests.gpu_util import DeviceScene, grad_close, to_np
+
+pytestmark = pytest.mark.gpu
+
+K, EPS = 60.0, 1e-3
+
+
+def _scene(seed):
+    return scenegen.make_scene(n=6000, extent_m=80.0, seed=seed, views=[
+        dict(width=120, height=90, off_nadir=20.0, delta=True, color_noise=0.02),
+        dict(width=96, height=80, off_nadir=12.0, delta=True, color_noise=0.02)])
+
+
+def _render(scene):
+    ds = DeviceScene(scene)
+    frame = Frame(scene.cameras, L.SS_PASS_MAIN | L.SS_PASS_SUN)
+    out = frame.forward(ds.splats, ds.dF, ds.color)
+    torch.cuda.synchronize()
+    return ds, frame, out
+
+
+def _views(frame, out, extra):
+    V = len(frame.targets) // 2
+    views = []
+    for c in range(V):
+        v = dict(rgb=out.rgb[c], depth=out.depth[c], alpha=out.alpha[c], sun_depth=out.depth[V + c],
+                 sun_alpha=out.alpha[V + c])
+        v.update(extra[c])
+        views.append(v)
+    return views
+
+
+def _margin_keep(scene, planes, c, k, bias):
+    m, frac = S.shade_margin(planes["depth"], planes["alpha"], planes["sun_depth"], planes["sun_alpha"],
+                             scene.cameras[c], k, bias, EPS)
+    return m > 1e-3
+
+
+@pytest.mark.parametrize("bias", [0.0, 0.01])
+def test_shade_forward_matches_oracle(bias):
+    scene = _scene(seed=21)
+    ds, frame, out = _render(scene)
+    V = len(scene.cameras)
+    La = torch.tensor([[0.2, 0.3, 0.4], [0.5, 0.35, 0.25]], device="cuda")
+    imgs = [torch.empty(3, c.height, c.width, device="cuda") for c in scene.cameras]
+    vis = [torch.empty(c.height, c.width, device="cuda") for c in scene.cameras]
+    views = _views(frame, out, [dict(image=imgs[c], vis=vis[c]) for c in range(V)])
+    cams = L.make_cameras(scene.cameras)
+    opts = L.default_shade_opts(esm_k=K, esm_bias=bias, alpha_eps=EPS)
+    L.shade_fwd(cams, V, ds.dF, La, opts, L.shade_io_array(views))
+    torch.cuda.synchronize()
+    shadowed = 0
+    for c in range(V):
+        p = {k: to_np(views[c][k]) for k in ("rgb", "depth", "alpha", "sun_depth", "sun_alpha")}
+        I, Vo = S.shade_forward(p["rgb"], p["depth"], p["alpha"], p["sun_depth"], p["sun_alpha"], scene.cameras[c],
+                                to_np(La[c]), K, bias, EPS, dF=to_np(ds.dF[c]))
+        keep = _margin_keep(scene, p, c, K, bias)
+        assert keep.mean() > 0.98
+        assert np.abs(to_np(vis[c]) - Vo)[keep].max() <= 1e-5
+        assert np.abs(to_np(imgs[c]) - I)[:, keep].max() <= 1e-5
+        shadowed += int((Vo[keep] < 0.99).sum())
+    assert shadowed > 100  # the scene casts shadows
+
+
+def test_shade_backward_matches_oracle():
+    scene = _scene(seed=22)
+    ds, frame, out = _render(scene)
+    V = len(scene.cameras)
+    rng = np.random.default_rng(3)
+    La = torch.tensor([[0.3, 0.2, 0.4], [0.45, 0.5, 0.3]], device="cuda")
+    zeros = lambda t: torch.zeros_like(t)
+    d_img, extra, keeps = [], [], []
+    for c in range(V):
+        cam = scene.cameras[c]
+        p = {k: to_np(t) for k, t in (("depth", out.depth[c]), ("alpha", out.alpha[c]), ("sun_depth", out.depth[V + c]),
+                                       ("sun_alpha", out.alpha[V + c]))}
+        keep = _margin_keep(scene, p, c, K, 0.0)
+        keeps.append(keep)
+        dI = rng.normal(size=(3, cam.height, cam.width)) * keep
+        d_img.append(torch.from_numpy(dI.astype(np.float32)).cuda())
+        extra.append(dict(image=torch.empty(3, cam.height, cam.width, device="cuda"), d_image=d_img[c],
+                          d_rgb=zeros(out.rgb[c]), d_depth=zeros(out.depth[c]), d_alpha=zeros(out.alpha[c]),
+                          d_sun_depth=zeros(out.depth[V + c]), d_sun_alpha=zeros(out.alpha[V + c])))
+    views = _views(frame, out, extra)
+    cams = L.make_cameras(scene.cameras)
+    opts = L.default_shade_opts(esm_k=K, esm_bias=0.0, alpha_eps=EPS)
+    d_La = torch.zeros(V, 3, device="cuda")
+    d_dF = torch.zeros(V, 2, 4, device="cuda")
+    L.shade_bwd(cams, V, ds.dF, La, opts, L.shade_io_array(views), d_La, d_dF)
+    torch.cuda.synchronize()
+    for c in range(V):
+        v = views[c]
+        p = {k: to_np(v[k]) for k in ("rgb", "depth", "alpha", "sun_depth", "sun_alpha")}
+        g = S.shade_backward(to_np(d_img[c]), p["rgb"], p["depth"], p["alpha"], p["sun_depth"], p["sun_alpha"],
+                             scene.cameras[c], to_np(La[c]), K, 0.0, EPS, dF=to_np(ds.dF[c]))
+        for key in ("rgb", "depth", "alpha", "sun_depth", "sun_alpha"):
+            grad_close(to_np(v["d_" + key]), g[key], name=f"view {c} d_{key}")
+        grad_close(to_np(d_La[c]), g["La"], name=f"view {c} d_La")
+        grad_close(to_np(d_dF[c]), g["dF"], name=f"view {c} d_dF")
+    assert any(np.abs(to_np(views[c]["d_sun_depth"])).max() > 0 for c in range(V))  # shadows carry gradient
+
+
+def test_shade_rejects_bad_arguments():
+    scene = _scene(seed=23)
+    cams = L.make_cameras(scene.cameras)
+    La = torch.zeros(2, 3, device="cuda")
+    opts = L.default_shade_opts()
+    io = L.shade_io_array([{}, {}])  # no planes
+    assert L.load().ss_shade_fwd(cams, 2, None, L.ptr(La), opts, io, None) == L.SS_ERR_INVALID_ARG
+    bad = L.default_shade_opts(alpha_eps=0.0)
+    assert L.load().ss_shade_fwd(cams, 2, None, L.ptr(La), bad, io, None) == L.SS_ERR_INVALID_ARG
