@@ -1,4 +1,4 @@
-"""torch.autograd.Function over the CUDA rasterizer (training form a).
+"""torch.autograd.Function over the CUDA rasterizer (training form a) and the shading (K7).
 
 Forward runs project -> bin/sort -> rasterize in the CUDA library; backward runs
 the hand-written adjoint (ss_rasterize_bwd).  Per pixel only T_final and the end
@@ -91,3 +91,61 @@ def render(frame: Frame, means, scales, quats, opacity, rgb, dF=None, color=None
             res.append(dict(depth=flat[i], alpha=flat[i + 1]))
             i += 2
     return res
+
+
+class _ShadeFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, frame: Frame, opts, dF, La, *planes):
+        V = frame.n_cams
+        dev = La.device
+        dFc = None if dF is None else dF.detach().float().contiguous()
+        Lac = La.detach().float().contiguous()
+        views, images, vis = [], [], []
+        for c in range(V):
+            rgb, depth, alpha, sd, sa = [t.detach().float().contiguous() for t in planes[5 * c:5 * c + 5]]
+            images.append(torch.empty_like(rgb))
+            vis.append(torch.empty_like(depth))
+            views.append(dict(rgb=rgb, depth=depth, alpha=alpha, sun_depth=sd, sun_alpha=sa, image=images[c],
+                              vis=vis[c]))
+        L.shade_fwd(frame.cams, V, dFc, Lac, opts, L.shade_io_array(views))
+        ctx.frame, ctx.opts, ctx.views, ctx.dF, ctx.La = frame, opts, views, dFc, Lac
+        ctx.has_dF = dF is not None
+        ctx.mark_non_differentiable(*vis)
+        return tuple(images) + tuple(vis)
+
+    @staticmethod
+    def backward(ctx, *gouts):
+        frame = ctx.frame
+        V = frame.n_cams
+        views, d_planes = [], []
+        for c in range(V):
+            v = dict(ctx.views[c])
+            g = gouts[c]
+            v["d_image"] = torch.zeros_like(v["rgb"]) if g is None else g.float().contiguous()
+            d = dict(d_rgb=torch.zeros_like(v["rgb"]), d_depth=torch.zeros_like(v["depth"]),
+                     d_alpha=torch.zeros_like(v["alpha"]), d_sun_depth=torch.zeros_like(v["sun_depth"]),
+                     d_sun_alpha=torch.zeros_like(v["sun_alpha"]))
+            v.update(d)
+            views.append(v)
+            d_planes += [d["d_rgb"], d["d_depth"], d["d_alpha"], d["d_sun_depth"], d["d_sun_alpha"]]
+        d_La = torch.zeros_like(ctx.La)
+        d_dF = torch.zeros(V, 2, 4, device=ctx.La.device) if ctx.has_dF else None
+        L.shade_bwd(frame.cams, V, ctx.dF, ctx.La, ctx.opts, L.shade_io_array(views), d_La, d_dF)
+        return (None, None, d_dF, d_La, *d_planes)
+
+
+def shade(frame: Frame, targets: Sequence[dict], La, dF=None, opts=None) -> List[dict]:
+    """Differentiable sun visibility and image formation (Sec. 3.1 Eq. image_formation) of every
+    main view of ``frame`` (rendered with both passes) from the dicts ``render`` returned:
+    I = (C A + c)(V + (1 - V) L_a).  La (V, 3) ambient light, dF (V, 2, 4) the camera deltas the
+    render used (the sun position depends on them).  Returns one dict per view: image (3, H, W)
+    and vis (H, W, not differentiable)."""
+    V = frame.n_cams
+    if len(frame.targets) != 2 * V:
+        raise ValueError("shade needs a frame rendered with the main and the sun pass")
+    planes = []
+    for c in range(V):
+        m, s = targets[c], targets[V + c]
+        planes += [m["rgb"], m["depth"], m["alpha"], s["depth"], s["alpha"]]
+    flat = _ShadeFn.apply(frame, opts if opts is not None else L.default_shade_opts(), dF, La, *planes)
+    return [dict(image=flat[c], vis=flat[V + c]) for c in range(V)]

@@ -73,14 +73,14 @@ def check_forward(gpu: dict, ora: dict, sun: bool, tol: float, margin: float = M
     return errs, excluded
 
 
-def grad_close(g: np.ndarray, ref: np.ndarray, rtol=GRAD_TOL, name=""):
-    """max|g - ref| <= rtol max|ref| and per element |g - ref| <= rtol (|ref| + 1e-3 max|ref|)."""
+def grad_close(g: np.ndarray, ref: np.ndarray, rtol=GRAD_TOL, name="", floor=1e-3):
+    """max|g - ref| <= rtol max|ref| and per element |g - ref| <= rtol (|ref| + floor max|ref|)."""
     scale = float(np.abs(ref).max())
     if scale == 0.0:
         assert float(np.abs(g).max()) == 0.0, name
         return 0.0
     d = np.abs(g - ref)
     assert d.max() <= rtol * scale, f"{name}: max err {d.max():.3e} vs {rtol * scale:.3e}"
-    bad = d > rtol * (np.abs(ref) + 1e-3 * scale)
+    bad = d > rtol * (np.abs(ref) + floor * scale)
     assert not bad.any(), f"{name}: {bad.sum()} elements outside the per-element bound; worst {d.max():.3e}"
     return float(d.max() / scale)
