@@ -237,6 +237,63 @@ def profiles_traffic(kernel: str):
         return None
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def measure_shade(torch, step, reps: int):
+    """Forward and backward of the shading (K7) over every main view of the step, on the step's
+    rasterized planes, with CUDA events; HBM roofline from the algorithmic bytes per main pixel
+    (forward: rgb, depth, alpha read, image written = 32 B; backward: d_image, rgb, depth, alpha
+    read, d_rgb read and written = 56 B) plus 8 B per sun pixel.  Data-dependent traffic (the
+    shadowed pixels' depth and alpha gradients, the sun-view atomics) is not counted."""
+    from paper_2606_28581_gb300 import _lib as L
+    f, out = step.frame, step.out
+    V = f.n_cams
+    if len(f.targets) != 2 * V:
+        return None
+    dev = out.rgb[0].device
+    La = torch.full((V, 3), 0.3, device=dev)
+    views_f, views_b = [], []
+    main_px = sun_px = 0
+    for c in range(V):
+        base = dict(rgb=out.rgb[c], depth=out.depth[c], alpha=out.alpha[c], sun_depth=out.depth[V + c],
+                    sun_alpha=out.alpha[V + c])
+        main_px += out.depth[c].numel()
+        sun_px += out.depth[V + c].numel()
+        views_f.append(dict(base, image=torch.empty_like(out.rgb[c])))
+        views_b.append(dict(base, d_image=torch.randn_like(out.rgb[c]), d_rgb=torch.zeros_like(out.rgb[c]),
+                            d_depth=torch.zeros_like(out.depth[c]), d_alpha=torch.zeros_like(out.alpha[c]),
+                            d_sun_depth=torch.zeros_like(out.depth[V + c]),
+                            d_sun_alpha=torch.zeros_like(out.alpha[V + c])))
+    io_f, io_b = L.shade_io_array(views_f), L.shade_io_array(views_b)
+    opts = L.default_shade_opts()
+    d_La = torch.zeros(V, 3, device=dev)
+    d_dF = torch.zeros(V, 2, 4, device=dev)
+    dF = step.dF
+    fwd = lambda: L.shade_fwd(f.cams, V, dF, La, opts, io_f)
+    bwd = lambda: L.shade_bwd(f.cams, V, dF, La, opts, io_b, d_La, d_dF)
+    fwd(); bwd()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    acc = np.zeros(2)
+    for _ in range(reps):
+        ev[0].record(); fwd(); ev[1].record(); bwd(); ev[2].record()
+        torch.cuda.synchronize()
+        acc += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])]
+    fms, bms = acc / reps
+    peak, basis = hbm_peak_gbs()
+    bf, bb = main_px * 32 + sun_px * 8, main_px * 56 + sun_px * 8
+    return {"bound": "hbm", "fwd_ms": float(fms), "bwd_ms": float(bms), "bytes_fwd": int(bf), "bytes_bwd": int(bb),
+            "fwd_gbs": bf / (fms * 1e-3) / 1e9, "bwd_gbs": bb / (bms * 1e-3) / 1e9, "peak_gbs": peak,
+            "peak_basis": basis, "fwd_frac": bf / (fms * 1e-3) / 1e9 / peak,
+            "bwd_frac": bb / (bms * 1e-3) / 1e9 / peak}
+
+
 # ------------------------------------------------------------------------------ oracle arm
 def oracle_sample(scene, seconds_target: float, seed: int = 0):
     """Time the FP64 oracle (forward + backward) on crops of view 0, growing the crop until
@@ -401,6 +458,9 @@ def run_ours(args, dist):
                 "frac_at_max_clock": achieved / (sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12),
                 "phase_ms": phase_ms}
 
+    # ---- sun visibility and image formation (K7) on the step's outputs, timed alone
+    shade = measure_shade(torch, step, k_steps)
+
     # ---- plain FP32 single-view arm: the same scene as one plain call sequence per view
     plain = None
     if not args.no_plain:
@@ -503,6 +563,7 @@ def run_ours(args, dist):
                 "roofline": roofline, "cpu_baseline": cpu, "plain_fp32": plain,
                 "batched_over_plain": (value / dist.world) / plain["value"] if plain else None,
                 "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+                "shade": shade,
                 "steps_per_s": 1e3 / ms_max, "peak_hbm_gb": peak_hbm_gb,
                 "device": {"sms": sms, "arch": arch, "name": torch.cuda.get_device_name()}}
         print(json.dumps(line), flush=True)
