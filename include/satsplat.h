@@ -320,6 +320,33 @@ ss_status ss_shade_bwd(const ss_camera* cams, int32_t n_cams, const float* dF, c
                        const ss_shade_opts* opts, const ss_shade_io* io, float* d_La, float* d_dF,
                        ss_stream_t stream);
 
+/* Depth-gradient surface normal (K8), Sec. 3.2 Eq. surface_normal: the world-space normal
+ * N = (grad_x p_s x grad_y p_s) / |grad_x p_s x grad_y p_s| of the point map p_s back-projected
+ * from a main view's rendered depth, for the normal-consistency regulariser (the rendered
+ * normal against N).  Per pixel x = (i + 0.5, j + 0.5):
+ *   z = D / alpha, h = max_alt - z, p_s = (X, Y, h) with B'[:, 0:2] (X, Y) = x - b' - B'[:, 2] h
+ *   grad_x p_s = p_s(i + 1, j) - p_s(i - 1, j), grad_y p_s = p_s(i, j + 1) - p_s(i, j - 1)
+ * N is multiplied by sign(det B'[:, 0:2]) so that flat ground gets (0, 0, 1).  A border pixel, or
+ * one whose own or a neighbour's alpha is below alpha_eps, gets N = 0 (and passes no gradient). */
+typedef struct {
+  const float* depth;    /* the main view's rasterize_fwd depth [H][W] */
+  const float* alpha;    /* and alpha [H][W] */
+  float* normal;         /* forward out: N [3][H][W] */
+  const float* d_normal; /* backward in: dL/dN [3][H][W] */
+  float* d_depth;        /* backward: ADDED to (atomically), the view's upstream */
+  float* d_alpha;        /* backward: ADDED to (atomically) */
+} ss_dnormal_io;
+
+/* cams: HOST array; dF: DEVICE [n_cams][2][4] or NULL; io: HOST array of n_cams.
+ * Errors: SS_ERR_INVALID_ARG. */
+ss_status ss_depth_normal_fwd(const ss_camera* cams, int32_t n_cams, const float* dF, float alpha_eps,
+                              const ss_dnormal_io* io, ss_stream_t stream);
+
+/* Adjoint of ss_depth_normal_fwd for io[v].d_normal: adds into io[v].d_depth / d_alpha (either may
+ * be NULL) and into d_dF (DEVICE [n_cams][2][4], accumulated, or NULL). */
+ss_status ss_depth_normal_bwd(const ss_camera* cams, int32_t n_cams, const float* dF, float alpha_eps,
+                              const ss_dnormal_io* io, float* d_dF, ss_stream_t stream);
+
 /* Status block of a frame's workspace.  SYNCHRONISES the stream.
  *   needed:    intersections the last ss_bin_and_sort needed
  *   nonfinite: splats culled for non-finite values by the last projection

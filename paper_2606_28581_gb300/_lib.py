@@ -60,6 +60,10 @@ class ss_shade_io(ctypes.Structure):
                 ("d_sun_depth", P), ("d_sun_alpha", P)]
 
 
+class ss_dnormal_io(ctypes.Structure):
+    _fields_ = [("depth", P), ("alpha", P), ("normal", P), ("d_normal", P), ("d_depth", P), ("d_alpha", P)]
+
+
 class ss_splat_grads(ctypes.Structure):
     _fields_ = [("means", P), ("scales", P), ("quats", P), ("opacity", P), ("rgb", P),
                 ("n_pad", ctypes.c_int64)]
@@ -68,7 +72,8 @@ class ss_splat_grads(ctypes.Structure):
 EXPORTS = ["ss_default_opts", "ss_status_string", "ss_workspace_size", "ss_project_splats",
            "ss_bin_and_sort", "ss_rasterize_fwd", "ss_rasterize_bwd", "ss_project_bwd", "ss_shadow_depth",
            "ss_frame_status", "ss_device_info", "ss_kernel_launches", "ss_render_fwd_noalloc",
-           "ss_noalloc_scratch_bytes", "ss_default_shade_opts", "ss_shade_fwd", "ss_shade_bwd"]
+           "ss_noalloc_scratch_bytes", "ss_default_shade_opts", "ss_shade_fwd", "ss_shade_bwd",
+           "ss_depth_normal_fwd", "ss_depth_normal_bwd"]
 
 _lock = threading.Lock()
 _lib = None
@@ -119,6 +124,9 @@ def load(path: Optional[str] = None):
         L.ss_default_shade_opts.restype = None
         L.ss_shade_fwd.argtypes = [PC, I32, P, P, PSO, PSI, P]
         L.ss_shade_bwd.argtypes = [PC, I32, P, P, PSO, PSI, P, P, P]
+        PNI = ctypes.POINTER(ss_dnormal_io)
+        L.ss_depth_normal_fwd.argtypes = [PC, I32, P, ctypes.c_float, PNI, P]
+        L.ss_depth_normal_bwd.argtypes = [PC, I32, P, ctypes.c_float, PNI, P, P]
         for name in EXPORTS:
             if name not in ("ss_default_opts", "ss_status_string", "ss_device_info", "ss_kernel_launches",
                             "ss_noalloc_scratch_bytes", "ss_default_shade_opts"):
@@ -307,3 +315,22 @@ def shade_fwd(cams, n_cams: int, dF, La, opts: ss_shade_opts, io, stream=None) -
 def shade_bwd(cams, n_cams: int, dF, La, opts: ss_shade_opts, io, d_La=None, d_dF=None, stream=None) -> None:
     _check(load().ss_shade_bwd(cams, n_cams, ptr(dF), ptr(La), ctypes.byref(opts), io, ptr(d_La), ptr(d_dF),
                                stream_ptr(stream)), "ss_shade_bwd")
+
+
+# ------------------------------------------------------------------------------ depth normal (K8)
+def dnormal_io_array(views: Sequence[dict]) -> ctypes.Array:
+    arr = (ss_dnormal_io * len(views))()
+    for i, v in enumerate(views):
+        for name, _ in ss_dnormal_io._fields_:
+            setattr(arr[i], name, ptr(v.get(name)))
+    return arr
+
+
+def depth_normal_fwd(cams, n_cams: int, dF, alpha_eps: float, io, stream=None) -> None:
+    _check(load().ss_depth_normal_fwd(cams, n_cams, ptr(dF), float(alpha_eps), io, stream_ptr(stream)),
+           "ss_depth_normal_fwd")
+
+
+def depth_normal_bwd(cams, n_cams: int, dF, alpha_eps: float, io, d_dF=None, stream=None) -> None:
+    _check(load().ss_depth_normal_bwd(cams, n_cams, ptr(dF), float(alpha_eps), io, ptr(d_dF), stream_ptr(stream)),
+           "ss_depth_normal_bwd")

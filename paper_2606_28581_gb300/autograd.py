@@ -149,3 +149,47 @@ def shade(frame: Frame, targets: Sequence[dict], La, dF=None, opts=None) -> List
         planes += [m["rgb"], m["depth"], m["alpha"], s["depth"], s["alpha"]]
     flat = _ShadeFn.apply(frame, opts if opts is not None else L.default_shade_opts(), dF, La, *planes)
     return [dict(image=flat[c], vis=flat[V + c]) for c in range(V)]
+
+
+class _DepthNormalFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, frame: Frame, alpha_eps: float, dF, *planes):
+        V = frame.n_cams
+        dFc = None if dF is None else dF.detach().float().contiguous()
+        views, normals = [], []
+        for c in range(V):
+            depth, alpha = [t.detach().float().contiguous() for t in planes[2 * c:2 * c + 2]]
+            normals.append(torch.empty(3, *depth.shape, device=depth.device))
+            views.append(dict(depth=depth, alpha=alpha, normal=normals[c]))
+        L.depth_normal_fwd(frame.cams, V, dFc, alpha_eps, L.dnormal_io_array(views))
+        ctx.frame, ctx.eps, ctx.views, ctx.dF, ctx.has_dF = frame, alpha_eps, views, dFc, dF is not None
+        return tuple(normals)
+
+    @staticmethod
+    def backward(ctx, *gouts):
+        frame = ctx.frame
+        V = frame.n_cams
+        views, d_planes = [], []
+        for c in range(V):
+            v = dict(ctx.views[c])
+            g = gouts[c]
+            v["d_normal"] = torch.zeros_like(v["normal"]) if g is None else g.float().contiguous()
+            v["d_depth"] = torch.zeros_like(v["depth"])
+            v["d_alpha"] = torch.zeros_like(v["alpha"])
+            views.append(v)
+            d_planes += [v["d_depth"], v["d_alpha"]]
+        d_dF = torch.zeros(V, 2, 4, device=views[0]["depth"].device) if ctx.has_dF else None
+        L.depth_normal_bwd(frame.cams, V, ctx.dF, ctx.eps, L.dnormal_io_array(views), d_dF)
+        return (None, None, d_dF, *d_planes)
+
+
+def depth_normal(frame: Frame, targets: Sequence[dict], dF=None, alpha_eps: float = 1e-3) -> List[torch.Tensor]:
+    """Differentiable depth-gradient surface normal N (3, H, W) of every main view of ``frame``
+    (Sec. 3.2 Eq. surface_normal) from the dicts ``render`` returned; with the rendered normal it
+    gives the normal-consistency regulariser, e.g. (alpha - (normal * N).sum(0)).mean().  dF (V, 2, 4)
+    the camera deltas the render used."""
+    V = frame.n_cams
+    planes = []
+    for c in range(V):
+        planes += [targets[c]["depth"], targets[c]["alpha"]]
+    return list(_DepthNormalFn.apply(frame, float(alpha_eps), dF, *planes))
