@@ -294,6 +294,46 @@ def measure_shade(torch, step, reps: int):
             "bwd_frac": bb / (bms * 1e-3) / 1e9 / peak}
 
 
+def measure_depth_normal(torch, step, reps: int):
+    """Forward and backward of the depth-gradient normal (K8) over every main view of the step;
+    HBM roofline from the algorithmic bytes per main pixel (forward: depth and alpha read, N
+    written = 20 B; backward: dN, depth, alpha read and the depth and alpha gradients read and
+    written = 36 B; the neighbours' reads and the atomics' re-reads hit L1/L2)."""
+    from paper_2606_28581_gb300 import _lib as L
+    f, out = step.frame, step.out
+    V = f.n_cams
+    main = [i for i, t in enumerate(f.targets) if not t.sun]
+    if len(main) != V:
+        return None
+    views_f, views_b = [], []
+    px = 0
+    for c in main:
+        d, a = out.depth[c], out.alpha[c]
+        px += d.numel()
+        views_f.append(dict(depth=d, alpha=a, normal=torch.empty(3, *d.shape, device=d.device)))
+        views_b.append(dict(depth=d, alpha=a, d_normal=torch.randn(3, *d.shape, device=d.device),
+                            d_depth=torch.zeros_like(d), d_alpha=torch.zeros_like(a)))
+    io_f, io_b = L.dnormal_io_array(views_f), L.dnormal_io_array(views_b)
+    d_dF = torch.zeros(V, 2, 4, device=out.depth[0].device)
+    fwd = lambda: L.depth_normal_fwd(f.cams, V, step.dF, 1e-3, io_f)
+    bwd = lambda: L.depth_normal_bwd(f.cams, V, step.dF, 1e-3, io_b, d_dF)
+    fwd(); bwd()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    acc = np.zeros(2)
+    for _ in range(reps):
+        ev[0].record(); fwd(); ev[1].record(); bwd(); ev[2].record()
+        torch.cuda.synchronize()
+        acc += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])]
+    fms, bms = acc / reps
+    peak, basis = hbm_peak_gbs()
+    bf, bb = px * 20, px * 36
+    return {"bound": "hbm", "fwd_ms": float(fms), "bwd_ms": float(bms), "bytes_fwd": int(bf), "bytes_bwd": int(bb),
+            "fwd_gbs": bf / (fms * 1e-3) / 1e9, "bwd_gbs": bb / (bms * 1e-3) / 1e9, "peak_gbs": peak,
+            "peak_basis": basis, "fwd_frac": bf / (fms * 1e-3) / 1e9 / peak,
+            "bwd_frac": bb / (bms * 1e-3) / 1e9 / peak}
+
+
 # ------------------------------------------------------------------------------ oracle arm
 def oracle_sample(scene, seconds_target: float, seed: int = 0):
     """Time the FP64 oracle (forward + backward) on crops of view 0, growing the crop until
@@ -458,8 +498,9 @@ def run_ours(args, dist):
                 "frac_at_max_clock": achieved / (sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12),
                 "phase_ms": phase_ms}
 
-    # ---- sun visibility and image formation (K7) on the step's outputs, timed alone
+    # ---- sun visibility and image formation (K7), depth-gradient normals (K8), timed alone
     shade = measure_shade(torch, step, k_steps)
+    dnormal = measure_depth_normal(torch, step, k_steps)
 
     # ---- plain FP32 single-view arm: the same scene as one plain call sequence per view
     plain = None
@@ -563,7 +604,7 @@ def run_ours(args, dist):
                 "roofline": roofline, "cpu_baseline": cpu, "plain_fp32": plain,
                 "batched_over_plain": (value / dist.world) / plain["value"] if plain else None,
                 "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-                "shade": shade,
+                "shade": shade, "depth_normal": dnormal,
                 "steps_per_s": 1e3 / ms_max, "peak_hbm_gb": peak_hbm_gb,
                 "device": {"sms": sms, "arch": arch, "name": torch.cuda.get_device_name()}}
         print(json.dumps(line), flush=True)

@@ -1,12 +1,13 @@
 // Depth-gradient surface normal (K8), Sec. 3.2 Eq. surface_normal, and its adjoint.
 //
-// One thread per main-view pixel, every view in one launch (blockIdx.y = view).  The point map
+// One block per 32 x 8 tile of a main view, one thread per pixel, every view in one launch
+// (blockIdx.y = view).  The point map
 // p_s = (X, Y, h) is affine in the pixel and in the height, so its central differences are
 //   grad_x p_s = a1 + (h(i+1) - h(i-1)) G,  grad_y p_s = a2 + (h(j+1) - h(j-1)) G,
 // with per-view a1 = (2 A^-1 e1, 0), a2 = (2 A^-1 e2, 0), G = (-A^-1 B'[:, 2], 1), A = B'[:, 0:2].
 // Forming them this way never subtracts two absolute world positions (which FP32 would round at
-// ~1e-7 of the scene size, far above a pixel's footprint).  Reads 5 depth and 5 alpha values per
-// pixel (neighbours from L1/L2), writes 3: HBM-bound.
+// ~1e-7 of the scene size, far above a pixel's footprint).  Per pixel the forward reads depth and
+// alpha once (a halo from L2) and writes 3 values: HBM-bound.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -59,55 +60,57 @@ __device__ __forceinline__ NormalCam normal_cam(const NormalParams& p, const Nor
   return c;
 }
 
-// The normal's inputs at pixel (px, py): whether it is defined, and the two height differences.
-struct NormalPix {
-  bool ok;
-  float dhx, dhy;   // h(i+1) - h(i-1), h(j+1) - h(j-1)
-  float ux, uy, uz, vx, vy, vz;  // grad_x p_s, grad_y p_s
-};
+// Tiles of kNX x kNY pixels per block (one thread each).  The alpha-normalised depth z of the
+// tile and a halo is staged once in shared memory (NaN where there is no surface or no pixel), so
+// each pixel's z is formed once instead of once per neighbour that needs it.
+constexpr int kNX = 32, kNY = 8;
 
-__device__ __forceinline__ NormalPix normal_pix(const NormalParams& p, const NormalView& v, const NormalCam& c,
-                                                int px, int py) {
-  NormalPix r;
-  r.ok = false;
-  r.dhx = r.dhy = 0.0f;
-  if (px < 1 || py < 1 || px >= v.W - 1 || py >= v.H - 1) return r;
-  const int64_t W = v.W;
-  const int64_t i = (int64_t)py * W + px;
-  const int64_t nb[5] = {i, i + 1, i - 1, i + W, i - W};
-  float z[5];
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const float a = v.io.alpha[nb[k]];
-    ok = ok && a >= p.eps;
-    z[k] = a >= p.eps ? v.io.depth[nb[k]] / a : 0.0f;
-  }
-  if (!ok) return r;
-  r.ok = true;
-  // h = max_alt - z: the differences of h are the negated differences of z
-  r.dhx = z[2] - z[1];
-  r.dhy = z[4] - z[3];
-  r.ux = 2.0f * c.Ai[0][0] + r.dhx * c.Gx;
-  r.uy = 2.0f * c.Ai[1][0] + r.dhx * c.Gy;
-  r.uz = r.dhx;
-  r.vx = 2.0f * c.Ai[0][1] + r.dhy * c.Gx;
-  r.vy = 2.0f * c.Ai[1][1] + r.dhy * c.Gy;
-  r.vz = r.dhy;
+__device__ __forceinline__ float z_at(const NormalParams& p, const NormalView& v, int x, int y) {
+  if (x < 0 || y < 0 || x >= v.W || y >= v.H) return __int_as_float(0x7fc00000);  // NaN: no pixel
+  const int64_t i = (int64_t)y * v.W + x;
+  const float a = v.io.alpha[i];
+  return a >= p.eps ? v.io.depth[i] / a : __int_as_float(0x7fc00000);
+}
+
+// u = grad_x p_s and v = grad_y p_s from the height differences dhx = z(i-1) - z(i+1) and
+// dhy = z(j-1) - z(j+1) (h = max_alt - z).
+struct NormalUV {
+  float ux, uy, uz, vx, vy, vz;
+};
+__device__ __forceinline__ NormalUV normal_uv(const NormalCam& c, float dhx, float dhy) {
+  NormalUV r;
+  r.ux = 2.0f * c.Ai[0][0] + dhx * c.Gx;
+  r.uy = 2.0f * c.Ai[1][0] + dhx * c.Gy;
+  r.uz = dhx;
+  r.vx = 2.0f * c.Ai[0][1] + dhy * c.Gx;
+  r.vy = 2.0f * c.Ai[1][1] + dhy * c.Gy;
+  r.vz = dhy;
   return r;
 }
 
-__global__ void __launch_bounds__(256) depth_normal_fwd_kernel(const __grid_constant__ NormalParams p) {
+__global__ void __launch_bounds__(kNX * kNY) depth_normal_fwd_kernel(const __grid_constant__ NormalParams p) {
+  __shared__ float sz[kNY + 2][kNX + 3];
   const int cam = blockIdx.y;
   const NormalView& v = p.v[cam];
-  const int64_t hw = (int64_t)v.W * v.H;
-  const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pix >= hw) return;
-  const int py = (int)(pix / v.W), px = (int)(pix - (int64_t)py * v.W);
+  const int bxs = (v.W + kNX - 1) / kNX;
+  const int by = blockIdx.x / bxs, bx = blockIdx.x - by * bxs;
+  if (by * kNY >= v.H) return;  // block-uniform: past this view's tiles
+  const int x0 = bx * kNX, y0 = by * kNY;
+  for (int k = threadIdx.x; k < (kNY + 2) * (kNX + 2); k += kNX * kNY) {
+    const int ty = k / (kNX + 2), tx = k - ty * (kNX + 2);
+    sz[ty][tx] = z_at(p, v, x0 - 1 + tx, y0 - 1 + ty);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kNX, ty = threadIdx.x / kNX;
+  const int px = x0 + tx, py = y0 + ty;
+  if (px >= v.W || py >= v.H) return;
   const NormalCam c = normal_cam(p, v, cam);
-  const NormalPix q = normal_pix(p, v, c, px, py);
+  const float zc = sz[ty + 1][tx + 1], zl = sz[ty + 1][tx], zr = sz[ty + 1][tx + 2], zu = sz[ty][tx + 1],
+              zd = sz[ty + 2][tx + 1];
   float n[3] = {0.0f, 0.0f, 0.0f};
-  if (q.ok) {
+  // a NaN (no surface, or outside the view) anywhere leaves the normal at 0
+  if (!(isnan(zc) || isnan(zl) || isnan(zr) || isnan(zu) || isnan(zd))) {
+    const NormalUV q = normal_uv(c, zl - zr, zu - zd);
     n[0] = q.uy * q.vz - q.uz * q.vy;
     n[1] = q.uz * q.vx - q.ux * q.vz;
     n[2] = q.ux * q.vy - q.uy * q.vx;
@@ -116,58 +119,88 @@ __global__ void __launch_bounds__(256) depth_normal_fwd_kernel(const __grid_cons
     n[1] *= s;
     n[2] *= s;
   }
+  const int64_t hw = (int64_t)v.W * v.H, pix = (int64_t)py * v.W + px;
 #pragma unroll
   for (int k = 0; k < 3; ++k) v.io.normal[k * hw + pix] = n[k];
 }
 
-__global__ void __launch_bounds__(256) depth_normal_bwd_kernel(const __grid_constant__ NormalParams p) {
-  __shared__ float red[8][8];
+// Gather form of the backward: a pixel's depth enters the normals of its four neighbours
+// (dhx = z(i-1) - z(i+1), dhy = z(j-1) - z(j+1)), so its gradient is
+// ddhx(i+1) - ddhx(i-1) + ddhy(j+1) - ddhy(j-1).  The block forms ddhx, ddhy once for the tile
+// and a halo of one pixel (from z staged with a halo of two), then every pixel gathers.
+__global__ void __launch_bounds__(kNX * kNY) depth_normal_bwd_kernel(const __grid_constant__ NormalParams p) {
+  __shared__ float sz[kNY + 4][kNX + 5];
+  __shared__ float sdx[kNY + 2][kNX + 3], sdy[kNY + 2][kNX + 3];
+  __shared__ float red[kNX * kNY / 32][8];
   const int cam = blockIdx.y;
   const NormalView& v = p.v[cam];
+  const int bxs = (v.W + kNX - 1) / kNX;
+  const int by = blockIdx.x / bxs, bx = blockIdx.x - by * bxs;
+  if (by * kNY >= v.H) return;  // block-uniform: past this view's tiles
+  const int x0 = bx * kNX, y0 = by * kNY;
   const int64_t hw = (int64_t)v.W * v.H;
-  const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const NormalCam c = normal_cam(p, v, cam);
-  // per-view sums: d A^-1 (4) and d G_xy (2), chained through A^-1 once per block
+  for (int k = threadIdx.x; k < (kNY + 4) * (kNX + 4); k += kNX * kNY) {
+    const int ty = k / (kNX + 4), tx = k - ty * (kNX + 4);
+    sz[ty][tx] = z_at(p, v, x0 - 2 + tx, y0 - 2 + ty);
+  }
+  __syncthreads();
+  // per-view sums over this tile's own pixels: d A^-1 (4) and d G_xy (2)
   float acc[6] = {0, 0, 0, 0, 0, 0};
-  if (pix < hw) {
-    const int py = (int)(pix / v.W), px = (int)(pix - (int64_t)py * v.W);
-    const NormalPix q = normal_pix(p, v, c, px, py);
-    if (q.ok) {
-      float n[3] = {q.uy * q.vz - q.uz * q.vy, q.uz * q.vx - q.ux * q.vz, q.ux * q.vy - q.uy * q.vx};
+  for (int k = threadIdx.x; k < (kNY + 2) * (kNX + 2); k += kNX * kNY) {
+    const int ty = k / (kNX + 2), tx = k - ty * (kNX + 2);  // halo-1 coordinates
+    const int px = x0 - 1 + tx, py = y0 - 1 + ty;
+    const float zc = sz[ty + 1][tx + 1], zl = sz[ty + 1][tx], zr = sz[ty + 1][tx + 2], zu = sz[ty][tx + 1],
+                zd = sz[ty + 2][tx + 1];
+    float ddhx = 0.0f, ddhy = 0.0f;
+    if (!(isnan(zc) || isnan(zl) || isnan(zr) || isnan(zu) || isnan(zd))) {
+      const float dhx = zl - zr, dhy = zu - zd;
+      const NormalUV q = normal_uv(c, dhx, dhy);
+      const float n[3] = {q.uy * q.vz - q.uz * q.vy, q.uz * q.vx - q.ux * q.vz, q.ux * q.vy - q.uy * q.vx};
       const float inv = rsqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-      float N[3] = {n[0] * inv, n[1] * inv, n[2] * inv};  // unsigned unit normal
+      const float N[3] = {n[0] * inv, n[1] * inv, n[2] * inv};  // unsigned unit normal
+      const int64_t pix = (int64_t)py * v.W + px;
       float dN[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) dN[k] = v.io.d_normal[k * hw + pix];
+      for (int j = 0; j < 3; ++j) dN[j] = v.io.d_normal[j * hw + pix];
       // N_out = sgn n / |n|: dn = sgn (dN - N (N . dN)) / |n|
       const float nd = N[0] * dN[0] + N[1] * dN[1] + N[2] * dN[2];
       float dc[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) dc[k] = c.sgn * (dN[k] - N[k] * nd) * inv;
+      for (int j = 0; j < 3; ++j) dc[j] = c.sgn * (dN[j] - N[j] * nd) * inv;
       // n = u x v: du = v x dc, dv = dc x u
       const float dux = q.vy * dc[2] - q.vz * dc[1], duy = q.vz * dc[0] - q.vx * dc[2],
                   duz = q.vx * dc[1] - q.vy * dc[0];
       const float dvx = dc[1] * q.uz - dc[2] * q.uy, dvy = dc[2] * q.ux - dc[0] * q.uz,
                   dvz = dc[0] * q.uy - dc[1] * q.ux;
       // u = a1 + dhx G, v = a2 + dhy G, G = (Gx, Gy, 1)
-      const float ddhx = dux * c.Gx + duy * c.Gy + duz;
-      const float ddhy = dvx * c.Gx + dvy * c.Gy + dvz;
-      // a1 = 2 A^-1[:, 0], a2 = 2 A^-1[:, 1]
-      acc[0] = 2.0f * dux;  // d A^-1[0][0]
-      acc[1] = 2.0f * dvx;  // d A^-1[0][1]
-      acc[2] = 2.0f * duy;  // d A^-1[1][0]
-      acc[3] = 2.0f * dvy;  // d A^-1[1][1]
-      acc[4] = q.dhx * dux + q.dhy * dvx;  // d G_x
-      acc[5] = q.dhx * duy + q.dhy * dvy;  // d G_y
-      // dhx = z(i-1) - z(i+1), dhy = z(j-1) - z(j+1); z = D / alpha
-      const int64_t W = v.W;
-      const int64_t nb[4] = {pix - 1, pix + 1, pix - W, pix + W};
-      const float dz[4] = {ddhx, -ddhx, ddhy, -ddhy};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float a = v.io.alpha[nb[k]], D = v.io.depth[nb[k]];
-        if (v.io.d_depth) atomicAdd(v.io.d_depth + nb[k], dz[k] / a);
-        if (v.io.d_alpha) atomicAdd(v.io.d_alpha + nb[k], -dz[k] * D / (a * a));
+      ddhx = dux * c.Gx + duy * c.Gy + duz;
+      ddhy = dvx * c.Gx + dvy * c.Gy + dvz;
+      if (tx >= 1 && tx <= kNX && ty >= 1 && ty <= kNY) {
+        // the tile's own pixel: a1 = 2 A^-1[:, 0], a2 = 2 A^-1[:, 1]
+        acc[0] += 2.0f * dux;  // d A^-1[0][0]
+        acc[1] += 2.0f * dvx;  // d A^-1[0][1]
+        acc[2] += 2.0f * duy;  // d A^-1[1][0]
+        acc[3] += 2.0f * dvy;  // d A^-1[1][1]
+        acc[4] += dhx * dux + dhy * dvx;  // d G_x
+        acc[5] += dhx * duy + dhy * dvy;  // d G_y
+      }
+    }
+    sdx[ty][tx] = ddhx;
+    sdy[ty][tx] = ddhy;
+  }
+  __syncthreads();
+  {
+    const int tx = threadIdx.x % kNX, ty = threadIdx.x / kNX;
+    const int px = x0 + tx, py = y0 + ty;
+    if (px < v.W && py < v.H) {
+      const float dz = sdx[ty + 1][tx + 2] - sdx[ty + 1][tx] + sdy[ty + 2][tx + 1] - sdy[ty][tx + 1];
+      if (dz != 0.0f) {
+        // z = D / alpha (a pixel that feeds a normal has a surface)
+        const int64_t pix = (int64_t)py * v.W + px;
+        const float a = v.io.alpha[pix], D = v.io.depth[pix];
+        if (v.io.d_depth) v.io.d_depth[pix] += dz / a;
+        if (v.io.d_alpha) v.io.d_alpha[pix] += -dz * D / (a * a);
       }
     }
   }
@@ -239,8 +272,9 @@ ss_status fill_normal(NormalParams& p, const ss_camera* cams, int32_t n_cams, co
 
 dim3 normal_grid(const ss_camera* cams, int32_t n_cams) {
   int64_t most = 0;
-  for (int c = 0; c < n_cams; ++c) most = std::max(most, (int64_t)cams[c].width * cams[c].height);
-  return dim3((unsigned)((most + 255) / 256), (unsigned)n_cams);
+  for (int c = 0; c < n_cams; ++c)
+    most = std::max(most, (int64_t)((cams[c].width + kNX - 1) / kNX) * ((cams[c].height + kNY - 1) / kNY));
+  return dim3((unsigned)most, (unsigned)n_cams);
 }
 
 }  // namespace
@@ -256,7 +290,7 @@ ss_status ss_depth_normal_fwd(const ss_camera* cams, int32_t n_cams, const float
   ss_status e = fill_normal(p, cams, n_cams, dF, alpha_eps, io, false);
   if (e != SS_OK) return e;
   count_launch();
-  depth_normal_fwd_kernel<<<normal_grid(cams, n_cams), 256, 0, (cudaStream_t)stream>>>(p);
+  depth_normal_fwd_kernel<<<normal_grid(cams, n_cams), kNX * kNY, 0, (cudaStream_t)stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }
 
@@ -267,7 +301,7 @@ ss_status ss_depth_normal_bwd(const ss_camera* cams, int32_t n_cams, const float
   if (e != SS_OK) return e;
   p.d_dF = d_dF;
   count_launch();
-  depth_normal_bwd_kernel<<<normal_grid(cams, n_cams), 256, 0, (cudaStream_t)stream>>>(p);
+  depth_normal_bwd_kernel<<<normal_grid(cams, n_cams), kNX * kNY, 0, (cudaStream_t)stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }
 
