@@ -60,11 +60,11 @@ def lib():
             L.ora_camera.argtypes = [P, I32, P, P, P, P]
             L.ora_project.argtypes = [I64, P, P, P, P, P, P, I32, P, P]
             L.ora_order.argtypes = [I64, P, P]
-            L.ora_render.argtypes = [I64, P, P, P, P, P, P, I32, P, P, I32, I32, I32, I32, I32] + [P] * 9
+            L.ora_render.argtypes = [I64, P, P, P, P, P, P, I32, P, P, I32, I32, I32, I32, I32] + [P] * 10
             L.ora_render_dual.argtypes = ([I64, P, P, P, P, P, P, I32, P, P, I32, I32, I32, I32, I32]
-                                          + [P] * 7 + [P] * 4)
+                                          + [P] * 7 + [P] * 5)
             L.ora_backward.argtypes = ([I64, P, P, P, P, P, P, I32, P, P, I32, I32, I32, I32, I32]
-                                       + [P] * 4 + [P] * 7)
+                                       + [P] * 5 + [P] * 7)
             L.ora_num_threads.restype = I32
             L.ora_set_threads.argtypes = [I32]
             _lib = L
@@ -177,8 +177,9 @@ def order(sc: SceneF64) -> np.ndarray:
 def render(sc: SceneF64, cam, sun=False, opts: Opts = Opts(), crop=None, brute=False,
            dF=None, color=None):
     """Forward render of a view (or its sun view).  Returns a dict of float64 planes:
-    rgb (3,h,w), depth, normal (3,h,w), alpha, T, margin_fwd, margin_bwd and int32
-    ncontrib / terminated.  ``color`` is the 3x4 [C|c] (identity for sun views)."""
+    rgb (3,h,w), depth, normal (3,h,w), alpha, distort (the distortion of the blending weights
+    along the ray, Sec. 4), T, margin_fwd, margin_bwd and int32 ncontrib / terminated.
+    ``color`` is the 3x4 [C|c] (identity for sun views)."""
     x0, y0, w, h = _crop(cam, sun, crop)
     rec = camera_record(cam, dF=dF, color=color)
     col = rec[C_COLOR:C_COLOR + 12].copy()
@@ -186,11 +187,11 @@ def render(sc: SceneF64, cam, sun=False, opts: Opts = Opts(), crop=None, brute=F
     out = dict(rgb=np.zeros((3, h, w)), depth=np.zeros((h, w)), normal=np.zeros((3, h, w)),
                alpha=np.zeros((h, w)), T=np.zeros((h, w)), margin_fwd=np.zeros((h, w)),
                margin_bwd=np.zeros((h, w)), ncontrib=np.zeros((h, w), np.int32),
-               terminated=np.zeros((h, w), np.int32))
+               terminated=np.zeros((h, w), np.int32), distort=np.zeros((h, w)))
     lib().ora_render(*sc.args(), _ptr(rec), int(sun), _ptr(col), _ptr(o), x0, y0, w, h, int(brute),
                      _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["normal"]), _ptr(out["alpha"]),
                      _ptr(out["T"]), _ptr(out["margin_fwd"]), _ptr(out["margin_bwd"]),
-                     _ptr(out["ncontrib"]), _ptr(out["terminated"]))
+                     _ptr(out["ncontrib"]), _ptr(out["terminated"]), _ptr(out["distort"]))
     return out
 
 
@@ -205,31 +206,31 @@ def render_dual(sc: SceneF64, cam, tangents: dict, sun=False, opts: Opts = Opts(
     t = {k: (None if tangents.get(k) is None else _d(tangents[k]))
          for k in ("means", "scales", "quats", "opacity", "rgb", "dF", "color")}
     out = dict(rgb=np.zeros((3, h, w)), depth=np.zeros((h, w)), normal=np.zeros((3, h, w)),
-               alpha=np.zeros((h, w)))
+               alpha=np.zeros((h, w)), distort=np.zeros((h, w)))
     lib().ora_render_dual(*sc.args(), _ptr(rec), int(sun), _ptr(col), _ptr(o), x0, y0, w, h,
                           int(brute), _ptr(t["means"]), _ptr(t["scales"]), _ptr(t["quats"]),
                           _ptr(t["opacity"]), _ptr(t["rgb"]), _ptr(t["dF"]), _ptr(t["color"]),
                           _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["normal"]),
-                          _ptr(out["alpha"]))
+                          _ptr(out["alpha"]), _ptr(out["distort"]))
     return out
 
 
 def backward(sc: SceneF64, cam, upstream: dict, sun=False, opts: Opts = Opts(), crop=None,
              brute=False, dF=None, color=None):
     """Reverse-mode gradients of sum(upstream * planes) for the crop.  ``upstream`` keys:
-    rgb (3,h,w), depth (h,w), normal (3,h,w), alpha (h,w); missing = 0."""
+    rgb (3,h,w), depth (h,w), normal (3,h,w), alpha (h,w), distort (h,w); missing = 0."""
     x0, y0, w, h = _crop(cam, sun, crop)
     rec = camera_record(cam, dF=dF, color=color)
     col = rec[C_COLOR:C_COLOR + 12].copy()
     o = opts.record()
     g = {k: (None if upstream.get(k) is None else _d(upstream[k]))
-         for k in ("rgb", "depth", "normal", "alpha")}
+         for k in ("rgb", "depth", "normal", "alpha", "distort")}
     n = sc.n
     out = dict(means=np.zeros((3, n)), scales=np.zeros((2, n)), quats=np.zeros((4, n)),
                opacity=np.zeros(n), rgb=np.zeros((3, n)), dF=np.zeros(8), color=np.zeros(12))
     lib().ora_backward(*sc.args(), _ptr(rec), int(sun), _ptr(col), _ptr(o), x0, y0, w, h,
                        int(brute), _ptr(g["rgb"]), _ptr(g["depth"]), _ptr(g["normal"]),
-                       _ptr(g["alpha"]), _ptr(out["means"]), _ptr(out["scales"]),
+                       _ptr(g["alpha"]), _ptr(g["distort"]), _ptr(out["means"]), _ptr(out["scales"]),
                        _ptr(out["quats"]), _ptr(out["opacity"]), _ptr(out["rgb"]),
                        _ptr(out["dF"]), _ptr(out["color"]))
     out["dF"] = out["dF"].reshape(2, 4)

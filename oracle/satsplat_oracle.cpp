@@ -25,6 +25,11 @@
  *   - front-to-back blending f = sum f_i a_i G^_i prod_{j<i} (1 - a_j G^_j) over
  *     splats ordered by the height-based depth of their centres   (Sec. 3.2 Eq. rasterization)
  *   - corrected albedo C A + c                           (Sec. 3.1 Eq. image_formation)
+ *   - distortion of the blending weights along the ray: the sum over composited
+ *     pairs j before i of 2 w_i w_j (z_i - z_j), w_i = a_i G^_i T_i and z_i the
+ *     depth of the ray-splat intersection (the point-sample distortion loss that
+ *     Sec. 4 adds to the training loss, in compositing order; it equals
+ *     sum_{i,j} w_i w_j |z_i - z_j| when that order is the order of z)
  * Readings where the paper is silent (alpha threshold 1/255, clamp 0.99, early
  * stop at T < 1e-4 excluding the stopping splat, ties by splat index, pixel
  * centres at +0.5, depth at the intersection point, normal flipped to face the
@@ -309,7 +314,7 @@ void build_bins(Bins& bins, const std::vector<Proj<S>>& P, const std::vector<int
 
 // ---------------------------------------------------------------- the forward definition
 template <class S> struct PixOut {
-  S rgb[3], depth, nrm[3], alpha, A[3];
+  S rgb[3], depth, nrm[3], alpha, A[3], dist;
   double T;
   int ncontrib, terminated;
   double mfwd, mbwd;
@@ -325,6 +330,7 @@ PixOut<S> render_pixel(const std::vector<Proj<S>>& P, const std::vector<int64_t>
   double mf = 1e300, mb = 1e300;
   out.ncontrib = 0;
   out.terminated = 0;
+  std::vector<S> wts, zs;  // weights and intersection depths of the composited splats
   for (int64_t k : cand) {
     const Proj<S>& p = P[k];
     if (p.culled) continue;
@@ -350,9 +356,16 @@ PixOut<S> render_pixel(const std::vector<Proj<S>>& P, const std::vector<int64_t>
     S z = p.deg ? p.zc : p.zc + p.dzdu * E.u + p.dzdv * E.v;
     D += w * z;
     for (int c = 0; c < 3; ++c) N[c] += w * p.n[c];
+    wts.push_back(w);
+    zs.push_back(z);
     T = Tn;
     out.ncontrib++;
   }
+  // distortion: every composited pair, the later splat i against each earlier one j
+  S dist(0.0);
+  for (size_t i = 0; i < wts.size(); ++i)
+    for (size_t j = 0; j < i; ++j) dist += S(2.0) * wts[i] * wts[j] * (zs[i] - zs[j]);
+  out.dist = dist;
   out.T = val(T);
   out.alpha = S(1.0) - T;
   out.depth = D;
@@ -388,7 +401,8 @@ void forward_image(const Scene& sc, const Dirs* dr, const double* cam, int sun, 
                    const double* opt, Crop cr, int brute,
                    // outputs (values for double, tangents for dual), each [h][w] or [3][h][w]
                    double* rgb, double* depth, double* nrm, double* alpha, double* Tfin,
-                   double* mfwd, double* mbwd, int32_t* ncontrib, int32_t* terminated) {
+                   double* mfwd, double* mbwd, int32_t* ncontrib, int32_t* terminated,
+                   double* dist) {
   Cam<S> C = assemble<S>(cam, dr ? dr->dF : nullptr, sun != 0);
   S color[12];
   for (int i = 0; i < 12; ++i) {
@@ -419,6 +433,7 @@ void forward_image(const Scene& sc, const Dirs* dr, const double* cam, int sun, 
       }
       put(depth, idx, o.depth);
       put(alpha, idx, o.alpha);
+      put(dist, idx, o.dist);
       if (Tfin) Tfin[idx] = o.T;
       if (mfwd) mfwd[idx] = o.mfwd;
       if (mbwd) mbwd[idx] = o.mbwd;
@@ -469,7 +484,7 @@ struct Walk {
 void backward_image(const Scene& sc, const double* cam, int sun, const double* color, const double* opt,
                     Crop cr, int brute,
                     const double* g_rgb, const double* g_depth, const double* g_nrm, const double* g_alpha,
-                    double* d_means, double* d_scales, double* d_quats, double* d_opac, double* d_rgb,
+                    const double* g_dist, double* d_means, double* d_scales, double* d_quats, double* d_opac, double* d_rgb,
                     double* d_dF, double* d_color) {
   Cam<double> C = assemble<double>(cam, nullptr, sun != 0);
   double col[12];
@@ -530,6 +545,29 @@ void backward_image(const Scene& sc, const double* cam, int sun, const double* c
           for (int c = 0; c < 3; ++c) gN[c] = g_nrm[c * hw + idx];
         if (g_depth) gD = g_depth[idx];
         if (g_alpha) gAl = g_alpha[idx];
+        // distortion: its partials in the weight and in the depth of each composited splat m,
+        // as plain sums over the other composited splats:
+        //   d/dw_m = sum_{j<m} 2 w_j (z_m - z_j) + sum_{i>m} 2 w_i (z_i - z_m)
+        //   d/dz_m = sum_{j<m} 2 w_m w_j - sum_{i>m} 2 w_i w_m
+        const double gDist = g_dist ? g_dist[idx] : 0.0;
+        const size_t nw = walk.size();
+        std::vector<double> hw(nw, 0.0), hz(nw, 0.0);
+        if (gDist != 0.0) {
+          for (size_t m = 0; m < nw; ++m) {
+            const double wm = walk[m].alpha * walk[m].T, zm = walk[m].z;
+            for (size_t j = 0; j < nw; ++j) {
+              if (j == m) continue;
+              const double wj = walk[j].alpha * walk[j].T, zj = walk[j].z;
+              if (j < m) {
+                hw[m] += 2.0 * wj * (zm - zj);
+                hz[m] += 2.0 * wm * wj;
+              } else {
+                hw[m] += 2.0 * wj * (zj - zm);
+                hz[m] -= 2.0 * wj * wm;
+              }
+            }
+          }
+        }
         // reverse walk: f = sum_i f_i a_i T_i, T_i = prod_{j<i} (1 - a_j);
         // df/da_i = T_i (f_i - S_i), S_i = sum_{j>i} f_j a_j prod_{i<l<j} (1 - a_l)
         double Sg = 0.0;  // g . S_i
@@ -537,7 +575,7 @@ void backward_image(const Scene& sc, const double* cam, int sun, const double* c
           const Walk& wk = walk[m];
           const Proj<double>& p = P[wk.k];
           double w = wk.alpha * wk.T;
-          double gf = gD * wk.z;
+          double gf = gD * wk.z + gDist * hw[m];
           for (int c = 0; c < 3; ++c) gf += gA[c] * p.rgb[c] + gN[c] * p.n[c];
           double dalpha = wk.T * (gf - Sg) + gAl * Tfinal / (1.0 - wk.alpha);
           Sg = wk.alpha * gf + (1.0 - wk.alpha) * Sg;
@@ -546,7 +584,7 @@ void backward_image(const Scene& sc, const double* cam, int sun, const double* c
             g[G_rgb + c] = w * gA[c];
             g[G_n + c] = w * gN[c];
           }
-          double dz = w * gD;
+          double dz = w * gD + gDist * hz[m];
           double du = 0, dv = 0;
           g[G_zc] = dz;
           if (!p.deg) {
@@ -756,15 +794,16 @@ void ora_order(int64_t n, const double* means, int64_t* order) {
 }
 
 /* Forward render of the crop (x0, y0, w, h) of one view (sun = 0) or its sun view (sun = 1).
- * Outputs are planar [C][h][w]; any output pointer may be NULL. */
+ * Outputs are planar [C][h][w]; any output pointer may be NULL.  o_dist is the distortion
+ * of the pixel's blending weights (see the header). */
 void ora_render(int64_t n, const double* means, const double* scales, const double* quats,
                 const double* opac, const double* rgb, const double* cam, int sun,
                 const double* color, const double* opt, int x0, int y0, int w, int h, int brute,
                 double* o_rgb, double* o_depth, double* o_nrm, double* o_alpha, double* o_T,
-                double* o_mfwd, double* o_mbwd, int32_t* o_ncontrib, int32_t* o_term) {
+                double* o_mfwd, double* o_mbwd, int32_t* o_ncontrib, int32_t* o_term, double* o_dist) {
   Scene sc = make_scene(n, means, scales, quats, opac, rgb);
   forward_image<double>(sc, nullptr, cam, sun, color, opt, Crop{x0, y0, w, h}, brute, o_rgb, o_depth,
-                        o_nrm, o_alpha, o_T, o_mfwd, o_mbwd, o_ncontrib, o_term);
+                        o_nrm, o_alpha, o_T, o_mfwd, o_mbwd, o_ncontrib, o_term, o_dist);
 }
 
 /* Directional derivative (forward mode, dual numbers) of the rendered planes along the
@@ -774,24 +813,25 @@ void ora_render_dual(int64_t n, const double* means, const double* scales, const
                      const double* color, const double* opt, int x0, int y0, int w, int h, int brute,
                      const double* t_means, const double* t_scales, const double* t_quats,
                      const double* t_opac, const double* t_rgb, const double* t_dF, const double* t_color,
-                     double* o_rgb, double* o_depth, double* o_nrm, double* o_alpha) {
+                     double* o_rgb, double* o_depth, double* o_nrm, double* o_alpha, double* o_dist) {
   Scene sc = make_scene(n, means, scales, quats, opac, rgb);
   Dirs d{t_means, t_scales, t_quats, t_opac, t_rgb, t_dF, t_color};
   forward_image<Dual>(sc, &d, cam, sun, color, opt, Crop{x0, y0, w, h}, brute, o_rgb, o_depth, o_nrm,
-                      o_alpha, nullptr, nullptr, nullptr, nullptr, nullptr);
+                      o_alpha, nullptr, nullptr, nullptr, nullptr, nullptr, o_dist);
 }
 
 /* Reverse-mode adjoint of the crop's planes: gradients are ADDED into the outputs.
- * Upstream planes are [C][h][w] over the crop (NULL = 0). */
+ * Upstream planes are [C][h][w] over the crop (NULL = 0); g_dist is the upstream of the
+ * distortion plane. */
 void ora_backward(int64_t n, const double* means, const double* scales, const double* quats,
                   const double* opac, const double* rgb, const double* cam, int sun,
                   const double* color, const double* opt, int x0, int y0, int w, int h, int brute,
                   const double* g_rgb, const double* g_depth, const double* g_nrm, const double* g_alpha,
-                  double* d_means, double* d_scales, double* d_quats, double* d_opac, double* d_rgb,
-                  double* d_dF, double* d_color) {
+                  const double* g_dist, double* d_means, double* d_scales, double* d_quats, double* d_opac,
+                  double* d_rgb, double* d_dF, double* d_color) {
   Scene sc = make_scene(n, means, scales, quats, opac, rgb);
   backward_image(sc, cam, sun, color, opt, Crop{x0, y0, w, h}, brute, g_rgb, g_depth, g_nrm, g_alpha,
-                 d_means, d_scales, d_quats, d_opac, d_rgb, d_dF, d_color);
+                 g_dist, d_means, d_scales, d_quats, d_opac, d_rgb, d_dF, d_color);
 }
 
 }  // extern "C"

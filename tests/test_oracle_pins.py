@@ -351,7 +351,8 @@ def _tangents(rng, sc):
 
 def _upstream(rng, out, mask=None):
     g = dict(rgb=rng.normal(size=out["rgb"].shape), depth=rng.normal(size=out["depth"].shape),
-             normal=rng.normal(size=out["normal"].shape), alpha=rng.normal(size=out["alpha"].shape))
+             normal=rng.normal(size=out["normal"].shape), alpha=rng.normal(size=out["alpha"].shape),
+             distort=rng.normal(size=out["distort"].shape))
     if mask is not None:
         for k in g:
             g[k] = g[k] * mask
@@ -431,12 +432,12 @@ def _render_f64(s64, cam, sun, dF_flat, col_flat):
     W, H_ = (cam.shadow_w, cam.shadow_h) if sun else (cam.width, cam.height)
     o = oracle.Opts().record()
     out = dict(rgb=np.zeros((3, H_, W)), depth=np.zeros((H_, W)), normal=np.zeros((3, H_, W)),
-               alpha=np.zeros((H_, W)))
+               alpha=np.zeros((H_, W)), distort=np.zeros((H_, W)))
     P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     col = np.ascontiguousarray(col_flat)
     oracle.lib().ora_render(*s64.args(), P(rec), int(sun), P(col), P(o), 0, 0, W, H_, 0,
                             P(out["rgb"]), P(out["depth"]), P(out["normal"]), P(out["alpha"]),
-                            None, None, None, None, None)
+                            None, None, None, None, None, P(out["distort"]))
     return out
 
 
@@ -464,10 +465,11 @@ def test_grad_dF_equals_grad_F():
             o = oracle.Opts().record()
             col = rec[oracle.C_COLOR:oracle.C_COLOR + 12].copy()
             pl = dict(rgb=np.zeros((3, cam.height, cam.width)), depth=np.zeros((cam.height, cam.width)),
-                      normal=np.zeros((3, cam.height, cam.width)), alpha=np.zeros((cam.height, cam.width)))
+                      normal=np.zeros((3, cam.height, cam.width)), alpha=np.zeros((cam.height, cam.width)),
+                      distort=np.zeros((cam.height, cam.width)))
             oracle.lib().ora_render(*s64.args(), P(rec), 0, P(col), P(o), 0, 0, cam.width, cam.height,
                                     0, P(pl["rgb"]), P(pl["depth"]), P(pl["normal"]), P(pl["alpha"]),
-                                    None, None, None, None, None)
+                                    None, None, None, None, None, P(pl["distort"]))
             fvals.append(sum(float(np.sum(g[k] * pl[k])) for k in g))
         fd = (fvals[0] - fvals[1]) / (2 * h)
         assert fd == pytest.approx(grads["dF"][idx], rel=1e-5, abs=1e-6)
