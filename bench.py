@@ -39,6 +39,10 @@ UNIT = "Mpix/s"
 #   backward: pair evaluation 20 + adjoint 63 + accumulation of 16 gradient fields 16
 FLOPS_FWD_PER_PAIR = 41
 FLOPS_BWD_PER_PAIR = 99
+# with the distortion of the blending weights: forward + 6 (its running sum), backward + 18 (its
+# partials in the weight and the depth and the running weighted depth behind the splat)
+FLOPS_FWD_PER_PAIR_DIST = 47
+FLOPS_BWD_PER_PAIR_DIST = 117
 FP32_LANES_PER_SM = 128
 
 WORKLOAD_TEXT = {
@@ -66,6 +70,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (16x16, batch 256)")
+    ap.add_argument("--no-distortion", action="store_true",
+                    help="skip timing the step with the distortion plane")
     ap.add_argument("--storage", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--profile", action="store_true",
                     help="short run for a profiler: no tuning, plain, e2e or CPU arms")
@@ -294,6 +300,46 @@ def measure_shade(torch, step, reps: int):
             "bwd_frac": bb / (bms * 1e-3) / 1e9 / peak}
 
 
+def measure_distortion(torch, mk, ups, reps: int, walked: int, base_ms: dict, peak_tflops: float):
+    """The same batched step with the distortion plane written by the forward and an upstream
+    distortion gradient in the backward: the step through its graphs, and the forward and
+    backward kernels with CUDA events, against the step without it."""
+    targets_ups = []
+    g = torch.Generator(device="cuda")
+    g.manual_seed(4321)
+    for u in ups:
+        u = dict(u)
+        if "rgb" in u:  # a main target
+            u["distort"] = torch.randn(*u["depth"].shape, device="cuda", generator=g)
+        targets_ups.append(u)
+    step = mk(targets_ups)
+    step.capture()
+    for _ in range(3):
+        step.replay()
+    ms = time_loop(torch, step.replay, reps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    acc = np.zeros(2)
+    for _ in range(reps):
+        step.forward_part()
+        step.zero_grads()
+        ev[0].record(); step.forward(); ev[1].record(); step.backward_pixels(); ev[2].record()
+        torch.cuda.synchronize()
+        acc += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])]
+    fms, bms = acc / reps
+    st = step.check()[0]
+    del step
+    torch.cuda.empty_cache()
+    if st != 0:
+        raise RuntimeError(f"distortion step status {st}")
+    bw = walked * FLOPS_BWD_PER_PAIR_DIST / (bms * 1e-3) / 1e12
+    return {"step_ms": float(ms), "rasterize_fwd_ms": float(fms), "rasterize_bwd_ms": float(bms),
+            "step_over_plain_step": float(ms / base_ms["step"]),
+            "fwd_over_plain_fwd": float(fms / base_ms["rasterize_fwd"]),
+            "bwd_over_plain_bwd": float(bms / base_ms["rasterize_bwd"]),
+            "bwd_roofline": {"bound": "alu", "achieved": bw, "peak": peak_tflops, "unit": "TFLOP/s",
+                             "frac": bw / peak_tflops, "flops_per_pair": FLOPS_BWD_PER_PAIR_DIST}}
+
+
 def measure_depth_normal(torch, step, reps: int):
     """Forward and backward of the depth-gradient normal (K8) over every main view of the step;
     HBM roofline from the algorithmic bytes per main pixel (forward: depth and alpha read, N
@@ -501,6 +547,11 @@ def run_ours(args, dist):
     # ---- sun visibility and image formation (K7), depth-gradient normals (K8), timed alone
     shade = measure_shade(torch, step, k_steps)
     dnormal = measure_depth_normal(torch, step, k_steps)
+    distortion = None
+    if not args.no_distortion:
+        mk_d = lambda u: BatchedStep(cams, splats, scene.n, dF, color, u, passes=passes, opts=opts,
+                                     distortion=True)
+        distortion = measure_distortion(torch, mk_d, ups, k_steps, walked, dict(phase_ms, step=ms), peak_tflops)
 
     # ---- plain FP32 single-view arm: the same scene as one plain call sequence per view
     plain = None
@@ -604,7 +655,7 @@ def run_ours(args, dist):
                 "roofline": roofline, "cpu_baseline": cpu, "plain_fp32": plain,
                 "batched_over_plain": (value / dist.world) / plain["value"] if plain else None,
                 "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-                "shade": shade, "depth_normal": dnormal,
+                "shade": shade, "depth_normal": dnormal, "distortion": distortion,
                 "steps_per_s": 1e3 / ms_max, "peak_hbm_gb": peak_hbm_gb,
                 "device": {"sms": sms, "arch": arch, "name": torch.cuda.get_device_name()}}
         print(json.dumps(line), flush=True)

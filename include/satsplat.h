@@ -127,7 +127,8 @@ typedef struct {
 } ss_raster_opts;
 
 /* Per render target I/O (device pointers; row-major [H][W] planes of the
- * target's own size, planar [3][H][W] for 3-channel outputs).
+ * target's own size, planar [3][H][W] for 3-channel outputs).  Caller-owned;
+ * unused pointers must be NULL.
  *   rgb     corrected colour C A + c (main targets only; NULL = not written)
  *   depth   sum_i w_i z_i, z_i the depth of the ray-splat intersection, not
  *           normalised by alpha (NULL = not written)
@@ -136,7 +137,17 @@ typedef struct {
  *   T_final, last  saved state for the backward pass (REQUIRED by ss_rasterize_fwd
  *           and ss_rasterize_bwd): final transmittance and the end of the
  *           pixel's walk in the sorted intersection list
- *   d_rgb, d_depth, d_normal, d_alpha  upstream gradients (backward; NULL = 0) */
+ *   d_rgb, d_depth, d_normal, d_alpha  upstream gradients (backward; NULL = 0)
+ *   distort  distortion of the blending weights along the pixel's ray, the
+ *           point-sample distortion that Sec. 4 adds to the training loss:
+ *           sum over composited pairs j before i of 2 w_i w_j (z_i - z_j), with
+ *           w_i the blending weight and z_i the intersection depth; it equals
+ *           sum_{i,j} w_i w_j |z_i - z_j| where the compositing order is the order
+ *           of z (NULL = not computed; the forward then runs without it)
+ *   d_distort  its upstream gradient (backward; NULL = 0).  Requires `depth`:
+ *           the adjoint reads the forward's depth plane, which must hold the
+ *           values that ss_rasterize_fwd wrote for this frame (SS_ERR_INVALID_ARG
+ *           when it is NULL) */
 typedef struct {
   float* rgb;
   float* depth;
@@ -148,6 +159,8 @@ typedef struct {
   const float* d_depth;
   const float* d_normal;
   const float* d_alpha;
+  float* distort;
+  const float* d_distort;
 } ss_target_io;
 
 /* Gradients with respect to the splat attributes: FP32 DEVICE arrays [C][n_pad]

@@ -47,7 +47,8 @@ class ss_raster_opts(ctypes.Structure):
 
 class ss_target_io(ctypes.Structure):
     _fields_ = [("rgb", P), ("depth", P), ("normal", P), ("alpha", P), ("T_final", P), ("last", P),
-                ("d_rgb", P), ("d_depth", P), ("d_normal", P), ("d_alpha", P)]
+                ("d_rgb", P), ("d_depth", P), ("d_normal", P), ("d_alpha", P), ("distort", P),
+                ("d_distort", P)]
 
 
 class ss_shade_opts(ctypes.Structure):

@@ -45,6 +45,8 @@ class _RenderFn(torch.autograd.Function):
         for i, t in enumerate(frame.targets):
             if not t.sun:
                 flat += [out.rgb[i], out.depth[i], out.normal[i], out.alpha[i]]
+                if frame.distortion:
+                    flat.append(out.distort[i])
             else:
                 flat += [out.depth[i], out.alpha[i]]
         return tuple(flat)
@@ -62,6 +64,8 @@ class _RenderFn(torch.autograd.Function):
         for t in frame.targets:
             if not t.sun:
                 up.append(dict(rgb=c(next(it)), depth=c(next(it)), normal=c(next(it)), alpha=c(next(it))))
+                if frame.distortion:
+                    up[-1]["distort"] = c(next(it))
             else:
                 up.append(dict(depth=c(next(it)), alpha=c(next(it))))
         dev = ctx.store[0].device
@@ -80,13 +84,17 @@ def render(frame: Frame, means, scales, quats, opacity, rgb, dF=None, color=None
 
     means (3, N), scales (2, N), quats (4, N) (w, x, y, z), opacity (N,), rgb (3, N): FP32.
     dF (V, 2, 4) camera deltas and color (V, 3, 4) [C | c], optional.
-    Returns one dict per target: rgb, depth, normal, alpha (sun targets: depth, alpha)."""
+    Returns one dict per target: rgb, depth, normal, alpha, and distort when the frame was made
+    with ``distortion=True`` (sun targets: depth, alpha)."""
     flat = _RenderFn.apply(frame, storage, means, scales, quats, opacity, rgb, dF, color)
     res, i = [], 0
     for t in frame.targets:
         if not t.sun:
             res.append(dict(rgb=flat[i], depth=flat[i + 1], normal=flat[i + 2], alpha=flat[i + 3]))
             i += 4
+            if frame.distortion:
+                res[-1]["distort"] = flat[i]
+                i += 1
         else:
             res.append(dict(depth=flat[i], alpha=flat[i + 1]))
             i += 2

@@ -40,14 +40,16 @@ class BatchedStep:
 
     ``splats``: dict of planar storage tensors [C, n_pad] (fp32 or bf16): means, scales,
     quats, opacity, rgb.  ``dF`` (V, 2, 4), ``color`` (V, 3, 4) fp32.  ``upstream``: one
-    dict of upstream gradient planes per target.  Gradients go to ``grads`` (fp32 [C, n_pad]),
+    dict of upstream gradient planes per target (with ``distortion``, a main target's dict may
+    hold the distortion's upstream under "distort").  Gradients go to ``grads`` (fp32 [C, n_pad]),
     ``d_dF`` and ``d_color``; they are zeroed at the start of each step."""
 
     def __init__(self, cameras: Sequence, splats: dict, n: int, dF, color, upstream: Sequence[dict],
                  passes: int = L.SS_PASS_MAIN | L.SS_PASS_SUN, opts: Optional[L.ss_raster_opts] = None,
-                 capacity_slack: float = 1.10, capacity: Optional[int] = None, device="cuda"):
+                 capacity_slack: float = 1.10, capacity: Optional[int] = None, device="cuda",
+                 distortion: bool = False):
         self.opts = opts if opts is not None else L.default_opts(persistent=1)
-        self.frame = Frame(cameras, passes, self.opts, device=device)
+        self.frame = Frame(cameras, passes, self.opts, device=device, distortion=distortion)
         self.tensors = splats
         self.n = int(n)
         self.splats = L.make_splats(splats["means"], splats["scales"], splats["quats"], splats["opacity"],
@@ -59,7 +61,7 @@ class BatchedStep:
         V = self.frame.n_cams
         self.d_dF = torch.zeros(V, 2, 4, device=device)
         self.d_color = torch.zeros(V, 3, 4, device=device)
-        self.out = Outputs(self.frame.targets, self.frame.device)
+        self.out = Outputs(self.frame.targets, self.frame.device, distortion)
         self._io_f = self.out.io_array()
         self._io_b = self.out.io_array(self.upstream)
         self._g = grads_struct(self.grads)

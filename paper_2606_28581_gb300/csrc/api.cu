@@ -234,6 +234,11 @@ ss_status fill_raster(RasterParams& rp, const ss_splats* s, const Layout& L, con
     b.d_depth = bwd ? a.d_depth : nullptr;
     b.d_normal = bwd ? a.d_normal : nullptr;
     b.d_alpha = bwd ? a.d_alpha : nullptr;
+    b.distort = bwd ? nullptr : a.distort;
+    b.d_distort = bwd ? a.d_distort : nullptr;
+    // the distortion adjoint reads the forward's depth plane (the weighted depth of the whole ray)
+    if (bwd && a.d_distort && !a.depth) return SS_ERR_INVALID_ARG;
+    rp.distort |= (b.distort || b.d_distort) ? 1 : 0;
   }
   rp.tcams = at<TargetCam>(ws, L.tcams);
   rp.geom = at<float4>(ws, L.geom);

@@ -88,6 +88,8 @@ struct TargetIO {
   const float* d_depth;
   const float* d_normal;
   const float* d_alpha;
+  float* distort;            // distortion of the blending weights (forward output)
+  const float* d_distort;    // its upstream (backward)
 };
 
 // ---------------------------------------------------------------- error-free transforms

@@ -88,6 +88,7 @@ struct RasterParams {
   CullConsts cull;
   float t_min;
   int32_t subblock_cull;   // 0: every staged splat is a candidate of every sub-block
+  int32_t distort;         // some target writes (forward) or back-propagates (backward) the distortion
   TargetIO io[kMaxTargets];
 };
 

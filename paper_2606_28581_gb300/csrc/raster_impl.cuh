@@ -237,7 +237,11 @@ __device__ __forceinline__ int compact_candidates(uint32_t mk, uint8_t* list) {
 // ------------------------------------------------------------------------------------------
 // K3 forward
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH, int BATCH, bool PERSIST>
+// DIST: the distortion of the blending weights along each ray is accumulated beside the planes:
+// each composited splat i adds w_i (z_i (1 - T_i) - D_i) = sum_{j<i} w_i w_j (z_i - z_j), with
+// 1 - T_i and D_i the weight and the weighted depth composited in front of it; the sum is
+// doubled when it is written.
+template <int TW, int TH, int BATCH, bool PERSIST, bool DIST>
 __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
   constexpr int NT = TW * TH / 2;
   static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are whole 8 x 8 warp blocks");
@@ -261,13 +265,13 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
     const uint2 range = p.ranges[tile];
     const int64_t recbase = (int64_t)t * p.n_pad;
 
-    float T[2], D[2], A0[2], A1[2], A2[2], N0[2], N1[2], N2[2], y[2];
+    float T[2], D[2], A0[2], A1[2], A2[2], N0[2], N1[2], N2[2], y[2], Dst[2];
     uint32_t last[2];
     bool done[2];
     uint32_t walked = 0;  // contributing pairs, the stopping one included
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      T[k] = 1.0f; D[k] = A0[k] = A1[k] = A2[k] = N0[k] = N1[k] = N2[k] = 0.0f;
+      T[k] = 1.0f; D[k] = A0[k] = A1[k] = A2[k] = N0[k] = N1[k] = N2[k] = Dst[k] = 0.0f;
       y[k] = (float)(lg.py0 + 2 * k) + 0.5f;
       last[k] = range.x;
       done[k] = !(lg.px < cam.W && lg.py0 + 2 * k < cam.H);
@@ -307,7 +311,9 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
           const bool stop = ck && Tn < p.t_min;  // this splat ends the walk and is not composited
           const bool take = ck && !stop;
           const float w = take ? e.alpha * T[k] : 0.0f;
-          D[k] += w * (g2.w + f0.x * e.u + f0.y * e.v);
+          const float z = g2.w + f0.x * e.u + f0.y * e.v;
+          if (DIST) Dst[k] = fmaf(w, fmaf(-z, T[k], z) - D[k], Dst[k]);
+          D[k] += w * z;
           if (!SUN) {
             A0[k] += w * f1.y;
             A1[k] += w * f1.z;
@@ -366,6 +372,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
         io.normal[2 * hw + pix] = N2[k];
       }
       if (io.alpha) io.alpha[pix] = 1.0f - T[k];
+      if (DIST && io.distort) io.distort[pix] = 2.0f * Dst[k];
       io.T_final[pix] = T[k];
       io.last[pix] = last[k];
     }
@@ -378,7 +385,13 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
 // ------------------------------------------------------------------------------------------
 // K4 backward
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH, int BATCH, bool PERSIST>
+// DIST: the adjoint of the distortion.  Its partial in the weight of splat m is
+// 2 (z_m W_m - M_m) + 2 (M'_m - z_m W'_m) and in its depth 2 w_m (W_m - W'_m), where W, M are the
+// weight and the weighted depth composited in front of m and W', M' those behind it.  In the
+// reverse walk W = 1 - T_m and W' = T_{m+1} - T_final, so W - W' = (1 + T_final) - T_m - T_{m+1};
+// M = D - M' - w_m z_m with D the forward's depth plane, so M' - M = E + w_m z_m with
+// E = 2 M' - D carried along the walk.  The weight partial joins the splat's per-pixel value f.
+template <int TW, int TH, int BATCH, bool PERSIST, bool DIST>
 __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
   constexpr int NT = TW * TH / 2;
   constexpr int NW = NT / 32;
@@ -414,6 +427,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
 
     // per pixel: T (recovered backwards), the composite behind (as g . S), the upstream
     float T[2], y[2], Sg[2], gD[2], gAlT[2], gR[2][3], gN[2][3];  // gAlT: d(alpha_out) T_final
+    float gDs2[2], c1[2], E[2];  // distortion: twice its upstream, 1 + T_final, 2 M' - D
     uint32_t lastp[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -422,6 +436,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
       y[k] = (float)py + 0.5f;
       T[k] = 1.0f;
       Sg[k] = gD[k] = gAlT[k] = 0.0f;
+      gDs2[k] = E[k] = 0.0f;
       lastp[k] = range.x;
 #pragma unroll
       for (int c = 0; c < 3; ++c) gR[k][c] = gN[k][c] = 0.0f;
@@ -443,8 +458,13 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
         }
         if (io.d_depth) gD[k] = io.d_depth[pix];
         if (io.d_alpha) gAlT[k] = io.d_alpha[pix] * T[k];
+        if (DIST && io.d_distort) {
+          gDs2[k] = 2.0f * io.d_distort[pix];
+          E[k] = -io.depth[pix];
+        }
         if (lastp[k] > range.x) atomicMax(&s_hi[hp], lastp[k]);
       }
+      c1[k] = 1.0f + T[k];
     }
     // the group's last walked position (exclusive): its walk ends there
     uint32_t glast = max(lastp[0], lastp[1]);
@@ -533,11 +553,19 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
             const float rom = __fdividef(1.0f, om);  // om >= 1 - alpha_max
             const float Ti = T[k] * rom;             // T in front of the splat
             const float z = g2.w + f0.x * e.u + f0.y * e.v;
-            const float gf = SUN ? gD[k] * z
-                                 : gD[k] * z + gR[k][0] * f1.y + gR[k][1] * f1.z + gR[k][2] * f1.w +
-                                       gN[k][0] * f0.z + gN[k][1] * f0.w + gN[k][2] * f1.x;
-            const float gs = gf - Sg[k];
+            float gf = SUN ? gD[k] * z
+                           : gD[k] * z + gR[k][0] * f1.y + gR[k][1] * f1.z + gR[k][2] * f1.w +
+                                 gN[k][0] * f0.z + gN[k][1] * f0.w + gN[k][2] * f1.x;
             const float w = a * Ti;
+            float dzd = 0.0f;  // the distortion's partial in z
+            if (DIST) {
+              const float dW = c1[k] - Ti - T[k];  // W - W'
+              const float wz = w * z;
+              gf = fmaf(gDs2[k], fmaf(z, dW, E[k] + wz), gf);
+              dzd = gDs2[k] * w * dW;
+              E[k] = fmaf(2.0f, wz, E[k]);
+            }
+            const float gs = gf - Sg[k];
             T[k] = Ti;
             Sg[k] = Sg[k] + a * gs;  // composite from this splat on: a f + (1 - a) S
             if (SUN) {
@@ -550,7 +578,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
               Gc[GF_NY] = (k == 0 ? 0.0f : Gc[GF_NY]) + w * gN[k][1];
               Gc[GF_NZ] = (k == 0 ? 0.0f : Gc[GF_NZ]) + w * gN[k][2];
             }
-            const float dz = w * gD[k];
+            const float dz = w * gD[k] + dzd;
             Gc[GF_ZC] = (k == 0 ? 0.0f : Gc[GF_ZC]) + dz;
             Gc[GF_DZDU] = (k == 0 ? 0.0f : Gc[GF_DZDU]) + dz * e.u;
             Gc[GF_DZDV] = (k == 0 ? 0.0f : Gc[GF_DZDV]) + dz * e.v;
@@ -623,7 +651,7 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH, int BATCH>
+template <int TW, int TH, int BATCH, bool DIST>
 cudaError_t launch_fwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
   constexpr int NT = TW * TH / 2;
   if (p.total_tiles == 0) return cudaSuccess;
@@ -633,24 +661,24 @@ cudaError_t launch_fwd_t(const RasterParams& p, bool persistent, int num_sms, cu
     if (per_sm == 0) {
       int v = 0;
       cudaError_t e =
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_fwd_kernel<TW, TH, BATCH, true>, NT, 0);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_fwd_kernel<TW, TH, BATCH, true, DIST>, NT, 0);
       if (e != cudaSuccess) return e;
       per_sm = v < 1 ? 1 : v;
     }
     int grid = num_sms * per_sm;
     if (grid > p.total_tiles) grid = p.total_tiles;
     count_launch();
-    raster_fwd_kernel<TW, TH, BATCH, true><<<grid, NT, 0, st>>>(p);
+    raster_fwd_kernel<TW, TH, BATCH, true, DIST><<<grid, NT, 0, st>>>(p);
   } else {
     count_launch();
-    raster_fwd_kernel<TW, TH, BATCH, false><<<p.total_tiles, NT, 0, st>>>(p);
+    raster_fwd_kernel<TW, TH, BATCH, false, DIST><<<p.total_tiles, NT, 0, st>>>(p);
   }
   return cudaGetLastError();
 }
 
 // The backward stages at most 224 splats per batch when the option asks for 256: its shared
 // accumulator is then 15 KB instead of 17 KB (measured 1.6 % faster on the 1M-splat batch).
-template <int TW, int TH, int BATCH_OPT>
+template <int TW, int TH, int BATCH_OPT, bool DIST>
 cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
   constexpr int BATCH = BATCH_OPT == 256 ? 224 : BATCH_OPT;
   constexpr int NT = TW * TH / 2;
@@ -660,27 +688,33 @@ cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cu
     if (per_sm == 0) {
       int v = 0;
       cudaError_t e =
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_bwd_kernel<TW, TH, BATCH, true>, NT, 0);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_bwd_kernel<TW, TH, BATCH, true, DIST>, NT, 0);
       if (e != cudaSuccess) return e;
       per_sm = v < 1 ? 1 : v;
     }
     int grid = num_sms * per_sm;
     if (grid > p.total_tiles) grid = p.total_tiles;
     count_launch();
-    raster_bwd_kernel<TW, TH, BATCH, true><<<grid, NT, 0, st>>>(p);
+    raster_bwd_kernel<TW, TH, BATCH, true, DIST><<<grid, NT, 0, st>>>(p);
   } else {
     count_launch();
-    raster_bwd_kernel<TW, TH, BATCH, false><<<p.total_tiles, NT, 0, st>>>(p);
+    raster_bwd_kernel<TW, TH, BATCH, false, DIST><<<p.total_tiles, NT, 0, st>>>(p);
   }
   return cudaGetLastError();
 }
 
-// Instantiates the launchers of one tile shape for both batch sizes.
+// Instantiates the launchers of one tile shape for both batch sizes, with and without the
+// distortion.
 #define SS_RASTER_DISPATCH(KIND, TW, TH)                                                                    \
   cudaError_t launch_raster_##KIND##_##TW##x##TH(const RasterParams& p, int batch, bool persistent,        \
                                                  int num_sms, cudaStream_t st) {                            \
-    if (batch == 128) return launch_##KIND##_t<TW, TH, 128>(p, persistent, num_sms, st);                    \
-    if (batch == 256) return launch_##KIND##_t<TW, TH, 256>(p, persistent, num_sms, st);                    \
+    const bool dist = p.distort != 0;                                                                        \
+    if (batch == 128)                                                                                        \
+      return dist ? launch_##KIND##_t<TW, TH, 128, true>(p, persistent, num_sms, st)                        \
+                  : launch_##KIND##_t<TW, TH, 128, false>(p, persistent, num_sms, st);                      \
+    if (batch == 256)                                                                                        \
+      return dist ? launch_##KIND##_t<TW, TH, 256, true>(p, persistent, num_sms, st)                        \
+                  : launch_##KIND##_t<TW, TH, 256, false>(p, persistent, num_sms, st);                      \
     return cudaErrorInvalidValue;                                                                            \
   }
 

@@ -26,10 +26,12 @@ class Target:
 
 class Outputs:
     """Planes of every render target: rgb (3,H,W) / depth (H,W) / normal (3,H,W) / alpha
-    (H,W) and the saved state T_final (H,W) f32 and last (H,W) int32 (uint32 bits)."""
+    (H,W) and the saved state T_final (H,W) f32 and last (H,W) int32 (uint32 bits).  With
+    ``distortion`` the main targets also get the distortion plane distort (H,W)."""
 
-    def __init__(self, targets: Sequence[Target], device):
+    def __init__(self, targets: Sequence[Target], device, distortion: bool = False):
         self.rgb, self.depth, self.normal, self.alpha, self.T_final, self.last = [], [], [], [], [], []
+        self.distort = []
         for t in targets:
             H, W = t.height, t.width
             f = lambda *s: torch.empty(*s, device=device, dtype=torch.float32)
@@ -39,6 +41,7 @@ class Outputs:
             self.alpha.append(f(H, W))
             self.T_final.append(f(H, W))
             self.last.append(torch.empty(H, W, device=device, dtype=torch.int32))
+            self.distort.append(f(H, W) if distortion and not t.sun else None)
 
     def io_array(self, upstream: Optional[dict] = None):
         n = len(self.depth)
@@ -48,12 +51,14 @@ class Outputs:
             a.rgb, a.depth, a.normal, a.alpha = (L.ptr(self.rgb[i]), L.ptr(self.depth[i]),
                                                  L.ptr(self.normal[i]), L.ptr(self.alpha[i]))
             a.T_final, a.last = L.ptr(self.T_final[i]), L.ptr(self.last[i])
+            a.distort = L.ptr(self.distort[i])
             if upstream is not None:
                 u = upstream[i]
                 a.d_rgb = L.ptr(u.get("rgb"))
                 a.d_depth = L.ptr(u.get("depth"))
                 a.d_normal = L.ptr(u.get("normal"))
                 a.d_alpha = L.ptr(u.get("alpha"))
+                a.d_distort = L.ptr(u.get("distort"))
         return arr
 
 
@@ -73,14 +78,17 @@ def n_pad_of(n: int) -> int:
 
 
 class Frame:
+    """``distortion``: the main targets' outputs include the distortion plane."""
+
     def __init__(self, cameras: Sequence, passes: int = L.SS_PASS_MAIN, opts: Optional[L.ss_raster_opts] = None,
-                 capacity: Optional[int] = None, device="cuda"):
+                 capacity: Optional[int] = None, device="cuda", distortion: bool = False):
         self.cam_objs = list(cameras)
         self.cams = L.make_cameras(self.cam_objs)
         self.n_cams = len(self.cam_objs)
         self.passes = int(passes)
         self.opts = opts if opts is not None else L.default_opts()
         self.device = torch.device(device)
+        self.distortion = bool(distortion)
         self.targets: List[Target] = []
         if self.passes & L.SS_PASS_MAIN:
             self.targets += [Target(i, False, c.width, c.height) for i, c in enumerate(self.cam_objs)]
@@ -132,7 +140,7 @@ class Frame:
     def forward(self, splats: L.ss_splats, dF=None, color=None, out: Optional[Outputs] = None,
                 sync: bool = True, stream=None) -> Outputs:
         self.project_and_bin(splats, dF, color, sync=sync, stream=stream)
-        out = out if out is not None else Outputs(self.targets, self.device)
+        out = out if out is not None else Outputs(self.targets, self.device, self.distortion)
         io = out.io_array()
         L.rasterize_fwd(splats, self.cams, self.n_cams, self.passes, self.opts, io, self.ws,
                         self.ws_bytes, self.capacity, stream)

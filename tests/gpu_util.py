@@ -81,6 +81,11 @@ def grad_close(g: np.ndarray, ref: np.ndarray, rtol=GRAD_TOL, name="", floor=1e-
         return 0.0
     d = np.abs(g - ref)
     assert d.max() <= rtol * scale, f"{name}: max err {d.max():.3e} vs {rtol * scale:.3e}"
-    bad = d > rtol * (np.abs(ref) + floor * scale)
-    assert not bad.any(), f"{name}: {bad.sum()} elements outside the per-element bound; worst {d.max():.3e}"
+    bound = rtol * (np.abs(ref) + floor * scale)
+    bad = d > bound
+    if bad.any():
+        i = int(np.argmax(np.where(bad, d / bound, 0.0)))
+        raise AssertionError(f"{name}: {bad.sum()} elements outside the per-element bound; worst at {i}: "
+                             f"got {g.flat[i]:.6e}, oracle {ref.flat[i]:.6e}, bound {bound.flat[i]:.3e}, "
+                             f"largest |oracle| {scale:.3e}")
     return float(d.max() / scale)
