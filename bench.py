@@ -74,7 +74,7 @@ def parse():
                     help="skip timing the step with the distortion plane")
     ap.add_argument("--storage", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--profile", action="store_true",
-                    help="short run for a profiler: no tuning, plain, e2e or CPU arms")
+                    help="short run for a profiler: no tuning, plain, e2e, CPU or distortion arms")
     return ap.parse_args()
 
 
@@ -462,7 +462,7 @@ def run_ours(args, dist):
     L.load()
     sms, arch = L.device_info()
     if args.profile:
-        args.no_plain = args.no_cpu = args.no_e2e = args.no_tune = True
+        args.no_plain = args.no_cpu = args.no_e2e = args.no_tune = args.no_distortion = True
 
     scene = scenegen.workload(args.workload, seed=dist.rank)
     cams = scene.cameras
