@@ -139,7 +139,7 @@ typedef struct {
  *           pixel's walk in the sorted intersection list
  *   d_rgb, d_depth, d_normal, d_alpha  upstream gradients (backward; NULL = 0)
  *   distort  distortion of the blending weights along the pixel's ray, the
- *           point-sample distortion that Sec. 4 adds to the training loss:
+ *           point-sample distortion that Supp. B adds to the training loss:
  *           sum over composited pairs j before i of 2 w_i w_j (z_i - z_j), with
  *           w_i the blending weight and z_i the intersection depth; it equals
  *           sum_{i,j} w_i w_j |z_i - z_j| where the compositing order is the order

@@ -178,7 +178,7 @@ def render(sc: SceneF64, cam, sun=False, opts: Opts = Opts(), crop=None, brute=F
            dF=None, color=None):
     """Forward render of a view (or its sun view).  Returns a dict of float64 planes:
     rgb (3,h,w), depth, normal (3,h,w), alpha, distort (the distortion of the blending weights
-    along the ray, Sec. 4), T, margin_fwd, margin_bwd and int32 ncontrib / terminated.
+    along the ray, Supp. B), T, margin_fwd, margin_bwd and int32 ncontrib / terminated.
     ``color`` is the 3x4 [C|c] (identity for sun views)."""
     x0, y0, w, h = _crop(cam, sun, crop)
     rec = camera_record(cam, dF=dF, color=color)

@@ -28,7 +28,7 @@
  *   - distortion of the blending weights along the ray: the sum over composited
  *     pairs j before i of 2 w_i w_j (z_i - z_j), w_i = a_i G^_i T_i and z_i the
  *     depth of the ray-splat intersection (the point-sample distortion loss that
- *     Sec. 4 adds to the training loss, in compositing order; it equals
+ *     Supp. B adds to the training loss, in compositing order; it equals
  *     sum_{i,j} w_i w_j |z_i - z_j| when that order is the order of z)
  * Readings where the paper is silent (alpha threshold 1/255, clamp 0.99, early
  * stop at T < 1e-4 excluding the stopping splat, ties by splat index, pixel

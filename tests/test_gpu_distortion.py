@@ -1,5 +1,5 @@
 """Distortion of the blending weights (the point-sample distortion that the training loss of
-Sec. 4 adds) on the CUDA path against the FP64 oracle, through the C ABI, the batched graph
+Supp. B adds) on the CUDA path against the FP64 oracle, through the C ABI, the batched graph
 step and the autograd form."""
 import numpy as np
 import pytest

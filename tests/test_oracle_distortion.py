@@ -1,5 +1,5 @@
 """Pins of the oracle's distortion plane (the point-sample distortion of the blending weights
-along each ray, which the training loss of Sec. 4 adds), checked against closed forms on
+along each ray, which the training loss of Supp. B adds), checked against closed forms on
 hand-built stacks of flat splats and against invariances of the definition.  The adjoint of
 the plane is checked against dual numbers and central differences with the rest of the
 rasterizer adjoint in ``test_oracle_pins.py``."""
