@@ -340,6 +340,67 @@ def measure_distortion(torch, mk, ups, reps: int, walked: int, base_ms: dict, pe
                              "frac": bw / peak_tflops, "flops_per_pair": FLOPS_BWD_PER_PAIR_DIST}}
 
 
+def measure_optimizer(torch, n: int, grads: dict, storage_dtype, reps: int):
+    """The fused Adam step (with the position noise) over the step's n splats, with CUDA events,
+    and one 3DGS-MCMC relocation with 5 % growth and about 5 % dead splats (host timer: the call
+    synchronises).  HBM roofline of the Adam step from its algorithmic bytes per splat: 13
+    gradients, 13 raw values and 26 moments read, 13 raw values and 26 moments written (4 B
+    each), and 13 stored values written (2 B in BF16, 4 B in FP32)."""
+    from paper_2606_28581_gb300 import _lib as L
+    from paper_2606_28581_gb300.frame import n_pad_of
+    cap = n + n // 20
+    n_pad = max(n_pad_of(cap), int(grads["means"].shape[-1]))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(99)
+    rows = dict(means=3, log_scales=2, quats=4, logit_opacity=1, rgb=3)
+    mk = lambda s: {k: torch.randn(c, n_pad, device="cuda", generator=g) * s for k, c in rows.items()}
+    raw, m, v = mk(0.3), mk(1e-2), mk(1e-2)
+    v = {k: t.abs() for k, t in v.items()}
+    raw["log_scales"].mul_(0.1).add_(-6.0)
+    gpad = {k: torch.zeros(t.shape[0], n_pad, device="cuda") for k, t in grads.items()}
+    for k, t in grads.items():
+        gpad[k][:, : t.shape[-1]] = t
+    st = {k: torch.zeros(c, n_pad, device="cuda", dtype=storage_dtype)
+          for k, c in dict(means=3, scales=2, quats=4, opacity=1, rgb=3).items()}
+    storage = L.make_splats(st["means"], st["scales"], st["quats"], st["opacity"], st["rgb"], n)
+    P = lambda d: L.make_params(d["means"], d["log_scales"], d["quats"], d["logit_opacity"], d["rgb"])
+    pp, pm, pv = P(raw), P(m), P(v)
+    gs = L.ss_splat_grads()
+    gs.means, gs.scales, gs.quats, gs.opacity, gs.rgb = (L.ptr(gpad[k]) for k in ("means", "scales", "quats",
+                                                                                   "opacity", "rgb"))
+    gs.n_pad = n_pad
+    it = [0]
+
+    def adam():
+        it[0] += 1
+        L.adam_step(pp, pm, pv, gs, storage, L.default_adam_opts(step=it[0]))
+
+    for _ in range(3):
+        adam()
+    ms = time_loop(torch, adam, reps)
+    per_splat = 4 * (13 + 13 + 26 + 13 + 26) + 13 * (2 if storage_dtype == torch.bfloat16 else 4)
+    peak, basis = hbm_peak_gbs()
+    gbs = n * per_splat / (ms * 1e-3) / 1e9
+    # relocation: about 5 % of the splats dead, 5 % growth
+    ws = torch.empty(L.mcmc_workspace_size(cap), dtype=torch.uint8, device="cuda")
+    logit0 = raw["logit_opacity"].clone()
+    dead = torch.rand(n_pad, device="cuda", generator=g) < 0.05
+    rl = []
+    for r in range(3):
+        raw["logit_opacity"].copy_(logit0)
+        raw["logit_opacity"][0, dead] = -8.0
+        st["opacity"].copy_(torch.sigmoid(raw["logit_opacity"]).to(storage_dtype))
+        storage.n = n
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_after = L.mcmc_relocate(pp, pm, pv, storage, cap, L.default_mcmc_opts(step=r), ws)
+        rl.append((time.perf_counter() - t0) * 1e3)
+    return {"bound": "hbm", "splats": n, "adam_ms": float(ms), "adam_bytes_per_splat": per_splat,
+            "adam_gbs": gbs, "peak_gbs": peak, "peak_basis": basis, "adam_frac": gbs / peak,
+            "relocate_ms": float(np.median(rl)), "relocate_n_after": int(n_after), "relocate_cap": int(cap),
+            "relocate_note": "host-timed, includes the one stream synchronisation of the call"}
+
+
 def measure_depth_normal(torch, step, reps: int):
     """Forward and backward of the depth-gradient normal (K8) over every main view of the step;
     HBM roofline from the algorithmic bytes per main pixel (forward: depth and alpha read, N
@@ -547,6 +608,7 @@ def run_ours(args, dist):
     # ---- sun visibility and image formation (K7), depth-gradient normals (K8), timed alone
     shade = measure_shade(torch, step, k_steps)
     dnormal = measure_depth_normal(torch, step, k_steps)
+    optimizer = measure_optimizer(torch, scene.n, step.grads, storage, k_steps)
     distortion = None
     if not args.no_distortion:
         mk_d = lambda u: BatchedStep(cams, splats, scene.n, dF, color, u, passes=passes, opts=opts,
@@ -655,7 +717,7 @@ def run_ours(args, dist):
                 "roofline": roofline, "cpu_baseline": cpu, "plain_fp32": plain,
                 "batched_over_plain": (value / dist.world) / plain["value"] if plain else None,
                 "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-                "shade": shade, "depth_normal": dnormal, "distortion": distortion,
+                "shade": shade, "depth_normal": dnormal, "distortion": distortion, "optimizer": optimizer,
                 "steps_per_s": 1e3 / ms_max, "peak_hbm_gb": peak_hbm_gb,
                 "device": {"sms": sms, "arch": arch, "name": torch.cuda.get_device_name()}}
         print(json.dumps(line), flush=True)

@@ -360,6 +360,105 @@ ss_status ss_depth_normal_fwd(const ss_camera* cams, int32_t n_cams, const float
 ss_status ss_depth_normal_bwd(const ss_camera* cams, int32_t n_cams, const float* dF, float alpha_eps,
                               const ss_dnormal_io* io, float* d_dF, ss_stream_t stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Optimiser step (training).  SatSplat trains with Adam at per-group learning rates (Supp. B)
+ * and relocates splats with the 3DGS-MCMC strategy under a bounded splat quota (Sec. 3.5,
+ * Sec. 4.4); the update rules are those of the cited works (Adam: Kingma and Ba, Algorithm 1;
+ * position noise and relocation: Kheradmand et al., 3D Gaussian Splatting as Markov Chain
+ * Monte Carlo).  Random numbers come from Philox4x64-10 (Salmon et al., SC'11) with key
+ * (seed, 0) and counter (index, step, stream, 0): stream 0 draws the position noise of splat
+ * `index`, stream 1 the source of relocation target `index`.
+ * --------------------------------------------------------------------------------------- */
+
+/* Raw (pre-activation) splat parameters, and Adam's moments laid out the same way: FP32 DEVICE
+ * arrays [C][n_pad], 16-byte aligned, n_pad a multiple of 8:
+ *   means [3], log_scales [2] (s = exp(x)), quats [4] (unnormalised),
+ *   logit_opacity [1] (o = 1 / (1 + exp(-x))), rgb [3] (identity). */
+typedef struct {
+  float* means;
+  float* log_scales;
+  float* quats;
+  float* logit_opacity;
+  float* rgb;
+  int64_t n_pad;
+} ss_splat_params;
+
+/* Adam options.  ss_default_adam_opts() fills the defaults in brackets (learning rates of
+ * Supp. B; the opacity rate, which it does not list, and eps follow 3D Gaussian splatting). */
+typedef struct {
+  float lr_means, lr_scales, lr_quats, lr_opacity, lr_rgb; /* [0.075, 0.001, 0.001, 0.05, 0.0025] */
+  float beta1, beta2, eps;                                 /* [0.9, 0.999, 1e-15] */
+  float noise_lr; /* [5e5] scale of the position noise; 0 = no noise */
+  float noise_k;  /* [100] steepness of the noise gate sigmoid(-k (o - t)) */
+  float noise_t;  /* [0.005] opacity at which the gate is 1/2 */
+  int32_t step;   /* Adam step t >= 1 (bias correction and the noise counter) */
+  uint64_t seed;  /* [0] */
+} ss_adam_opts;
+
+void ss_default_adam_opts(ss_adam_opts* opts);
+
+/* One fused optimiser step over the splats 0..storage->n-1, in place:
+ *   - the rasterizer's gradients `grads` (with respect to the activated values) are chained
+ *     through the activations (d log s = s ds, d logit o = o (1 - o) do);
+ *   - Adam with bias correction on every raw parameter:
+ *       m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ *       x -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps);
+ *   - then the 3DGS-MCMC position noise from the updated parameters:
+ *       mu += lr_means noise_lr sigmoid(-k (o - t)) Sigma eta, eta ~ N(0, I) (Box-Muller on
+ *       Philox uniforms ((x >> 40) + 0.5) 2^-24), Sigma = R diag(s_u^2, s_v^2, 0) R^T
+ *       (a surfel's covariance: the noise stays in its plane);
+ *   - the activated values are written to the rasterizer's storage arrays `storage` (fp32
+ *     or bf16, rounded to nearest even): its pointers are WRITTEN here.
+ * params, exp_avg, exp_avg_sq, grads and storage must share n_pad.  One launch, no
+ * workspace.  Errors: SS_ERR_INVALID_ARG (pointers, alignment, n_pad, options). */
+ss_status ss_adam_step(const ss_splat_params* params, const ss_splat_params* exp_avg,
+                       const ss_splat_params* exp_avg_sq, const ss_splat_grads* grads,
+                       const ss_splats* storage, const ss_adam_opts* opts, ss_stream_t stream);
+
+/* Adam (no noise) over a flat FP32 DEVICE array of n values, in place: the per-camera deltas
+ * (Supp. B: lr 1e-4) and colour corrections (lr 1e-3).  Uses beta1, beta2, eps and step of
+ * `opts`.  Errors: SS_ERR_INVALID_ARG. */
+ss_status ss_adam_flat(float* param, float* exp_avg, float* exp_avg_sq, const float* grad, int64_t n,
+                       float lr, const ss_adam_opts* opts, ss_stream_t stream);
+
+/* 3DGS-MCMC relocation options.  ss_default_mcmc_opts() fills the defaults in brackets. */
+typedef struct {
+  float min_opacity; /* [0.005] a splat is dead iff its stored opacity <= min_opacity */
+  float growth;      /* [0.05] growth per call: min(cap - n, floor(n growth)) new splats */
+  int32_t n_max;     /* [51] largest copy count N in the opacity and scale rule */
+  int32_t step;      /* counter word of the draws (e.g. the index of this relocation) */
+  uint64_t seed;     /* [0] */
+} ss_mcmc_opts;
+
+void ss_default_mcmc_opts(ss_mcmc_opts* opts);
+
+/* Bytes of device workspace ss_mcmc_relocate needs for a budget of `cap` splats.  Host only.
+ * Errors: SS_ERR_INVALID_ARG when cap < 1 or cap >= 2^31. */
+ss_status ss_mcmc_workspace_size(int64_t cap, size_t* bytes);
+
+/* 3DGS-MCMC relocation and growth, in place, for the splats 0..storage->n-1 (n = the active
+ * count) under the budget `cap`:
+ *   - dead splats (stored opacity <= min_opacity) and the new slots n..n_after-1,
+ *     n_after = n + min(cap - n, floor(n growth)), are the targets, in that order;
+ *   - target j takes a live source drawn with probability proportional to opacity: integer
+ *     weights floor(o 2^24) of the stored opacities, r = floor(x W / 2^64) for the total W
+ *     and the first Philox word x of counter (j, step, 1, 0), and the source is the last splat
+ *     whose exclusive prefix sum of weights is <= r (exact integer arithmetic);
+ *   - a source drawn c times gets, with N = min(c + 1, n_max), o' = 1 - (1 - o)^(1/N)
+ *     (clamped to [min_opacity, 1 - 2^-23]) and s' = s o / sum_{j=1}^{N} (-1)^(j-1) C(N, j)
+ *     o'^j / sqrt(j) (the relocation rule, its double sum collapsed), in FP64;
+ *   - every target then copies its source's raw parameters, and the moments of the sources
+ *     and the targets are zeroed; the storage arrays are rewritten for them.
+ * When no splat is alive nothing changes and n_after = n.  params, moments and storage need
+ * n_pad >= cap.  SYNCHRONISES the stream once (it reads the dead count and the total weight
+ * before sizing the draws).  *n_after (host) receives the new active count.  d_stats, if not
+ * NULL, is a DEVICE int64 [2] that receives (dead count, total weight W).
+ * Errors: SS_ERR_INVALID_ARG (pointers, sizes, options, workspace), SS_ERR_CUDA. */
+ss_status ss_mcmc_relocate(const ss_splat_params* params, const ss_splat_params* exp_avg,
+                           const ss_splat_params* exp_avg_sq, const ss_splats* storage, int64_t cap,
+                           const ss_mcmc_opts* opts, void* ws, size_t ws_bytes, int64_t* n_after,
+                           int64_t* d_stats, ss_stream_t stream);
+
 /* Status block of a frame's workspace.  SYNCHRONISES the stream.
  *   needed:    intersections the last ss_bin_and_sort needed
  *   nonfinite: splats culled for non-finite values by the last projection

@@ -105,12 +105,22 @@ def activated(raw: dict) -> dict:
                 opacity=sigmoid(raw["logit_opacity"]), rgb=raw["rgb"].copy())
 
 
+def adam_update(x, m, v, g, lr: float, beta1: float, beta2: float, eps: float, step: int):
+    """Adam with bias correction (Kingma and Ba, Algorithm 1) on arrays; returns (x, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    return x - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
 def adam_step(raw: dict, m: dict, v: dict, grads: dict, lr: dict, beta1: float, beta2: float, eps: float,
               step: int, noise_lr: float = 0.0, noise_k: float = 100.0, noise_t: float = 0.005,
-              seed: int = 0):
+              seed: int = 0, index=None):
     """One optimiser step on copies of the raw parameters and moments ([C][n] float64 dicts).
     `grads` are with respect to the activated values (keys means, scales, quats, opacity, rgb);
-    `lr` is keyed by raw parameter name.  Returns (raw, m, v, storage)."""
+    `lr` is keyed by raw parameter name.  `index` gives the splat index of each column (the
+    counter of its noise draw; default 0..n-1).  Returns (raw, m, v, storage)."""
     raw = {k: np.array(a, np.float64) for k, a in raw.items()}
     m = {k: np.array(a, np.float64) for k, a in m.items()}
     v = {k: np.array(a, np.float64) for k, a in v.items()}
@@ -120,23 +130,23 @@ def adam_step(raw: dict, m: dict, v: dict, grads: dict, lr: dict, beta1: float, 
     o = sigmoid(raw["logit_opacity"])
     g["logit_opacity"] = g["logit_opacity"] * o * (1.0 - o)
     for k in raw:
-        m[k] = beta1 * m[k] + (1.0 - beta1) * g[k]
-        v[k] = beta2 * v[k] + (1.0 - beta2) * g[k] * g[k]
-        m_hat = m[k] / (1.0 - beta1 ** step)
-        v_hat = v[k] / (1.0 - beta2 ** step)
-        raw[k] = raw[k] - lr[k] * m_hat / (np.sqrt(v_hat) + eps)
+        raw[k], m[k], v[k] = adam_update(raw[k], m[k], v[k], g[k], lr[k], beta1, beta2, eps, step)
     if noise_lr != 0.0:
-        raw["means"] = raw["means"] + position_noise(raw, lr["means"], noise_lr, noise_k, noise_t, step, seed)
+        raw["means"] = raw["means"] + position_noise(raw, lr["means"], noise_lr, noise_k, noise_t, step, seed,
+                                                     index)
     return raw, m, v, activated(raw)
 
 
-def position_noise(raw: dict, lr_means: float, noise_lr: float, k: float, t: float, step: int, seed: int):
-    """lr_means * noise_lr * sigmoid(-k (o - t)) * Sigma eta for every splat ([3, n])."""
+def position_noise(raw: dict, lr_means: float, noise_lr: float, k: float, t: float, step: int, seed: int,
+                   index=None):
+    """lr_means * noise_lr * sigmoid(-k (o - t)) * Sigma eta for every splat ([3, n]); column c
+    draws with the counter of splat index[c] (default c)."""
     n = raw["means"].shape[1]
+    idx = range(n) if index is None else [int(i) for i in index]
     o = sigmoid(raw["logit_opacity"][0])
     s = np.exp(raw["log_scales"])
     R = rotation(raw["quats"])
-    eta = np.array([noise_normals(i, step, seed) for i in range(n)]).T  # [3, n]
+    eta = np.array([noise_normals(i, step, seed) for i in idx]).T  # [3, n]
     out = np.zeros((3, n))
     for i in range(n):
         Sigma = R[:, :, i] @ np.diag([s[0, i] ** 2, s[1, i] ** 2, 0.0]) @ R[:, :, i].T

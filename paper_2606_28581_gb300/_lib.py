@@ -70,11 +70,28 @@ class ss_splat_grads(ctypes.Structure):
                 ("n_pad", ctypes.c_int64)]
 
 
+class ss_splat_params(ctypes.Structure):
+    _fields_ = [("means", P), ("log_scales", P), ("quats", P), ("logit_opacity", P), ("rgb", P),
+                ("n_pad", ctypes.c_int64)]
+
+
+class ss_adam_opts(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("lr_means", "lr_scales", "lr_quats", "lr_opacity", "lr_rgb", "beta1",
+                                               "beta2", "eps", "noise_lr", "noise_k", "noise_t")] + \
+               [("step", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class ss_mcmc_opts(ctypes.Structure):
+    _fields_ = [("min_opacity", ctypes.c_float), ("growth", ctypes.c_float), ("n_max", ctypes.c_int32),
+                ("step", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 EXPORTS = ["ss_default_opts", "ss_status_string", "ss_workspace_size", "ss_project_splats",
            "ss_bin_and_sort", "ss_rasterize_fwd", "ss_rasterize_bwd", "ss_project_bwd", "ss_shadow_depth",
            "ss_frame_status", "ss_device_info", "ss_kernel_launches", "ss_render_fwd_noalloc",
            "ss_noalloc_scratch_bytes", "ss_default_shade_opts", "ss_shade_fwd", "ss_shade_bwd",
-           "ss_depth_normal_fwd", "ss_depth_normal_bwd"]
+           "ss_depth_normal_fwd", "ss_depth_normal_bwd", "ss_default_adam_opts", "ss_adam_step", "ss_adam_flat",
+           "ss_default_mcmc_opts", "ss_mcmc_workspace_size", "ss_mcmc_relocate"]
 
 _lock = threading.Lock()
 _lib = None
@@ -128,9 +145,19 @@ def load(path: Optional[str] = None):
         PNI = ctypes.POINTER(ss_dnormal_io)
         L.ss_depth_normal_fwd.argtypes = [PC, I32, P, ctypes.c_float, PNI, P]
         L.ss_depth_normal_bwd.argtypes = [PC, I32, P, ctypes.c_float, PNI, P, P]
+        PPA, PAO, PMO = ctypes.POINTER(ss_splat_params), ctypes.POINTER(ss_adam_opts), ctypes.POINTER(ss_mcmc_opts)
+        L.ss_default_adam_opts.argtypes = [PAO]
+        L.ss_default_adam_opts.restype = None
+        L.ss_adam_step.argtypes = [PPA, PPA, PPA, PG, PS, PAO, P]
+        L.ss_adam_flat.argtypes = [P, P, P, P, I64, ctypes.c_float, PAO, P]
+        L.ss_default_mcmc_opts.argtypes = [PMO]
+        L.ss_default_mcmc_opts.restype = None
+        L.ss_mcmc_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
+        L.ss_mcmc_relocate.argtypes = [PPA, PPA, PPA, PS, I64, PMO, P, SZ, ctypes.POINTER(I64), P, P]
         for name in EXPORTS:
             if name not in ("ss_default_opts", "ss_status_string", "ss_device_info", "ss_kernel_launches",
-                            "ss_noalloc_scratch_bytes", "ss_default_shade_opts"):
+                            "ss_noalloc_scratch_bytes", "ss_default_shade_opts", "ss_default_adam_opts",
+                            "ss_default_mcmc_opts"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -335,3 +362,62 @@ def depth_normal_fwd(cams, n_cams: int, dF, alpha_eps: float, io, stream=None) -
 def depth_normal_bwd(cams, n_cams: int, dF, alpha_eps: float, io, d_dF=None, stream=None) -> None:
     _check(load().ss_depth_normal_bwd(cams, n_cams, ptr(dF), float(alpha_eps), io, ptr(d_dF), stream_ptr(stream)),
            "ss_depth_normal_bwd")
+
+
+# ------------------------------------------------------------------------------ optimiser step
+def default_adam_opts(**overrides) -> ss_adam_opts:
+    o = ss_adam_opts()
+    load().ss_default_adam_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def default_mcmc_opts(**overrides) -> ss_mcmc_opts:
+    o = ss_mcmc_opts()
+    load().ss_default_mcmc_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def make_params(means, log_scales, quats, logit_opacity, rgb) -> ss_splat_params:
+    """ss_splat_params over planar fp32 [C, n_pad] tensors (raw parameters or Adam moments)."""
+    import torch
+
+    ts = (means, log_scales, quats, logit_opacity, rgb)
+    for t in ts:
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("parameter rows must be contiguous float32 [C, n_pad] tensors")
+    p = ss_splat_params()
+    p.means, p.log_scales, p.quats, p.logit_opacity, p.rgb = (ptr(t) for t in ts)
+    p.n_pad = int(means.shape[-1])
+    return p
+
+
+def adam_step(params: ss_splat_params, exp_avg: ss_splat_params, exp_avg_sq: ss_splat_params, grads,
+              storage, opts: ss_adam_opts, stream=None) -> None:
+    _check(load().ss_adam_step(ctypes.byref(params), ctypes.byref(exp_avg), ctypes.byref(exp_avg_sq),
+                               ctypes.byref(grads), ctypes.byref(storage), ctypes.byref(opts), stream_ptr(stream)),
+           "ss_adam_step")
+
+
+def adam_flat(param, exp_avg, exp_avg_sq, grad, lr: float, opts: ss_adam_opts, stream=None) -> None:
+    _check(load().ss_adam_flat(ptr(param), ptr(exp_avg), ptr(exp_avg_sq), ptr(grad), int(param.numel()), float(lr),
+                               ctypes.byref(opts), stream_ptr(stream)), "ss_adam_flat")
+
+
+def mcmc_workspace_size(cap: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(load().ss_mcmc_workspace_size(int(cap), ctypes.byref(b)), "ss_mcmc_workspace_size")
+    return int(b.value)
+
+
+def mcmc_relocate(params: ss_splat_params, exp_avg: ss_splat_params, exp_avg_sq: ss_splat_params, storage,
+                  cap: int, opts: ss_mcmc_opts, ws, d_stats=None, stream=None) -> int:
+    """Relocation and growth in place; returns the new active count (synchronises the stream)."""
+    n_after = ctypes.c_int64(0)
+    _check(load().ss_mcmc_relocate(ctypes.byref(params), ctypes.byref(exp_avg), ctypes.byref(exp_avg_sq),
+                                   ctypes.byref(storage), int(cap), ctypes.byref(opts), ptr(ws), int(ws.numel()),
+                                   ctypes.byref(n_after), ptr(d_stats), stream_ptr(stream)), "ss_mcmc_relocate")
+    return int(n_after.value)

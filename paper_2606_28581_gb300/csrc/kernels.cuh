@@ -107,6 +107,10 @@ struct ScanPlan {
 ScanPlan plan_scan(int64_t n);
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, unsigned long long* scratch,
                                const ScanPlan& plan, unsigned long long* total, cudaStream_t st);
+// the same scan with 64-bit (unsaturated) outputs
+cudaError_t exclusive_scan_u32_u64(const uint32_t* in, unsigned long long* out, int64_t n,
+                                   unsigned long long* scratch, const ScanPlan& plan, unsigned long long* total,
+                                   cudaStream_t st);
 
 struct RadixPlan {
   int64_t capacity;     // max elements

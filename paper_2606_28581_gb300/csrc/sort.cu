@@ -106,13 +106,16 @@ ScanPlan plan_scan(int64_t n) {
   return p;
 }
 
-cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, unsigned long long* scratch,
-                               const ScanPlan& plan, unsigned long long* total, cudaStream_t st) {
+namespace {
+// uint32 in; Tout = uint32 (saturated) or uint64 out
+template <typename Tout>
+cudaError_t exclusive_scan_t(const uint32_t* in, Tout* out, int64_t n, unsigned long long* scratch,
+                             const ScanPlan& plan, unsigned long long* total, cudaStream_t st) {
   if (n == 0) return cudaMemsetAsync(total, 0, sizeof(unsigned long long), st);
   const int L = plan.levels;
   if (L == 0) {
     count_launch();
-    scan_down_kernel<uint32_t, uint32_t><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
+    scan_down_kernel<uint32_t, Tout><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
     return cudaGetLastError();
   }
   // up: block sums
@@ -136,9 +139,21 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uns
         scratch + plan.level_off[l + 1], nullptr);
   }
   count_launch();
-  scan_down_kernel<uint32_t, uint32_t><<<(unsigned)plan.level_n[0], kScanThreads, 0, st>>>(
+  scan_down_kernel<uint32_t, Tout><<<(unsigned)plan.level_n[0], kScanThreads, 0, st>>>(
       in, out, n, scratch + plan.level_off[0], nullptr);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, unsigned long long* scratch,
+                               const ScanPlan& plan, unsigned long long* total, cudaStream_t st) {
+  return exclusive_scan_t<uint32_t>(in, out, n, scratch, plan, total, st);
+}
+
+cudaError_t exclusive_scan_u32_u64(const uint32_t* in, unsigned long long* out, int64_t n,
+                                   unsigned long long* scratch, const ScanPlan& plan, unsigned long long* total,
+                                   cudaStream_t st) {
+  return exclusive_scan_t<unsigned long long>(in, out, n, scratch, plan, total, st);
 }
 
 // ------------------------------------------------------------------------------------------
