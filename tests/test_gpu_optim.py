@@ -206,3 +206,93 @@ def test_optimiser_rejects_bad_arguments():
         L.mcmc_relocate(p, p, p, storage, 1000, L.default_mcmc_opts(), ws)
     with pytest.raises(L.SatSplatError):
         L.mcmc_relocate(p, p, p, storage, n, L.default_mcmc_opts(n_max=52), ws)
+
+
+def test_full_size_adam_and_relocation_1M():
+    """The bench's optimiser workload: 1M splats, BF16 storage.  The Adam step is checked on 3000
+    sampled splats (the oracle draws their noise with their own indices); the relocation (about
+    5 % dead, 5 % growth under a budget of 1.05M) is checked on every splat."""
+    rng = np.random.default_rng(11)
+    n, cap = 1_000_000, 1_050_000
+    n_pad = n_pad_of(cap)
+    raw = _rand_params(rng, n_pad, n)
+    m = {k: (rng.normal(size=a.shape) * 1e-2).astype(np.float32) for k, a in raw.items()}
+    v = {k: (rng.uniform(size=a.shape) * 1e-4).astype(np.float32) for k, a in raw.items()}
+    g = {k: rng.normal(size=(c, n_pad)).astype(np.float32) for k, c in GRAD_ROWS.items()}
+    opts = L.default_adam_opts(step=3, seed=5)
+    tp, tm, tv, tg = _dev(raw), _dev(m), _dev(v), _dev(g)
+    st, storage = _storage(n, n_pad, torch.bfloat16)
+    grads = L.ss_splat_grads()
+    grads.means, grads.scales, grads.quats, grads.opacity, grads.rgb = (L.ptr(tg[k]) for k in GRAD_ROWS)
+    grads.n_pad = n_pad
+    L.adam_step(_params_struct(tp), _params_struct(tm), _params_struct(tv), grads, storage, opts)
+    torch.cuda.synchronize()
+    idx = np.sort(rng.choice(n, 3000, replace=False))
+    f32 = lambda x: float(np.float32(x))
+    lr = dict(means=f32(opts.lr_means), log_scales=f32(opts.lr_scales), quats=f32(opts.lr_quats),
+              logit_opacity=f32(opts.lr_opacity), rgb=f32(opts.lr_rgb))
+    sel = lambda d: {k: a[:, idx].astype(np.float64) for k, a in d.items()}
+    ora, om, ov, _ = O.adam_step(sel(raw), sel(m), sel(v), sel(g), lr, f32(opts.beta1), f32(opts.beta2),
+                                 f32(opts.eps), 3, noise_lr=f32(opts.noise_lr), noise_k=f32(opts.noise_k),
+                                 noise_t=f32(opts.noise_t), seed=5, index=idx)
+    for k in raw:
+        _close_update(to_np(tp[k])[:, idx], ora[k], raw[k][:, idx].astype(np.float64), "raw " + k,
+                      per_column=k == "means")
+        _close_update(to_np(tm[k])[:, idx], om[k], m[k][:, idx].astype(np.float64), "m " + k)
+    # relocation on the state the step left, with opacities redrawn so that about 5 % of the
+    # splats are dead
+    dead = torch.from_numpy(rng.uniform(size=n_pad) < 0.05).cuda()
+    tp["logit_opacity"].copy_(torch.from_numpy(rng.normal(0.0, 2.0, (1, n_pad)).astype(np.float32)).cuda())
+    tp["logit_opacity"][0, dead] = -8.0
+    st["opacity"].copy_(torch.sigmoid(tp["logit_opacity"]).to(torch.bfloat16))
+    before = {k: to_np(t) for k, t in tp.items()}
+    mb, vb = {k: to_np(t) for k, t in tm.items()}, {k: to_np(t) for k, t in tv.items()}
+    stored = to_np(st["opacity"])[0]
+    ws = torch.empty(L.mcmc_workspace_size(cap), dtype=torch.uint8, device="cuda")
+    mo = L.default_mcmc_opts(step=2, seed=8)
+    n_after = L.mcmc_relocate(_params_struct(tp), _params_struct(tm), _params_struct(tv), storage, cap, mo, ws)
+    torch.cuda.synchronize()
+    new, nm, nv, o_after, info = O.relocate(before, mb, vb, stored, n, cap, f32(mo.min_opacity), f32(mo.growth),
+                                            mo.n_max, 2, 8)
+    assert n_after == o_after == cap and len(info["targets"]) > 90_000
+    split = np.zeros(n_pad, bool)
+    split[info["targets"]] = True
+    split[list(info["counts"])] = True
+    for k in raw:
+        gk = to_np(tp[k])
+        if k in ("log_scales", "logit_opacity"):
+            np.testing.assert_array_equal(gk[:, ~split], new[k][:, ~split].astype(np.float32).astype(np.float64))
+            assert np.all(np.abs(gk[:, split] - new[k][:, split]) <= 2 * ULP32 * np.abs(new[k][:, split]) + 1e-30)
+        else:
+            np.testing.assert_array_equal(gk, new[k].astype(np.float32).astype(np.float64), err_msg=k)
+        np.testing.assert_array_equal(to_np(tm[k]), nm[k].astype(np.float32).astype(np.float64), err_msg=k)
+
+
+def test_training_loop_reduces_the_loss():
+    """A few dozen fused steps on a small scene (render, L2 loss on the colour, backward through the
+    C ABI, Adam, one relocation): the optimiser, the relocation and the rasterizer work together."""
+    import scenegen
+    from paper_2606_28581_gb300.frame import Frame
+    from paper_2606_28581_gb300.optim import SplatOptimizer
+    from tests.gpu_util import DeviceScene
+
+    scene = scenegen.make_scene(n=1500, extent_m=40.0, seed=51, views=[dict(width=64, height=64, off_nadir=10.0)])
+    ds = DeviceScene(scene)
+    frame = Frame(scene.cameras, L.SS_PASS_MAIN)
+    target = frame.forward(ds.splats, ds.dF, ds.color).rgb[0].clone()
+    rng = np.random.default_rng(52)
+    rgb0 = np.clip(scene.rgb + rng.normal(0, 0.2, scene.rgb.shape), 0.01, 0.99)
+    adam = L.default_adam_opts(lr_means=1e-4, lr_rgb=0.02, noise_lr=0.0)
+    opt = SplatOptimizer(scene.means, scene.scales, scene.quats, scene.opacity, rgb0, cap=1600,
+                         storage=torch.float32, adam=adam)
+    losses = []
+    for it in range(40):
+        out = frame.forward(opt.splats, ds.dF, ds.color)
+        diff = out.rgb[0] - target
+        losses.append(float((diff * diff).sum()))
+        opt.zero_grad()
+        frame.backward(opt.splats, out, [dict(rgb=2 * diff)], opt.grads)
+        opt.step()
+        if it == 20:
+            assert opt.relocate() >= 1500
+    assert losses[-1] < 0.3 * losses[0], losses[::8]
