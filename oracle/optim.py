@@ -72,6 +72,40 @@ def philox4x64(counter, key, rounds: int = 10):
     return c0, c1, c2, c3
 
 
+def _mulhilo64(a, b):
+    """(high, low) 64-bit words of the 128-bit products of uint64 arrays (32-bit limbs)."""
+    m32 = np.uint64(0xFFFFFFFF)
+    s32 = np.uint64(32)
+    a_lo, a_hi = a & m32, a >> s32
+    b_lo, b_hi = b & m32, b >> s32
+    ll, hl, lh, hh = a_lo * b_lo, a_hi * b_lo, a_lo * b_hi, a_hi * b_hi
+    cross = (ll >> s32) + (hl & m32) + (lh & m32)
+    hi = hh + (hl >> s32) + (lh >> s32) + (cross >> s32)
+    return hi, a * b
+
+
+def philox4x64_vec(c0, c1, c2, c3, k0: int, k1: int, rounds: int = 10):
+    """Philox4x64-R over uint64 counter arrays (the same generator as philox4x64, vectorised)."""
+    with np.errstate(over="ignore"):
+        c0, c1, c2, c3 = (np.asarray(c, np.uint64).copy() for c in (c0, c1, c2, c3))
+        k0, k1 = np.uint64(k0 & MASK64), np.uint64(k1 & MASK64)
+        m0, m1 = np.uint64(PHILOX_M0), np.uint64(PHILOX_M1)
+        for r in range(rounds):
+            if r > 0:
+                k0 = np.uint64((int(k0) + PHILOX_W0) & MASK64)
+                k1 = np.uint64((int(k1) + PHILOX_W1) & MASK64)
+            hi0, lo0 = _mulhilo64(np.full_like(c0, m0), c0)
+            hi1, lo1 = _mulhilo64(np.full_like(c2, m1), c2)
+            c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    return c0, c1, c2, c3
+
+
+def mulhi64_vec(a, b):
+    """floor(a b / 2^64) for uint64 arrays."""
+    with np.errstate(over="ignore"):
+        return _mulhilo64(np.asarray(a, np.uint64), np.asarray(b, np.uint64))[0]
+
+
 def uniform24(x: int) -> float:
     """A uniform in (0, 1) from the top 24 bits of a 64-bit word (exact in float32)."""
     return ((x >> 40) + 0.5) / float(1 << 24)

@@ -244,6 +244,51 @@ def workload(name: str, seed: int = 0, n: Optional[int] = None) -> Scene:
     raise ValueError(f"unknown workload {name!r}")
 
 
+@dataclasses.dataclass
+class DSM:
+    """A digital surface model on a north-up grid (world units): pixel (i, j) (column i, row j)
+    is the point (x0 + i gsd, y0 - j gsd, height[j, i]); rgb is its orthophoto colour."""
+    height: np.ndarray  # (H, W) float32
+    rgb: np.ndarray     # (3, H, W) float32
+    x0: float
+    y0: float
+    gsd: float
+    scale_m: float
+
+
+def make_dsm(*, size_px: int, extent_m: float, seed: int = 0, n_buildings: Optional[int] = None) -> DSM:
+    """A seeded synthetic DSM of a built-up area, in the world frame of ``make_scene``
+    (world = metres / (extent / 2)).
+
+    Recipe: the smooth terrain of ``make_splats`` (0-20 m); axis-aligned rectangular buildings
+    (footprints U[10, 60] m per side, heights U[5, 30] m above the terrain at their centre,
+    flat roofs), about one per 50 x 50 m; orthophoto: terrain colour a smooth function of
+    position plus N(0, 0.03) noise, one uniform colour per roof."""
+    rng = np.random.default_rng(seed)
+    scale_m = extent_m / 2.0
+    h = _height_field(rng, extent_m)
+    gsd_m = extent_m / size_px
+    c = (np.arange(size_px) + 0.5) * gsd_m - extent_m / 2
+    X, Y = np.meshgrid(c, -c)  # row j goes south
+    Z = h(X, Y)
+    rgb = np.stack([0.35 + 0.15 * np.sin(X / 37.0), 0.40 + 0.10 * np.cos(Y / 53.0),
+                    0.30 + 0.10 * np.sin((X + Y) / 71.0)])
+    rgb = rgb + rng.normal(0.0, 0.03, rgb.shape)
+    nb = n_buildings if n_buildings is not None else max(1, int((extent_m / 50.0) ** 2))
+    for _ in range(nb):
+        cx, cy = rng.uniform(-extent_m / 2, extent_m / 2, 2)
+        wx, wy = rng.uniform(10.0, 60.0, 2)
+        top = float(h(np.array([cx]), np.array([cy]))[0]) + rng.uniform(5.0, 30.0)
+        m = (np.abs(X - cx) <= wx / 2) & (np.abs(Y - cy) <= wy / 2)
+        Z = np.where(m, np.maximum(Z, top), Z)
+        col = rng.uniform(0.2, 0.9, 3)
+        for k in range(3):
+            rgb[k] = np.where(m, col[k], rgb[k])
+    return DSM(height=_f32(Z / scale_m), rgb=_f32(np.clip(rgb, 0.0, 1.0)),
+               x0=float(np.float32(c[0] / scale_m)), y0=float(np.float32(-c[0] / scale_m)),
+               gsd=float(np.float32(gsd_m / scale_m)), scale_m=scale_m)
+
+
 def to_bf16_exact(x: np.ndarray) -> np.ndarray:
     """Round float32 values to bfloat16 (nearest-even) and return them widened back to
     float32, i.e. exactly the values a BF16 store holds."""
