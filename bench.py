@@ -401,6 +401,30 @@ def measure_optimizer(torch, n: int, grads: dict, storage_dtype, reps: int):
             "relocate_note": "host-timed, includes the one stream synchronisation of the call"}
 
 
+def measure_init(torch, reps: int):
+    """The geometry-aware initialisation over a 2048 x 2048 DSM of 1 km^2 (0.5 m) with 1M
+    samples, with CUDA events around the whole call (weights, scan, draws, cell sort, kNN)."""
+    import scenegen
+    from paper_2606_28581_gb300 import _lib as L
+    from paper_2606_28581_gb300.frame import n_pad_of
+    dsm = scenegen.make_dsm(size_px=2048, extent_m=1000.0, seed=6)
+    Z = torch.from_numpy(dsm.height).cuda()
+    rgb = torch.from_numpy(dsm.rgb).cuda()
+    d = L.make_dsm(Z, rgb, dsm.x0, dsm.y0, dsm.gsd)
+    n = 1_000_000
+    n_pad = n_pad_of(n)
+    st = {k: torch.zeros(c, n_pad, device="cuda", dtype=torch.bfloat16)
+          for k, c in dict(means=3, scales=2, quats=4, opacity=1, rgb=3).items()}
+    out = L.make_splats(st["means"], st["scales"], st["quats"], st["opacity"], st["rgb"], n)
+    ws = torch.empty(L.init_workspace_size(d, n), dtype=torch.uint8, device="cuda")
+    opts = L.default_init_opts()
+    run = lambda: L.dsm_init(d, opts, out, ws)
+    run()
+    ms = time_loop(torch, run, reps)
+    return {"dsm_px": [2048, 2048], "samples": n, "ms": float(ms), "msamples_per_s": n / (ms * 1e-3) / 1e6,
+            "storage": "bf16"}
+
+
 def measure_depth_normal(torch, step, reps: int):
     """Forward and backward of the depth-gradient normal (K8) over every main view of the step;
     HBM roofline from the algorithmic bytes per main pixel (forward: depth and alpha read, N
@@ -609,6 +633,7 @@ def run_ours(args, dist):
     shade = measure_shade(torch, step, k_steps)
     dnormal = measure_depth_normal(torch, step, k_steps)
     optimizer = measure_optimizer(torch, scene.n, step.grads, storage, k_steps)
+    init = None if args.profile else measure_init(torch, 3)
     distortion = None
     if not args.no_distortion:
         mk_d = lambda u: BatchedStep(cams, splats, scene.n, dF, color, u, passes=passes, opts=opts,
@@ -718,6 +743,7 @@ def run_ours(args, dist):
                 "batched_over_plain": (value / dist.world) / plain["value"] if plain else None,
                 "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
                 "shade": shade, "depth_normal": dnormal, "distortion": distortion, "optimizer": optimizer,
+                "init": init,
                 "steps_per_s": 1e3 / ms_max, "peak_hbm_gb": peak_hbm_gb,
                 "device": {"sms": sms, "arch": arch, "name": torch.cuda.get_device_name()}}
         print(json.dumps(line), flush=True)

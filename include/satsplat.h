@@ -459,6 +459,52 @@ ss_status ss_mcmc_relocate(const ss_splat_params* params, const ss_splat_params*
                            const ss_mcmc_opts* opts, void* ws, size_t ws_bytes, int64_t* n_after,
                            int64_t* d_stats, ss_stream_t stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Geometry-aware initialisation (Sec. 3.4): splat centres sampled from a DSM with probability
+ * proportional to the local surface area, oriented by the DSM's local normal, sized by the
+ * mean distance to their nearest neighbours.  Runs once, before training.
+ * --------------------------------------------------------------------------------------- */
+
+/* A DSM on a north-up grid: pixel (i, j) (column i, row j) is the point
+ * (x0 + i gsd, y0 - j gsd, heights[j][i]) in world units.
+ *   heights  DEVICE [height_px][width] fp32
+ *   rgb      DEVICE [3][height_px][width] fp32 orthophoto colour, or NULL (0.5 grey) */
+typedef struct {
+  const float* heights;
+  const float* rgb;
+  int32_t width, height_px;
+  float x0, y0, gsd;
+} ss_dsm;
+
+typedef struct {
+  int32_t knn_k;   /* [3] neighbours of the scale estimate, 1..8 */
+  float opacity;   /* [0.1] initial opacity, in (0, 1) */
+  uint64_t seed;   /* [0] */
+} ss_init_opts;
+
+void ss_default_init_opts(ss_init_opts* opts);
+
+/* Bytes of device workspace ss_dsm_init needs for `n` samples of `dsm`.  Host only.
+ * Errors: SS_ERR_INVALID_ARG (sizes: width * height_px < 2^31, n < 2^31, gsd > 0). */
+ss_status ss_init_workspace_size(const ss_dsm* dsm, int64_t n, size_t* bytes);
+
+/* Draw out->n initial splats into the storage arrays `out` (fp32 or bf16; WRITTEN):
+ *   - per DSM pixel the tangents dx = (gsd, 0, dz_x) and dy = (0, gsd, dz_y), finite
+ *     differences toward +x and +y (central inside, one-sided on the border); the area
+ *     weight |dx x dy| as the integer w = floor(sqrt(dz_x^2 + dz_y^2 + gsd^2) 2^16 / gsd),
+ *     evaluated in fp32 with IEEE operations in that order;
+ *   - sample s draws Philox4x64-10 with key (seed, 0) and counter (s, 0, 2, 0): the pixel is
+ *     the last one whose exclusive prefix sum of weights is <= floor(x W / 2^64) (W the total),
+ *     and the centre is the pixel's point + u dx + v dy with u, v uniform in (-1/2, 1/2);
+ *   - the rotation [t_u t_v n]: t_u = dx / |dx|, t_v the Gram-Schmidt residual of dy,
+ *     n = t_u x t_v (the DSM normal), as a quaternion (w, x, y, z) with w >= 0;
+ *   - scales s_u = s_v = the mean distance to the knn_k nearest other samples (exact, by a
+ *     ring search over a uniform grid of cells); opacity = opts->opacity; rgb from the
+ *     orthophoto at the pixel.
+ * Requires out->n > knn_k.  Errors: SS_ERR_INVALID_ARG, SS_ERR_CUDA. */
+ss_status ss_dsm_init(const ss_dsm* dsm, const ss_init_opts* opts, const ss_splats* out, void* ws, size_t ws_bytes,
+                      ss_stream_t stream);
+
 /* Status block of a frame's workspace.  SYNCHRONISES the stream.
  *   needed:    intersections the last ss_bin_and_sort needed
  *   nonfinite: splats culled for non-finite values by the last projection

@@ -81,6 +81,15 @@ class ss_adam_opts(ctypes.Structure):
                [("step", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
+class ss_dsm(ctypes.Structure):
+    _fields_ = [("heights", P), ("rgb", P), ("width", ctypes.c_int32), ("height_px", ctypes.c_int32),
+                ("x0", ctypes.c_float), ("y0", ctypes.c_float), ("gsd", ctypes.c_float)]
+
+
+class ss_init_opts(ctypes.Structure):
+    _fields_ = [("knn_k", ctypes.c_int32), ("opacity", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
 class ss_mcmc_opts(ctypes.Structure):
     _fields_ = [("min_opacity", ctypes.c_float), ("growth", ctypes.c_float), ("n_max", ctypes.c_int32),
                 ("step", ctypes.c_int32), ("seed", ctypes.c_uint64)]
@@ -91,7 +100,8 @@ EXPORTS = ["ss_default_opts", "ss_status_string", "ss_workspace_size", "ss_proje
            "ss_frame_status", "ss_device_info", "ss_kernel_launches", "ss_render_fwd_noalloc",
            "ss_noalloc_scratch_bytes", "ss_default_shade_opts", "ss_shade_fwd", "ss_shade_bwd",
            "ss_depth_normal_fwd", "ss_depth_normal_bwd", "ss_default_adam_opts", "ss_adam_step", "ss_adam_flat",
-           "ss_default_mcmc_opts", "ss_mcmc_workspace_size", "ss_mcmc_relocate"]
+           "ss_default_mcmc_opts", "ss_mcmc_workspace_size", "ss_mcmc_relocate", "ss_default_init_opts",
+           "ss_init_workspace_size", "ss_dsm_init"]
 
 _lock = threading.Lock()
 _lib = None
@@ -154,10 +164,15 @@ def load(path: Optional[str] = None):
         L.ss_default_mcmc_opts.restype = None
         L.ss_mcmc_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
         L.ss_mcmc_relocate.argtypes = [PPA, PPA, PPA, PS, I64, PMO, P, SZ, ctypes.POINTER(I64), P, P]
+        PD, PIN = ctypes.POINTER(ss_dsm), ctypes.POINTER(ss_init_opts)
+        L.ss_default_init_opts.argtypes = [PIN]
+        L.ss_default_init_opts.restype = None
+        L.ss_init_workspace_size.argtypes = [PD, I64, ctypes.POINTER(SZ)]
+        L.ss_dsm_init.argtypes = [PD, PIN, PS, P, SZ, P]
         for name in EXPORTS:
             if name not in ("ss_default_opts", "ss_status_string", "ss_device_info", "ss_kernel_launches",
                             "ss_noalloc_scratch_bytes", "ss_default_shade_opts", "ss_default_adam_opts",
-                            "ss_default_mcmc_opts"):
+                            "ss_default_mcmc_opts", "ss_default_init_opts"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -421,3 +436,32 @@ def mcmc_relocate(params: ss_splat_params, exp_avg: ss_splat_params, exp_avg_sq:
                                    ctypes.byref(storage), int(cap), ctypes.byref(opts), ptr(ws), int(ws.numel()),
                                    ctypes.byref(n_after), ptr(d_stats), stream_ptr(stream)), "ss_mcmc_relocate")
     return int(n_after.value)
+
+
+# ------------------------------------------------------------------------------ initialisation
+def default_init_opts(**overrides) -> ss_init_opts:
+    o = ss_init_opts()
+    load().ss_default_init_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def make_dsm(heights, rgb, x0: float, y0: float, gsd: float) -> ss_dsm:
+    """ss_dsm over a device heights tensor (H, W) fp32 and an optional rgb (3, H, W) fp32."""
+    d = ss_dsm()
+    d.heights, d.rgb = ptr(heights), ptr(rgb)
+    d.height_px, d.width = int(heights.shape[0]), int(heights.shape[1])
+    d.x0, d.y0, d.gsd = float(x0), float(y0), float(gsd)
+    return d
+
+
+def init_workspace_size(dsm: ss_dsm, n: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(load().ss_init_workspace_size(ctypes.byref(dsm), int(n), ctypes.byref(b)), "ss_init_workspace_size")
+    return int(b.value)
+
+
+def dsm_init(dsm: ss_dsm, opts: ss_init_opts, out, ws, stream=None) -> None:
+    _check(load().ss_dsm_init(ctypes.byref(dsm), ctypes.byref(opts), ctypes.byref(out), ptr(ws), int(ws.numel()),
+                              stream_ptr(stream)), "ss_dsm_init")

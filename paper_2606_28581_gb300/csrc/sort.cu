@@ -281,11 +281,10 @@ cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_
                                                                        nblocks);
     cudaError_t e = exclusive_scan_u32(hist, hist_off, 256 * nblocks, scan_scratch, hs,
                                        scan_scratch + hs.scratch_elems - 1, st);
-    if (e != cudaSuccess) return e; {
+    if (e != cudaSuccess) return e;
     count_launch();
     radix_downsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n_host, n_dev, shift,
                                                                          mask, hist_off, nblocks);
-  }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uint32_t* t;

@@ -279,11 +279,16 @@ def make_dsm(*, size_px: int, extent_m: float, seed: int = 0, n_buildings: Optio
         cx, cy = rng.uniform(-extent_m / 2, extent_m / 2, 2)
         wx, wy = rng.uniform(10.0, 60.0, 2)
         top = float(h(np.array([cx]), np.array([cy]))[0]) + rng.uniform(5.0, 30.0)
-        m = (np.abs(X - cx) <= wx / 2) & (np.abs(Y - cy) <= wy / 2)
-        Z = np.where(m, np.maximum(Z, top), Z)
         col = rng.uniform(0.2, 0.9, 3)
-        for k in range(3):
-            rgb[k] = np.where(m, col[k], rgb[k])
+        # the pixels whose centres lie in the footprint (columns by x, rows by -y)
+        i0 = int(np.searchsorted(c, cx - wx / 2, side="left"))
+        i1 = int(np.searchsorted(c, cx + wx / 2, side="right"))
+        j0 = int(np.searchsorted(c, -(cy + wy / 2), side="left"))
+        j1 = int(np.searchsorted(c, -(cy - wy / 2), side="right"))
+        if i0 >= i1 or j0 >= j1:
+            continue
+        Z[j0:j1, i0:i1] = np.maximum(Z[j0:j1, i0:i1], top)
+        rgb[:, j0:j1, i0:i1] = col[:, None, None]
     return DSM(height=_f32(Z / scale_m), rgb=_f32(np.clip(rgb, 0.0, 1.0)),
                x0=float(np.float32(c[0] / scale_m)), y0=float(np.float32(-c[0] / scale_m)),
                gsd=float(np.float32(gsd_m / scale_m)), scale_m=scale_m)
