@@ -20,7 +20,10 @@
  *     s = (cos(phi)/tan(theta), sin(phi)/tan(theta), 1), rendering depth for
  *     shadow mapping (Sec. 3.3 Eq. sun_camera_Bxy; Supp. A);
  *   - per-camera 3x4 colour correction C A + c (Sec. 3.1 Eq. image_formation);
- *   - the reverse-mode adjoint of all of the above.
+ *   - the reverse-mode adjoint of all of the above;
+ *   - beside the rasterizer: the sun visibility and image formation, the depth-gradient
+ *     normal, the distortion of the blending weights, the optimiser step (Adam with the
+ *     3DGS-MCMC noise and relocation) and the geometry-aware DSM initialisation.
  * Constants the paper leaves open (alpha threshold, alpha clamp, early-stop
  * transmittance, sigma, det threshold) are fields of ss_raster_opts.
  *
