@@ -10,6 +10,18 @@ using namespace ss;
 namespace ss {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int device_sm_count() {
+  static int dev_sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (dev_sms[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    dev_sms[dev] = v;
+  }
+  return dev_sms[dev];
+}
 }  // namespace ss
 
 namespace {
@@ -189,17 +201,7 @@ ss_status check_ws(const Layout& L, void* ws, size_t ws_bytes) {
   return SS_OK;
 }
 
-int num_sms_cached() {
-  static int dev_sms[64] = {0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-  if (dev_sms[dev] == 0) {
-    int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
-    dev_sms[dev] = v;
-  }
-  return dev_sms[dev];
-}
+int num_sms_cached() { return device_sm_count(); }
 
 ProjectCommon common_of(const ss_splats* s, const Layout& L, void* ws) {
   ProjectCommon c;

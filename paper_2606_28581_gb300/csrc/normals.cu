@@ -1,7 +1,8 @@
 // Depth-gradient surface normal (K8), Sec. 3.2 Eq. surface_normal, and its adjoint.
 //
-// One block per 32 x 8 tile of a main view, one thread per pixel, every view in one launch
-// (blockIdx.y = view).  The point map
+// Blocks of 32 x 8 threads, one per pixel of a tile; every view in one launch (blockIdx.y = view),
+// and each block loops over tiles of its view, about as many blocks as the SMs hold at once
+// (one block per tile measured slower).  The point map
 // p_s = (X, Y, h) is affine in the pixel and in the height, so its central differences are
 //   grad_x p_s = a1 + (h(i+1) - h(i-1)) G,  grad_y p_s = a2 + (h(j+1) - h(j-1)) G,
 // with per-view a1 = (2 A^-1 e1, 0), a2 = (2 A^-1 e2, 0), G = (-A^-1 B'[:, 2], 1), A = B'[:, 0:2].
@@ -15,6 +16,7 @@
 #include "kernels.cuh"
 
 namespace ss {
+int device_sm_count();  // SMs of the current device (cached)
 
 struct NormalView {
   float F[2][4];  // host F_xy; dF is added on the device
@@ -93,9 +95,12 @@ __global__ void __launch_bounds__(kNX * kNY) depth_normal_fwd_kernel(const __gri
   const int cam = blockIdx.y;
   const NormalView& v = p.v[cam];
   const int bxs = (v.W + kNX - 1) / kNX;
-  const int by = blockIdx.x / bxs, bx = blockIdx.x - by * bxs;
-  if (by * kNY >= v.H) return;  // block-uniform: past this view's tiles
+  const int ntiles = bxs * ((v.H + kNY - 1) / kNY);
+  const NormalCam c = normal_cam(p, v, cam);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int by = tile / bxs, bx = tile - by * bxs;
   const int x0 = bx * kNX, y0 = by * kNY;
+  __syncthreads();  // the previous tile's reads of sz are done
   for (int k = threadIdx.x; k < (kNY + 2) * (kNX + 2); k += kNX * kNY) {
     const int ty = k / (kNX + 2), tx = k - ty * (kNX + 2);
     sz[ty][tx] = z_at(p, v, x0 - 1 + tx, y0 - 1 + ty);
@@ -103,8 +108,7 @@ __global__ void __launch_bounds__(kNX * kNY) depth_normal_fwd_kernel(const __gri
   __syncthreads();
   const int tx = threadIdx.x % kNX, ty = threadIdx.x / kNX;
   const int px = x0 + tx, py = y0 + ty;
-  if (px >= v.W || py >= v.H) return;
-  const NormalCam c = normal_cam(p, v, cam);
+  if (px >= v.W || py >= v.H) continue;
   const float zc = sz[ty + 1][tx + 1], zl = sz[ty + 1][tx], zr = sz[ty + 1][tx + 2], zu = sz[ty][tx + 1],
               zd = sz[ty + 2][tx + 1];
   float n[3] = {0.0f, 0.0f, 0.0f};
@@ -122,12 +126,15 @@ __global__ void __launch_bounds__(kNX * kNY) depth_normal_fwd_kernel(const __gri
   const int64_t hw = (int64_t)v.W * v.H, pix = (int64_t)py * v.W + px;
 #pragma unroll
   for (int k = 0; k < 3; ++k) v.io.normal[k * hw + pix] = n[k];
+  }  // tiles
 }
 
 // Gather form of the backward: a pixel's depth enters the normals of its four neighbours
 // (dhx = z(i-1) - z(i+1), dhy = z(j-1) - z(j+1)), so its gradient is
 // ddhx(i+1) - ddhx(i-1) + ddhy(j+1) - ddhy(j-1).  The block forms ddhx, ddhy once for the tile
-// and a halo of one pixel (from z staged with a halo of two), then every pixel gathers.
+// and a halo of one pixel (from z staged with a halo of two), then every pixel gathers.  Each
+// block loops over several tiles of its view (blockIdx.x, + gridDim.x, ...) and adds its
+// per-view sums to the camera gradient once.
 __global__ void __launch_bounds__(kNX * kNY) depth_normal_bwd_kernel(const __grid_constant__ NormalParams p) {
   __shared__ float sz[kNY + 4][kNX + 5];
   __shared__ float sdx[kNY + 2][kNX + 3], sdy[kNY + 2][kNX + 3];
@@ -135,18 +142,20 @@ __global__ void __launch_bounds__(kNX * kNY) depth_normal_bwd_kernel(const __gri
   const int cam = blockIdx.y;
   const NormalView& v = p.v[cam];
   const int bxs = (v.W + kNX - 1) / kNX;
-  const int by = blockIdx.x / bxs, bx = blockIdx.x - by * bxs;
-  if (by * kNY >= v.H) return;  // block-uniform: past this view's tiles
-  const int x0 = bx * kNX, y0 = by * kNY;
+  const int ntiles = bxs * ((v.H + kNY - 1) / kNY);
   const int64_t hw = (int64_t)v.W * v.H;
   const NormalCam c = normal_cam(p, v, cam);
+  // per-view sums over the tiles' own pixels: d A^-1 (4) and d G_xy (2)
+  float acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int by = tile / bxs, bx = tile - by * bxs;
+  const int x0 = bx * kNX, y0 = by * kNY;
+  __syncthreads();  // the previous tile's reads of the shared planes are done
   for (int k = threadIdx.x; k < (kNY + 4) * (kNX + 4); k += kNX * kNY) {
     const int ty = k / (kNX + 4), tx = k - ty * (kNX + 4);
     sz[ty][tx] = z_at(p, v, x0 - 2 + tx, y0 - 2 + ty);
   }
   __syncthreads();
-  // per-view sums over this tile's own pixels: d A^-1 (4) and d G_xy (2)
-  float acc[6] = {0, 0, 0, 0, 0, 0};
   for (int k = threadIdx.x; k < (kNY + 2) * (kNX + 2); k += kNX * kNY) {
     const int ty = k / (kNX + 2), tx = k - ty * (kNX + 2);  // halo-1 coordinates
     const int px = x0 - 1 + tx, py = y0 - 1 + ty;
@@ -204,6 +213,7 @@ __global__ void __launch_bounds__(kNX * kNY) depth_normal_bwd_kernel(const __gri
       }
     }
   }
+  }  // tiles
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
@@ -277,6 +287,19 @@ dim3 normal_grid(const ss_camera* cams, int32_t n_cams) {
   return dim3((unsigned)most, (unsigned)n_cams);
 }
 
+// as many blocks in all as the SMs hold at once, each looping over tiles of its view
+template <class K>
+dim3 normal_loop_grid(const ss_camera* cams, int32_t n_cams, K kernel, int& per_sm) {
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kNX * kNY, 0) != cudaSuccess || v < 1) v = 1;
+    per_sm = v;
+  }
+  const dim3 full = normal_grid(cams, n_cams);
+  const int64_t want = ((int64_t)device_sm_count() * per_sm + n_cams - 1) / n_cams;
+  return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(full.x, want)), (unsigned)n_cams);
+}
+
 }  // namespace
 }  // namespace ss
 
@@ -290,7 +313,9 @@ ss_status ss_depth_normal_fwd(const ss_camera* cams, int32_t n_cams, const float
   ss_status e = fill_normal(p, cams, n_cams, dF, alpha_eps, io, false);
   if (e != SS_OK) return e;
   count_launch();
-  depth_normal_fwd_kernel<<<normal_grid(cams, n_cams), kNX * kNY, 0, (cudaStream_t)stream>>>(p);
+  static int per_sm = 0;
+  depth_normal_fwd_kernel<<<normal_loop_grid(cams, n_cams, depth_normal_fwd_kernel, per_sm), kNX * kNY, 0,
+                            (cudaStream_t)stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }
 
@@ -301,7 +326,9 @@ ss_status ss_depth_normal_bwd(const ss_camera* cams, int32_t n_cams, const float
   if (e != SS_OK) return e;
   p.d_dF = d_dF;
   count_launch();
-  depth_normal_bwd_kernel<<<normal_grid(cams, n_cams), kNX * kNY, 0, (cudaStream_t)stream>>>(p);
+  static int per_sm = 0;
+  depth_normal_bwd_kernel<<<normal_loop_grid(cams, n_cams, depth_normal_bwd_kernel, per_sm), kNX * kNY, 0,
+                            (cudaStream_t)stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }
 
