@@ -32,20 +32,23 @@ def _crops(frame, picks, seed):
     return out
 
 
-def _zero_upstream(frame):
+def _zero_upstream(frame, distortion=False):
     ups = []
     for t in frame.targets:
         z = lambda c: torch.zeros((c, t.height, t.width) if c > 1 else (t.height, t.width), device="cuda")
         u = dict(depth=z(1), alpha=z(1))
         if not t.sun:
             u.update(rgb=z(3), normal=z(3))
+            if distortion:
+                u["distort"] = z(1)
         ups.append(u)
     return ups
 
 
-def _check_step(scene, ds, frame, out, run_backward, upstream, crops, tol, seed):
+def _check_step(scene, ds, frame, out, run_backward, upstream, crops, tol, seed, distortion=False):
     """Forward planes of every crop against the oracle; then the backward with upstream
-    gradients inside the crops (margin pixels zeroed) against the oracle's crop adjoint."""
+    gradients inside the crops (margin pixels zeroed) against the oracle's crop adjoint.  With
+    ``distortion`` the main targets' distortion planes and their upstream are included."""
     s64 = ds.stored_scene64()
     rng = np.random.default_rng(seed)
     V = len(scene.cameras)
@@ -60,6 +63,10 @@ def _check_step(scene, ds, frame, out, run_backward, upstream, crops, tol, seed)
             gpu.update(rgb=to_np(out.rgb[ti]), normal=to_np(out.normal[ti]))
         _, exc = check_forward(gpu, ora, sun=t.sun, tol=tol, crop=crop, max_excluded=None)
         excluded.append(exc)
+        if distortion and not t.sun:
+            x0, y0, w, h = crop
+            dd = np.abs(to_np(out.distort[ti])[y0:y0 + h, x0:x0 + w] - ora["distort"])
+            assert dd[ora["margin_fwd"] >= MARGIN].max() <= tol, dd.max()
         # upstream inside the crop, zero on margin pixels
         x0, y0, w, h = crop
         keep = (ora["margin_bwd"] >= MARGIN).astype(np.float64)
@@ -67,6 +74,8 @@ def _check_step(scene, ds, frame, out, run_backward, upstream, crops, tol, seed)
         u_np = dict(depth=d * keep, alpha=a * keep)
         if not t.sun:
             u_np.update(rgb=r * keep, normal=n * keep)
+            if distortion:
+                u_np["distort"] = rng.normal(size=(h, w)) * keep
         for k, v in u_np.items():
             upstream[ti][k][..., y0:y0 + h, x0:x0 + w] = torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
         u64 = {k: np.asarray(v, np.float32).astype(np.float64) for k, v in u_np.items()}
@@ -87,13 +96,14 @@ def _check_step(scene, ds, frame, out, run_backward, upstream, crops, tol, seed)
     grad_close(d_color.cpu().numpy().astype(np.float64), ref["color_v"], name="color")
 
 
-def _batched_parity(name, picks, seed):
+def _batched_parity(name, picks, seed, distortion=False):
     scene = scenegen.workload(name)
     ds = DeviceScene(scene, dtype=torch.bfloat16)
     probe = Frame(scene.cameras, L.SS_PASS_MAIN | L.SS_PASS_SUN)
-    ups = _zero_upstream(probe)
+    ups = _zero_upstream(probe, distortion)
     splats = dict(means=ds.means, scales=ds.scales, quats=ds.quats, opacity=ds.opacity, rgb=ds.rgb)
-    step = BatchedStep(scene.cameras, splats, ds.n, ds.dF, ds.color, ups, opts=L.default_opts(persistent=1))
+    step = BatchedStep(scene.cameras, splats, ds.n, ds.dF, ds.color, ups, opts=L.default_opts(persistent=1),
+                       distortion=distortion)
     step.capture()
     step.replay()
     torch.cuda.synchronize()
@@ -106,13 +116,19 @@ def _batched_parity(name, picks, seed):
         torch.cuda.synchronize()
         return step.grads, step.d_dF, step.d_color
 
-    _check_step(scene, ds, step.frame, step.out, run_backward, ups, crops, BF16_TOL, seed)
+    _check_step(scene, ds, step.frame, step.out, run_backward, ups, crops, BF16_TOL, seed, distortion)
 
 
 def test_batched_1M_16_views_bf16_graph_step():
     """1M splats, 16 views of uneven size with camera deltas, their shadow passes, BF16 storage,
     persistent launches replayed from the CUDA graphs: crops of three views and two sun views."""
     _batched_parity("batched", lambda V: [0, V // 2, V - 1, V + 1, 2 * V - 2], seed=31)
+
+
+def test_batched_1M_16_views_bf16_graph_step_with_distortion():
+    """The same step with the distortion plane written by the forward and back-propagated from
+    the crops (the launch configuration of the bench's distortion line)."""
+    _batched_parity("batched", lambda V: [1, V // 2 + 1, V + 3], seed=35, distortion=True)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
