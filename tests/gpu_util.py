@@ -4,6 +4,7 @@ import numpy as np
 import torch
 
 import oracle
+import scenegen
 from paper_2606_28581_gb300 import _lib as L
 from paper_2606_28581_gb300.frame import Frame, n_pad_of, pad_planar, zero_grads
 
@@ -18,6 +19,7 @@ MAX_EXCLUDED = 1e-3   # fraction of pixels that may be excluded
 class DeviceScene:
     def __init__(self, scene, dtype=torch.float32):
         self.scene = scene
+        self.dtype = dtype
         n = scene.n
         self.n = n
         self.n_pad = n_pad_of(n)
@@ -30,9 +32,13 @@ class DeviceScene:
         self.color = torch.from_numpy(np.stack([c.color for c in scene.cameras]).astype(np.float32)).to(DEV)
 
     def stored_scene64(self):
-        """The stored values (after any BF16 rounding), widened exactly, for the oracle."""
-        g = lambda x: x[:, : self.n].float().cpu().numpy().astype(np.float64)
-        return oracle.SceneF64(g(self.means), g(self.scales), g(self.quats), g(self.opacity)[0], g(self.rgb))
+        """The stored values (after any BF16 rounding, done here on the host), widened exactly,
+        for the oracle."""
+        sc = self.scene
+        r = (lambda a: scenegen.to_bf16_exact(np.asarray(a, np.float32))) if self.dtype == torch.bfloat16 else \
+            (lambda a: np.asarray(a, np.float32))
+        g = lambda a: r(a).astype(np.float64)
+        return oracle.SceneF64(g(sc.means), g(sc.scales), g(sc.quats), g(sc.opacity), g(sc.rgb))
 
 
 def run_forward(ds: DeviceScene, passes=L.SS_PASS_MAIN, opts=None, cams=None):

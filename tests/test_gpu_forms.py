@@ -60,8 +60,9 @@ def test_autograd_matches_oracle_adjoint(storage):
     scene = scene3()
     P = masters(scene)
     frame = Frame(scene.cameras, L.SS_PASS_MAIN | L.SS_PASS_SUN)
-    # the oracle sees exactly the stored values
-    st = {k: P[k].detach().to(storage).float().cpu().numpy().astype(np.float64)
+    # the oracle sees exactly the stored values (rounded to BF16 here, on the host)
+    rnd = scenegen.to_bf16_exact if storage == torch.bfloat16 else (lambda a: a)
+    st = {k: rnd(np.asarray(getattr(scene, k), np.float32)).astype(np.float64)
           for k in ("means", "scales", "quats", "opacity", "rgb")}
     s64 = oracle.SceneF64(st["means"], st["scales"], st["quats"], st["opacity"], st["rgb"])
     ws = weights(frame, scene, 3, s64)

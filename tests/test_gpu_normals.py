@@ -1,7 +1,7 @@
 """Depth-gradient surface normal (K8) against the FP64 oracle, through the C ABI and the autograd
-form: on the rasterizer's planes (isolating the normal arithmetic) and end to end as the
-normal-consistency regulariser alpha - n . N (render -> depth_normal chain against the oracle
-chain)."""
+form: on planes the FP64 oracle renders, rounded to float32 and given to both sides (isolating
+the normal arithmetic), and end to end as the normal-consistency regulariser alpha - n . N
+(render -> depth_normal chain on the GPU against the oracle chain)."""
 import numpy as np
 import pytest
 import torch
@@ -11,7 +11,7 @@ import scenegen
 from oracle import normals as NO
 from paper_2606_28581_gb300 import _lib as L
 from paper_2606_28581_gb300.frame import Frame
-from tests.gpu_util import MARGIN, DeviceScene, grad_close, to_np
+from tests.gpu_util import MARGIN, grad_close, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -38,38 +38,38 @@ def _alpha_margin(alpha):
 
 def test_depth_normal_matches_oracle_forward_and_backward():
     scene = _scene(31)
-    ds = DeviceScene(scene)
-    frame = Frame(scene.cameras, L.SS_PASS_MAIN)
-    out = frame.forward(ds.splats, ds.dF, ds.color)
-    torch.cuda.synchronize()
+    s64 = oracle.SceneF64.of(scene)
+    dF = torch.from_numpy(np.stack([c.dF_xy for c in scene.cameras]).astype(np.float32)).cuda()
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     V = len(scene.cameras)
     cams = L.make_cameras(scene.cameras)
     rng = np.random.default_rng(4)
     views = []
     for c in range(V):
         cam = scene.cameras[c]
-        views.append(dict(depth=out.depth[c], alpha=out.alpha[c],
+        om = oracle.render(s64, cam, color=cam.color)
+        views.append(dict(depth=f(om["depth"]), alpha=f(om["alpha"]),
                           normal=torch.empty(3, cam.height, cam.width, device="cuda")))
-    L.depth_normal_fwd(cams, V, ds.dF, EPS, L.dnormal_io_array(views))
+    L.depth_normal_fwd(cams, V, dF, EPS, L.dnormal_io_array(views))
     torch.cuda.synchronize()
     dNs, keeps = [], []
     for c in range(V):
         cam = scene.cameras[c]
         d, a = to_np(views[c]["depth"]), to_np(views[c]["alpha"])
-        N, ok = NO.depth_normal(d, a, cam, EPS, dF=to_np(ds.dF[c]))
+        N, ok = NO.depth_normal(d, a, cam, EPS, dF=to_np(dF[c]))
         keep = _alpha_margin(a)
         keeps.append(keep)
         assert ok.mean() > 0.5
         assert np.abs(to_np(views[c]["normal"]) - N)[:, keep].max() <= 1e-4
         dNs.append(rng.normal(size=(3, cam.height, cam.width)) * keep)
         views[c].update(d_normal=torch.from_numpy(dNs[c].astype(np.float32)).cuda(),
-                        d_depth=torch.zeros_like(out.depth[c]), d_alpha=torch.zeros_like(out.alpha[c]))
+                        d_depth=torch.zeros_like(views[c]["depth"]), d_alpha=torch.zeros_like(views[c]["alpha"]))
     d_dF = torch.zeros(V, 2, 4, device="cuda")
-    L.depth_normal_bwd(cams, V, ds.dF, EPS, L.dnormal_io_array(views), d_dF)
+    L.depth_normal_bwd(cams, V, dF, EPS, L.dnormal_io_array(views), d_dF)
     torch.cuda.synchronize()
     for c in range(V):
         d, a = to_np(views[c]["depth"]), to_np(views[c]["alpha"])
-        g = NO.depth_normal_backward(dNs[c], d, a, scene.cameras[c], EPS, dF=to_np(ds.dF[c]))
+        g = NO.depth_normal_backward(dNs[c], d, a, scene.cameras[c], EPS, dF=to_np(dF[c]))
         grad_close(to_np(views[c]["d_depth"]), g["depth"], name=f"view {c} d_depth")
         grad_close(to_np(views[c]["d_alpha"]), g["alpha"], name=f"view {c} d_alpha")
         grad_close(to_np(d_dF[c]), g["dF"], name=f"view {c} d_dF", floor=1e-2)

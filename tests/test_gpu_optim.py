@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+import scenegen
 from oracle import optim as O
 from paper_2606_28581_gb300 import _lib as L
 from paper_2606_28581_gb300.frame import n_pad_of
@@ -120,9 +121,11 @@ def _relocation_state(rng, n, cap, dead_frac, dtype):
     v = {k: rng.uniform(size=a.shape).astype(np.float32) for k, a in raw.items()}
     st, storage = _storage(n, n_pad, dtype)
     act = O.activated({k: a.astype(np.float64) for k, a in raw.items()})
+    rnd = scenegen.to_bf16_exact if dtype == torch.bfloat16 else (lambda a: a)
+    host = {k: rnd(a.astype(np.float32)) for k, a in act.items()}  # the stored values, rounded here
     for k in st:
-        st[k].copy_(torch.from_numpy(act[k].astype(np.float32)).to(dtype))
-    return raw, m, v, st, storage, n_pad
+        st[k].copy_(torch.from_numpy(host[k]).to(dtype))
+    return raw, m, v, st, storage, n_pad, host["opacity"][0].astype(np.float64)
 
 
 @pytest.mark.parametrize("dtype,n,cap,dead_frac", [(torch.float32, 5000, 6000, 0.08),
@@ -130,12 +133,11 @@ def _relocation_state(rng, n, cap, dead_frac, dtype):
                                                    (torch.float32, 3001, 3001, 0.3)])
 def test_mcmc_relocation_matches_oracle(dtype, n, cap, dead_frac):
     rng = np.random.default_rng(n + cap)
-    raw, m, v, st, storage, n_pad = _relocation_state(rng, n, cap, dead_frac, dtype)
+    raw, m, v, st, storage, n_pad, stored = _relocation_state(rng, n, cap, dead_frac, dtype)
     tp, tm, tv = _dev(raw), _dev(m), _dev(v)
     opts = L.default_mcmc_opts(step=9, seed=777)
     ws = torch.empty(L.mcmc_workspace_size(cap), dtype=torch.uint8, device="cuda")
     stats = torch.zeros(2, dtype=torch.int64, device="cuda")
-    stored = to_np(st["opacity"])[0]  # the opacity the decisions read, before the call
     n_after = L.mcmc_relocate(_params_struct(tp), _params_struct(tm), _params_struct(tv), storage, cap, opts, ws,
                               d_stats=stats)
     torch.cuda.synchronize()
@@ -177,7 +179,7 @@ def test_mcmc_relocation_matches_oracle(dtype, n, cap, dead_frac):
 
 def test_mcmc_without_live_splats_changes_nothing():
     rng = np.random.default_rng(9)
-    raw, m, v, st, storage, n_pad = _relocation_state(rng, 300, 400, 2.0, torch.float32)
+    raw, m, v, st, storage, n_pad, _ = _relocation_state(rng, 300, 400, 2.0, torch.float32)
     tp, tm, tv = _dev(raw), _dev(m), _dev(v)
     ws = torch.empty(L.mcmc_workspace_size(400), dtype=torch.uint8, device="cuda")
     n_after = L.mcmc_relocate(_params_struct(tp), _params_struct(tm), _params_struct(tv), storage, 400,
@@ -239,15 +241,20 @@ def test_full_size_adam_and_relocation_1M():
         _close_update(to_np(tp[k])[:, idx], ora[k], raw[k][:, idx].astype(np.float64), "raw " + k,
                       per_column=k == "means")
         _close_update(to_np(tm[k])[:, idx], om[k], m[k][:, idx].astype(np.float64), "m " + k)
-    # relocation on the state the step left, with opacities redrawn so that about 5 % of the
-    # splats are dead
-    dead = torch.from_numpy(rng.uniform(size=n_pad) < 0.05).cuda()
-    tp["logit_opacity"].copy_(torch.from_numpy(rng.normal(0.0, 2.0, (1, n_pad)).astype(np.float32)).cuda())
-    tp["logit_opacity"][0, dead] = -8.0
-    st["opacity"].copy_(torch.sigmoid(tp["logit_opacity"]).to(torch.bfloat16))
-    before = {k: to_np(t) for k, t in tp.items()}
-    mb, vb = {k: to_np(t) for k, t in tm.items()}, {k: to_np(t) for k, t in tv.items()}
-    stored = to_np(st["opacity"])[0]
+    # relocation on a fresh host-drawn state (about 5 % of the splats dead) in the same buffers
+    raw = _rand_params(rng, n_pad, n)
+    raw["logit_opacity"][0] = rng.normal(0.0, 2.0, n_pad).astype(np.float32)
+    raw["logit_opacity"][0, rng.uniform(size=n_pad) < 0.05] = -8.0
+    m = {k: rng.normal(size=a.shape).astype(np.float32) for k, a in raw.items()}
+    v = {k: rng.uniform(size=a.shape).astype(np.float32) for k, a in raw.items()}
+    for src, dst in ((raw, tp), (m, tm), (v, tv)):
+        for k in src:
+            dst[k].copy_(torch.from_numpy(src[k]))
+    stored_np = scenegen.to_bf16_exact(O.sigmoid(raw["logit_opacity"].astype(np.float64)).astype(np.float32))
+    st["opacity"].copy_(torch.from_numpy(stored_np).to(torch.bfloat16))
+    before = {k: a.astype(np.float64) for k, a in raw.items()}
+    mb, vb = {k: a.astype(np.float64) for k, a in m.items()}, {k: a.astype(np.float64) for k, a in v.items()}
+    stored = stored_np[0].astype(np.float64)
     ws = torch.empty(L.mcmc_workspace_size(cap), dtype=torch.uint8, device="cuda")
     mo = L.default_mcmc_opts(step=2, seed=8)
     n_after = L.mcmc_relocate(_params_struct(tp), _params_struct(tm), _params_struct(tv), storage, cap, mo, ws)

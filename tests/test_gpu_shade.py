@@ -1,9 +1,9 @@
 """Sun visibility and image formation (K7) against the FP64 shading oracle, through the C ABI.
 
-The rasterizer renders a view and its sun view on the GPU; the shading kernels and the oracle
-then take the same planes (widened exactly to float64 for the oracle), so the comparison isolates
-the shading arithmetic.  Pixels whose decisions sit within FP32 reach of a threshold are
-excluded (and counted)."""
+The FP64 oracle renders a view and its sun view; the planes, rounded to float32, are the input
+of both the shading kernels and the shading oracle (widened back exactly), so the comparison
+isolates the shading arithmetic.  Pixels whose decisions sit within FP32 reach of a threshold
+are excluded (and counted).  The chain test at the end runs the whole path on the GPU."""
 import numpy as np
 import pytest
 import torch
@@ -12,7 +12,7 @@ import scenegen
 from oracle import shade as S
 from paper_2606_28581_gb300 import _lib as L
 from paper_2606_28581_gb300.frame import Frame
-from tests.gpu_util import DeviceScene, grad_close, to_np
+from tests.gpu_util import grad_close, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -25,23 +25,24 @@ def _scene(seed):
         dict(width=96, height=80, off_nadir=12.0, delta=True, color_noise=0.02)])
 
 
-def _render(scene):
-    ds = DeviceScene(scene)
-    frame = Frame(scene.cameras, L.SS_PASS_MAIN | L.SS_PASS_SUN)
-    out = frame.forward(ds.splats, ds.dF, ds.color)
-    torch.cuda.synchronize()
-    return ds, frame, out
+def _planes(scene):
+    """Each view's planes and its sun view's, rendered by the FP64 oracle and rounded to float32
+    (on the device), and the cameras' deltas."""
+    import oracle
+    s64 = oracle.SceneF64.of(scene)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    planes = []
+    for cam in scene.cameras:
+        om = oracle.render(s64, cam, color=cam.color)
+        osun = oracle.render(s64, cam, sun=True)
+        planes.append(dict(rgb=f(om["rgb"]), depth=f(om["depth"]), alpha=f(om["alpha"]), sun_depth=f(osun["depth"]),
+                           sun_alpha=f(osun["alpha"])))
+    dF = torch.from_numpy(np.stack([c.dF_xy for c in scene.cameras]).astype(np.float32)).cuda()
+    return planes, dF
 
 
-def _views(frame, out, extra):
-    V = len(frame.targets) // 2
-    views = []
-    for c in range(V):
-        v = dict(rgb=out.rgb[c], depth=out.depth[c], alpha=out.alpha[c], sun_depth=out.depth[V + c],
-                 sun_alpha=out.alpha[V + c])
-        v.update(extra[c])
-        views.append(v)
-    return views
+def _views(planes, extra):
+    return [dict(planes[c], **extra[c]) for c in range(len(planes))]
 
 
 def _margin_keep(scene, planes, c, k, bias):
@@ -53,21 +54,21 @@ def _margin_keep(scene, planes, c, k, bias):
 @pytest.mark.parametrize("bias", [0.0, 0.01])
 def test_shade_forward_matches_oracle(bias):
     scene = _scene(seed=21)
-    ds, frame, out = _render(scene)
+    planes, dF = _planes(scene)
     V = len(scene.cameras)
     La = torch.tensor([[0.2, 0.3, 0.4], [0.5, 0.35, 0.25]], device="cuda")
     imgs = [torch.empty(3, c.height, c.width, device="cuda") for c in scene.cameras]
     vis = [torch.empty(c.height, c.width, device="cuda") for c in scene.cameras]
-    views = _views(frame, out, [dict(image=imgs[c], vis=vis[c]) for c in range(V)])
+    views = _views(planes, [dict(image=imgs[c], vis=vis[c]) for c in range(V)])
     cams = L.make_cameras(scene.cameras)
     opts = L.default_shade_opts(esm_k=K, esm_bias=bias, alpha_eps=EPS)
-    L.shade_fwd(cams, V, ds.dF, La, opts, L.shade_io_array(views))
+    L.shade_fwd(cams, V, dF, La, opts, L.shade_io_array(views))
     torch.cuda.synchronize()
     shadowed = 0
     for c in range(V):
         p = {k: to_np(views[c][k]) for k in ("rgb", "depth", "alpha", "sun_depth", "sun_alpha")}
         I, Vo = S.shade_forward(p["rgb"], p["depth"], p["alpha"], p["sun_depth"], p["sun_alpha"], scene.cameras[c],
-                                to_np(La[c]), K, bias, EPS, dF=to_np(ds.dF[c]))
+                                to_np(La[c]), K, bias, EPS, dF=to_np(dF[c]))
         keep = _margin_keep(scene, p, c, K, bias)
         assert keep.mean() > 0.98
         assert np.abs(to_np(vis[c]) - Vo)[keep].max() <= 1e-5
@@ -78,7 +79,7 @@ def test_shade_forward_matches_oracle(bias):
 
 def test_shade_backward_matches_oracle():
     scene = _scene(seed=22)
-    ds, frame, out = _render(scene)
+    planes, dF = _planes(scene)
     V = len(scene.cameras)
     rng = np.random.default_rng(3)
     La = torch.tensor([[0.3, 0.2, 0.4], [0.45, 0.5, 0.3]], device="cuda")
@@ -86,27 +87,27 @@ def test_shade_backward_matches_oracle():
     d_img, extra, keeps = [], [], []
     for c in range(V):
         cam = scene.cameras[c]
-        p = {k: to_np(t) for k, t in (("depth", out.depth[c]), ("alpha", out.alpha[c]), ("sun_depth", out.depth[V + c]),
-                                       ("sun_alpha", out.alpha[V + c]))}
+        p = {k: to_np(planes[c][k]) for k in ("depth", "alpha", "sun_depth", "sun_alpha")}
         keep = _margin_keep(scene, p, c, K, 0.0)
         keeps.append(keep)
         dI = rng.normal(size=(3, cam.height, cam.width)) * keep
         d_img.append(torch.from_numpy(dI.astype(np.float32)).cuda())
         extra.append(dict(image=torch.empty(3, cam.height, cam.width, device="cuda"), d_image=d_img[c],
-                          d_rgb=zeros(out.rgb[c]), d_depth=zeros(out.depth[c]), d_alpha=zeros(out.alpha[c]),
-                          d_sun_depth=zeros(out.depth[V + c]), d_sun_alpha=zeros(out.alpha[V + c])))
-    views = _views(frame, out, extra)
+                          d_rgb=zeros(planes[c]["rgb"]), d_depth=zeros(planes[c]["depth"]),
+                          d_alpha=zeros(planes[c]["alpha"]), d_sun_depth=zeros(planes[c]["sun_depth"]),
+                          d_sun_alpha=zeros(planes[c]["sun_alpha"])))
+    views = _views(planes, extra)
     cams = L.make_cameras(scene.cameras)
     opts = L.default_shade_opts(esm_k=K, esm_bias=0.0, alpha_eps=EPS)
     d_La = torch.zeros(V, 3, device="cuda")
     d_dF = torch.zeros(V, 2, 4, device="cuda")
-    L.shade_bwd(cams, V, ds.dF, La, opts, L.shade_io_array(views), d_La, d_dF)
+    L.shade_bwd(cams, V, dF, La, opts, L.shade_io_array(views), d_La, d_dF)
     torch.cuda.synchronize()
     for c in range(V):
         v = views[c]
         p = {k: to_np(v[k]) for k in ("rgb", "depth", "alpha", "sun_depth", "sun_alpha")}
         g = S.shade_backward(to_np(d_img[c]), p["rgb"], p["depth"], p["alpha"], p["sun_depth"], p["sun_alpha"],
-                             scene.cameras[c], to_np(La[c]), K, 0.0, EPS, dF=to_np(ds.dF[c]))
+                             scene.cameras[c], to_np(La[c]), K, 0.0, EPS, dF=to_np(dF[c]))
         for key in ("rgb", "depth", "alpha", "sun_depth", "sun_alpha"):
             grad_close(to_np(v["d_" + key]), g[key], name=f"view {c} d_{key}")
         grad_close(to_np(d_La[c]), g["La"], name=f"view {c} d_La")
