@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(kNX * kNY) depth_normal_fwd_kernel(const __gri
 // and a halo of one pixel (from z staged with a halo of two), then every pixel gathers.  Each
 // block loops over several tiles of its view (blockIdx.x, + gridDim.x, ...) and adds its
 // per-view sums to the camera gradient once.
-__global__ void __launch_bounds__(kNX * kNY) depth_normal_bwd_kernel(const __grid_constant__ NormalParams p) {
+// eight blocks per SM (32 registers) measured 20 % faster than the six of its natural register count
+__global__ void __launch_bounds__(kNX * kNY, 8) depth_normal_bwd_kernel(const __grid_constant__ NormalParams p) {
   __shared__ float sz[kNY + 4][kNX + 5];
   __shared__ float sdx[kNY + 2][kNX + 3], sdy[kNY + 2][kNX + 3];
   __shared__ float red[kNX * kNY / 32][8];

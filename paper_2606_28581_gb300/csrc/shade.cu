@@ -127,7 +127,9 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float x) {
   if (k == 0) v.x = x; else if (k == 1) v.y = x; else if (k == 2) v.z = x; else v.w = x;
 }
 
-__global__ void __launch_bounds__(256) shade_fwd_kernel(const __grid_constant__ ShadeParams p) {
+// Both shading kernels are latency-bound: eight blocks per SM (32 registers, a few spilled) measured
+// 15-20 % faster than the four that their natural register count allows.
+__global__ void __launch_bounds__(256, 8) shade_fwd_kernel(const __grid_constant__ ShadeParams p) {
   const int cam = blockIdx.y;
   const ShadeView& v = p.v[cam];
   const int64_t hw = (int64_t)v.W * v.H;
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(256) shade_fwd_kernel(const __grid_constant__ 
 }
 
 // One pixel per thread: four per thread measured slower here (its sun-view atomics serialise).
-__global__ void __launch_bounds__(256) shade_bwd_kernel(const __grid_constant__ ShadeParams p) {
+__global__ void __launch_bounds__(256, 8) shade_bwd_kernel(const __grid_constant__ ShadeParams p) {
   __shared__ float red[8][10];
   const int cam = blockIdx.y;
   const ShadeView& v = p.v[cam];
