@@ -633,7 +633,7 @@ def run_ours(args, dist):
     shade = measure_shade(torch, step, k_steps)
     dnormal = measure_depth_normal(torch, step, k_steps)
     optimizer = measure_optimizer(torch, scene.n, step.grads, storage, k_steps)
-    init = None if args.profile else measure_init(torch, 3)
+    init = measure_init(torch, 3)
     distortion = None
     if not args.no_distortion:
         mk_d = lambda u: BatchedStep(cams, splats, scene.n, dF, color, u, passes=passes, opts=opts,
