@@ -394,11 +394,12 @@ def measure_optimizer(torch, n: int, grads: dict, storage_dtype, reps: int):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         n_after = L.mcmc_relocate(pp, pm, pv, storage, cap, L.default_mcmc_opts(step=r), ws)
+        torch.cuda.synchronize()  # the call returns before its last kernels finish
         rl.append((time.perf_counter() - t0) * 1e3)
     return {"bound": "hbm", "splats": n, "adam_ms": float(ms), "adam_bytes_per_splat": per_splat,
             "adam_gbs": gbs, "peak_gbs": peak, "peak_basis": basis, "adam_frac": gbs / peak,
             "relocate_ms": float(np.median(rl)), "relocate_n_after": int(n_after), "relocate_cap": int(cap),
-            "relocate_note": "host-timed, includes the one stream synchronisation of the call"}
+            "relocate_note": "host-timed from the call to the end of its last kernel (a synchronisation after it)"}
 
 
 def measure_init(torch, reps: int):

@@ -63,6 +63,7 @@ struct InitParams {
   uint32_t* idx;              // [n] sample index
   const uint32_t* skeys;      // sorted
   const uint32_t* sidx;
+  float* spts;                // [3][n] the positions in cell order
   uint32_t* cstart;           // [NX NY]
   uint32_t* cend;
   // outputs
@@ -190,22 +191,29 @@ __global__ void __launch_bounds__(256) init_sample_kernel(const __grid_constant_
   p.idx[s] = (uint32_t)s;
 }
 
+// cell ranges of the sorted samples, and their positions gathered into cell order
 __global__ void __launch_bounds__(256) init_cells_kernel(const __grid_constant__ InitParams p) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.n) return;
   const uint32_t k = p.skeys[s];
   if (s == 0 || p.skeys[s - 1] != k) p.cstart[k] = (uint32_t)s;
   if (s == p.n - 1 || p.skeys[s + 1] != k) p.cend[k] = (uint32_t)(s + 1);
+  const uint32_t o = p.sidx[s];
+  p.spts[s] = p.pts[o];
+  p.spts[p.n + s] = p.pts[p.n + o];
+  p.spts[2 * p.n + s] = p.pts[2 * p.n + o];
 }
 
 // mean distance to the K nearest other samples: rings of cells around the sample's cell until
-// the K-th distance is within the searched radius (every unsearched sample is at least r h away)
+// the K-th distance is within the searched radius (every unsearched sample is at least r h away).
+// Threads take the samples in cell order, so a warp searches the same few cells.
 template <int K>
 __global__ void __launch_bounds__(256) init_knn_kernel(const __grid_constant__ InitParams p) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= p.n) return;
-  const float x = p.pts[s], y = p.pts[p.n + s], z = p.pts[2 * p.n + s];
-  const uint32_t key = cell_of(p, x, y);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.n) return;
+  const int64_t s = p.sidx[t];
+  const float x = p.spts[t], y = p.spts[p.n + t], z = p.spts[2 * p.n + t];
+  const uint32_t key = p.skeys[t];
   const int cx = (int)(key % (uint32_t)p.NX), cy = (int)(key / (uint32_t)p.NX);
   float best[K];
 #pragma unroll
@@ -221,10 +229,9 @@ __global__ void __launch_bounds__(256) init_knn_kernel(const __grid_constant__ I
         if (xx < 0 || xx >= p.NX) continue;
         const int c = yy * p.NX + xx;
         const uint32_t b = p.cstart[c], e = p.cend[c];
-        for (uint32_t t = b; t < e; ++t) {
-          const uint32_t o = p.sidx[t];
-          if (o == (uint32_t)s) continue;
-          const float ex = p.pts[o] - x, ey = p.pts[p.n + o] - y, ez = p.pts[2 * p.n + o] - z;
+        for (uint32_t u = b; u < e; ++u) {
+          if (u == (uint32_t)t) continue;
+          const float ex = p.spts[u] - x, ey = p.spts[p.n + u] - y, ez = p.spts[2 * p.n + u] - z;
           float d2 = ex * ex + ey * ey + ez * ez;
           if (d2 < best[K - 1]) {
 #pragma unroll
@@ -255,7 +262,7 @@ constexpr size_t kAl = 256;
 size_t up(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 
 struct InitLayout {
-  size_t w, excl, scan, total, pts, keys_a, vals_a, keys_b, vals_b, hist, hist_off, rscan, cstart, cend, bytes;
+  size_t w, excl, scan, total, pts, spts, keys_a, vals_a, keys_b, vals_b, hist, hist_off, rscan, cstart, cend, bytes;
   ScanPlan wplan;
   RadixPlan rplan;
   int NX, NY;
@@ -289,6 +296,7 @@ bool layout_of(int32_t W, int32_t H, float g, int64_t n, InitLayout& L) {
   L.scan = take(8 * L.wplan.scratch_elems);
   L.total = take(8);
   L.pts = take(12 * (size_t)n);
+  L.spts = take(12 * (size_t)n);
   L.keys_a = take(4 * (size_t)n);
   L.vals_a = take(4 * (size_t)n);
   L.keys_b = take(4 * (size_t)n);
@@ -363,6 +371,7 @@ ss_status ss_dsm_init(const ss_dsm* dsm, const ss_init_opts* opts, const ss_spla
   unsigned long long* total = at_<unsigned long long>(ws, L.total);
   p.total = total;
   p.pts = at_<float>(ws, L.pts);
+  p.spts = at_<float>(ws, L.spts);
   p.gx0 = dsm->x0 - 0.5f * dsm->gsd;
   p.gy0 = dsm->y0 + 0.5f * dsm->gsd;
   p.h = L.h;

@@ -281,6 +281,8 @@ struct McmcParams {
   uint32_t* counts;  // [n_active] times each splat was drawn
   uint32_t* tgt;     // [n_targets]
   uint32_t* src;     // [n_targets]
+  uint32_t* ulist;   // the distinct sources, in no particular order
+  uint32_t* n_ulist; // their count
   int64_t* d_stats;  // optional
   const unsigned long long* totals;  // [2]: dead count, total weight
 };
@@ -328,7 +330,8 @@ __global__ void __launch_bounds__(256) mcmc_draw_kernel(const __grid_constant__ 
   const int64_t s = lo - 1;
   q.tgt[j] = (uint32_t)t;
   q.src[j] = (uint32_t)s;
-  atomicAdd(&q.counts[s], 1u);
+  // the first draw of a source lists it once, so that the split rule runs densely over them
+  if (atomicAdd(&q.counts[s], 1u) == 0u) q.ulist[atomicAdd(q.n_ulist, 1u)] = (uint32_t)s;
 }
 
 // the activation of raw row r, as the Adam step stores it
@@ -350,10 +353,10 @@ __device__ __forceinline__ void storage_slot(int r, int& grp, int& row) {
 // the sources: o' = 1 - (1 - o)^(1/N) and s' = s o / sum_{j=1}^{N} (-1)^(j-1) C(N, j) o'^j / sqrt(j),
 // in FP64; moments zeroed, storage rewritten
 __global__ void __launch_bounds__(256) mcmc_sources_kernel(const __grid_constant__ McmcParams q) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= q.n_active) return;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= q.n_targets || k >= (int64_t)*q.n_ulist) return;
+  const int64_t i = q.ulist[k];
   const uint32_t c = q.counts[i];
-  if (c == 0u) return;
   const int N = (int)min((uint32_t)q.n_max, c + 1u);
   const double x = (double)q.p.row[9][i];
   const double o = 1.0 / (1.0 + exp(-x));
@@ -453,7 +456,7 @@ constexpr size_t kAlignMc = 256;
 size_t up(size_t x) { return (x + kAlignMc - 1) / kAlignMc * kAlignMc; }
 
 struct McmcLayout {
-  size_t w, dead, dpos, excl, counts, tgt, src, scratch_a, scratch_b, totals, total;
+  size_t w, dead, dpos, excl, counts, tgt, src, ulist, nlist, scratch_a, scratch_b, totals, total;
   ScanPlan plan;
 };
 
@@ -469,6 +472,8 @@ McmcLayout mcmc_layout(int64_t cap) {
   L.counts = take(4 * (size_t)cap);
   L.tgt = take(4 * (size_t)cap);
   L.src = take(4 * (size_t)cap);
+  L.ulist = take(4 * (size_t)cap);
+  L.nlist = take(16);
   L.scratch_a = take(8 * L.plan.scratch_elems);
   L.scratch_b = take(8 * L.plan.scratch_elems);
   L.totals = take(16);
@@ -637,6 +642,8 @@ ss_status ss_mcmc_relocate(const ss_splat_params* params, const ss_splat_params*
   q.counts = at_<uint32_t>(ws, L.counts);
   q.tgt = at_<uint32_t>(ws, L.tgt);
   q.src = at_<uint32_t>(ws, L.src);
+  q.ulist = at_<uint32_t>(ws, L.ulist);
+  q.n_ulist = at_<uint32_t>(ws, L.nlist);
   q.d_stats = d_stats;
   unsigned long long* totals = at_<unsigned long long>(ws, L.totals);
   q.totals = totals;
@@ -665,10 +672,11 @@ ss_status ss_mcmc_relocate(const ss_splat_params* params, const ss_splat_params*
   q.n_targets = q.n_dead + (grown - n);
   *n_after = grown;
   if (q.n_targets == 0) return SS_OK;
+  if (cudaMemsetAsync(q.n_ulist, 0, sizeof(uint32_t), st) != cudaSuccess) return SS_ERR_CUDA;
   count_launch();
   mcmc_draw_kernel<<<blocks_for(q.n_targets), 256, 0, st>>>(q);
   count_launch();
-  mcmc_sources_kernel<<<blocks_for(n), 256, 0, st>>>(q);
+  mcmc_sources_kernel<<<blocks_for(q.n_targets), 256, 0, st>>>(q);
   count_launch();
   mcmc_copy_kernel<<<blocks_for(q.n_targets), 256, 0, st>>>(q);
   return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
