@@ -37,6 +37,39 @@ __device__ __forceinline__ int find_target(const TargetCam* tc, int n_targets, i
   return lo;
 }
 
+// ---------------------------------------------------------------- paired FP32 arithmetic
+// A lane's two pixels share every operation, so the forward keeps their state in float2 and
+// uses the paired FP32 instructions (one issue, two IEEE round-to-nearest results), each lane
+// bitwise equal to the scalar operation.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// eval_pair (common.cuh) of one splat at a lane's two pixels (x, y.x) and (x, y.y), with the
+// same operations in the same order: bitwise the same alpha and decisions as two scalar calls.
+struct PairEval2 {
+  float2 u, v, alpha;
+  bool contrib0, contrib1;
+};
+
+__device__ __forceinline__ PairEval2 eval_pair2(const float4 g0, const float4 g1, const float4 g2, float x,
+                                                float2 y, const EvalConsts& k) {
+  PairEval2 e;
+  const float dx = __fsub_rn(__fsub_rn(x, g0.x), g0.z);
+  const float2 dy = add2(add2(y, bc2(-g0.y)), bc2(-g0.w));
+  e.u = fma2(bc2(g1.y), dy, bc2(__fmul_rn(g1.x, dx)));
+  e.v = fma2(bc2(g1.w), dy, bc2(__fmul_rn(g1.z, dx)));
+  const float2 pu = mul2(bc2(-0.5f), fma2(e.u, e.u, mul2(e.v, e.v)));
+  const float2 ps = mul2(neg2(fma2(bc2(dx), bc2(dx), mul2(dy, dy))), bc2(k.inv2s2));
+  const float2 lp = add2(make_float2(fmaxf(pu.x, ps.x), fmaxf(pu.y, ps.y)), bc2(g2.x));
+  e.alpha = make_float2(fminf(__expf(lp.x), k.amax), fminf(__expf(lp.y), k.amax));
+  e.contrib0 = e.alpha.x >= k.amin;
+  e.contrib1 = e.alpha.y >= k.amin;
+  return e;
+}
+
 // Transposed reduction of 16 values over the 8 lanes of a group: lane gl of the group ends
 // with the group sums of fields 2 gl and 2 gl + 1 (in v[0], v[1]).
 __device__ __forceinline__ void group_reduce16(float v[16]) {
@@ -265,17 +298,13 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
     const uint2 range = p.ranges[tile];
     const int64_t recbase = (int64_t)t * p.n_pad;
 
-    float T[2], D[2], A0[2], A1[2], A2[2], N0[2], N1[2], N2[2], y[2], Dst[2];
-    uint32_t last[2];
-    bool done[2];
+    // the lane's two pixels (rows py0 and py0 + 2) side by side: .x and .y
+    float2 T = bc2(1.0f), D = bc2(0.0f), A0 = bc2(0.0f), A1 = bc2(0.0f), A2 = bc2(0.0f), N0 = bc2(0.0f),
+           N1 = bc2(0.0f), N2 = bc2(0.0f), Dst = bc2(0.0f);
+    const float2 y = make_float2((float)lg.py0 + 0.5f, (float)(lg.py0 + 2) + 0.5f);
+    uint32_t last0 = range.x, last1 = range.x;
+    bool done0 = !(lg.px < cam.W && lg.py0 < cam.H), done1 = !(lg.px < cam.W && lg.py0 + 2 < cam.H);
     uint32_t walked = 0;  // contributing pairs, the stopping one included
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      T[k] = 1.0f; D[k] = A0[k] = A1[k] = A2[k] = N0[k] = N1[k] = N2[k] = Dst[k] = 0.0f;
-      y[k] = (float)(lg.py0 + 2 * k) + 0.5f;
-      last[k] = range.x;
-      done[k] = !(lg.px < cam.W && lg.py0 + 2 * k < cam.H);
-    }
     const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (uint32_t b0 = range.x; b0 < range.y; b0 += BATCH) {
       const int nb = min((int)(range.y - b0), BATCH);
@@ -292,7 +321,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
         if (!sun) sf[i][1] = f[1];  // a sun view composites depth alone
         smask[i] = p.subblock_cull ? subblock_mask<TW, TH>(g0, g1, g2, lg.x0, lg.y0, p.cull) : 0xffffu;
       }
-      const bool all_done = done[0] && done[1];
+      const bool all_done = done0 && done1;
       if (__syncthreads_and(all_done)) break;
       const uint32_t mk = batch_masks<TW, BATCH>(smask, nb);
       // a group whose 16 pixels have all stopped walks nothing
@@ -300,31 +329,35 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
       const uint8_t* list = slist[tid >> 3];
       const int total = compact_candidates(gdone ? 0u : mk, slist[tid >> 3]);
       const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
-      // two splats per step: their four pair evaluations are independent; only the
-      // compositing runs in order (splat a, then splat b) for each pixel.  A sun view
-      // (SUN) composites depth alone: it has no colour or normal output.
+      // two splats per step: their pair evaluations are independent; only the compositing
+      // runs in order (splat a, then splat b) for each pixel.  A sun view (SUN) composites
+      // depth alone: it has no colour or normal output.
       auto walk = [&](auto sun_c) {
         constexpr bool SUN = decltype(sun_c)::value;
-        auto composite = [&](const PairEval& e, bool ck, int k, const float4& g2, const float4& f0,
+        auto composite = [&](const PairEval2& e, bool ck0, bool ck1, const float4& g2, const float4& f0,
                              const float4& f1, uint32_t pos) {
-          const float Tn = T[k] * (1.0f - e.alpha);
-          const bool stop = ck && Tn < p.t_min;  // this splat ends the walk and is not composited
-          const bool take = ck && !stop;
-          const float w = take ? e.alpha * T[k] : 0.0f;
-          const float z = g2.w + f0.x * e.u + f0.y * e.v;
-          if (DIST) Dst[k] = fmaf(w, fmaf(-z, T[k], z) - D[k], Dst[k]);
-          D[k] += w * z;
+          const float2 Tn = mul2(T, add2(bc2(1.0f), neg2(e.alpha)));
+          // a splat that takes T below t_min ends the walk and is not composited
+          const bool stop0 = ck0 && Tn.x < p.t_min, stop1 = ck1 && Tn.y < p.t_min;
+          const bool take0 = ck0 && !stop0, take1 = ck1 && !stop1;
+          const float2 aT = mul2(e.alpha, T);
+          const float2 w = make_float2(take0 ? aT.x : 0.0f, take1 ? aT.y : 0.0f);
+          const float2 z = fma2(bc2(f0.y), e.v, fma2(bc2(f0.x), e.u, bc2(g2.w)));
+          if (DIST) Dst = fma2(w, add2(fma2(neg2(z), T, z), neg2(D)), Dst);
+          D = fma2(w, z, D);
           if (!SUN) {
-            A0[k] += w * f1.y;
-            A1[k] += w * f1.z;
-            A2[k] += w * f1.w;
-            N0[k] += w * f0.z;
-            N1[k] += w * f0.w;
-            N2[k] += w * f1.x;
+            A0 = fma2(w, bc2(f1.y), A0);
+            A1 = fma2(w, bc2(f1.z), A1);
+            A2 = fma2(w, bc2(f1.w), A2);
+            N0 = fma2(w, bc2(f0.z), N0);
+            N1 = fma2(w, bc2(f0.w), N1);
+            N2 = fma2(w, bc2(f1.x), N2);
           }
-          T[k] = take ? Tn : T[k];
-          last[k] = take ? pos : last[k];
-          done[k] = done[k] || stop;
+          T = make_float2(take0 ? Tn.x : T.x, take1 ? Tn.y : T.y);
+          last0 = take0 ? pos : last0;
+          last1 = take1 ? pos : last1;
+          done0 = done0 || stop0;
+          done1 = done1 || stop1;
         };
         for (int st = 0; st < nsteps; st += 2) {
           // lanes whose group has nothing left evaluate a stand-in and composite nothing
@@ -333,27 +366,24 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
           const int jb = has_b ? list[st + 1] : ja;
           const float4 ga0 = sg[ja][0], ga1 = sg[ja][1], ga2 = sg[ja][2];
           const float4 gb0 = sg[jb][0], gb1 = sg[jb][1], gb2 = sg[jb][2];
-          const PairEval ea0 = eval_pair(ga0, ga1, ga2, x, y[0], p.k);
-          const PairEval ea1 = eval_pair(ga0, ga1, ga2, x, y[1], p.k);
-          const PairEval eb0 = eval_pair(gb0, gb1, gb2, x, y[0], p.k);
-          const PairEval eb1 = eval_pair(gb0, gb1, gb2, x, y[1], p.k);
+          const PairEval2 ea = eval_pair2(ga0, ga1, ga2, x, y, p.k);
+          const PairEval2 eb = eval_pair2(gb0, gb1, gb2, x, y, p.k);
           const float4 fa0 = sf[ja][0], fb0 = sf[jb][0];
           const float4 fa1 = SUN ? zero4 : sf[ja][1], fb1 = SUN ? zero4 : sf[jb][1];
           const uint32_t pa = b0 + (uint32_t)ja + 1u, pb = b0 + (uint32_t)jb + 1u;
-          const bool ca0 = has_a && !done[0] && ea0.contrib, ca1 = has_a && !done[1] && ea1.contrib;
+          const bool ca0 = has_a && !done0 && ea.contrib0, ca1 = has_a && !done1 && ea.contrib1;
           walked += (uint32_t)ca0 + (uint32_t)ca1;
-          composite(ea0, ca0, 0, ga2, fa0, fa1, pa);
-          composite(ea1, ca1, 1, ga2, fa0, fa1, pa);
-          const bool cb0 = has_b && !done[0] && eb0.contrib, cb1 = has_b && !done[1] && eb1.contrib;
+          composite(ea, ca0, ca1, ga2, fa0, fa1, pa);
+          const bool cb0 = has_b && !done0 && eb.contrib0, cb1 = has_b && !done1 && eb.contrib1;
           walked += (uint32_t)cb0 + (uint32_t)cb1;
-          composite(eb0, cb0, 0, gb2, fb0, fb1, pb);
-          composite(eb1, cb1, 1, gb2, fb0, fb1, pb);
+          composite(eb, cb0, cb1, gb2, fb0, fb1, pb);
         }
       };
       if (sun) walk(std::true_type{}); else walk(std::false_type{});
     }
     const TargetIO io = p.io[t];
     const int64_t hw = (int64_t)cam.W * cam.H;
+    auto pick = [](float2 v, int k) { return k == 0 ? v.x : v.y; };
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int py = lg.py0 + 2 * k;
@@ -361,20 +391,21 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
       const int64_t pix = (int64_t)py * cam.W + lg.px;
       if (io.rgb) {
         // the splats carry C rgb; the offset c completes C A + c (Sec. 3.1 Eq. image_formation)
-        io.rgb[pix] = A0[k] + cam.C[3];
-        io.rgb[hw + pix] = A1[k] + cam.C[7];
-        io.rgb[2 * hw + pix] = A2[k] + cam.C[11];
+        io.rgb[pix] = pick(A0, k) + cam.C[3];
+        io.rgb[hw + pix] = pick(A1, k) + cam.C[7];
+        io.rgb[2 * hw + pix] = pick(A2, k) + cam.C[11];
       }
-      if (io.depth) io.depth[pix] = D[k];
+      if (io.depth) io.depth[pix] = pick(D, k);
       if (io.normal) {
-        io.normal[pix] = N0[k];
-        io.normal[hw + pix] = N1[k];
-        io.normal[2 * hw + pix] = N2[k];
+        io.normal[pix] = pick(N0, k);
+        io.normal[hw + pix] = pick(N1, k);
+        io.normal[2 * hw + pix] = pick(N2, k);
       }
-      if (io.alpha) io.alpha[pix] = 1.0f - T[k];
-      if (DIST && io.distort) io.distort[pix] = 2.0f * Dst[k];
-      io.T_final[pix] = T[k];
-      io.last[pix] = last[k];
+      const float Tk = pick(T, k);
+      if (io.alpha) io.alpha[pix] = 1.0f - Tk;
+      if (DIST && io.distort) io.distort[pix] = 2.0f * pick(Dst, k);
+      io.T_final[pix] = Tk;
+      io.last[pix] = k == 0 ? last0 : last1;
     }
     // algorithmic work counter: one atomic per warp
     const unsigned int wsum = __reduce_add_sync(0xffffffffu, walked);
