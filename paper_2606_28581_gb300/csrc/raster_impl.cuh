@@ -50,8 +50,11 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 // eval_pair (common.cuh) of one splat at a lane's two pixels (x, y.x) and (x, y.y), with the
 // same operations in the same order: bitwise the same alpha and decisions as two scalar calls.
 struct PairEval2 {
-  float2 u, v, alpha;
-  bool contrib0, contrib1;
+  float dx;                   // x - c (the lane's pixels share a column)
+  float2 dy, u, v, alpha;
+  bool contrib0, contrib1;    // alpha >= alpha_min
+  bool uwin0, uwin1;          // the uv Gaussian won the max (ties: uv)
+  bool clamped0, clamped1;    // alpha_max reached
 };
 
 __device__ __forceinline__ PairEval2 eval_pair2(const float4 g0, const float4 g1, const float4 g2, float x,
@@ -59,12 +62,19 @@ __device__ __forceinline__ PairEval2 eval_pair2(const float4 g0, const float4 g1
   PairEval2 e;
   const float dx = __fsub_rn(__fsub_rn(x, g0.x), g0.z);
   const float2 dy = add2(add2(y, bc2(-g0.y)), bc2(-g0.w));
+  e.dx = dx;
+  e.dy = dy;
   e.u = fma2(bc2(g1.y), dy, bc2(__fmul_rn(g1.x, dx)));
   e.v = fma2(bc2(g1.w), dy, bc2(__fmul_rn(g1.z, dx)));
   const float2 pu = mul2(bc2(-0.5f), fma2(e.u, e.u, mul2(e.v, e.v)));
   const float2 ps = mul2(neg2(fma2(bc2(dx), bc2(dx), mul2(dy, dy))), bc2(k.inv2s2));
+  e.uwin0 = pu.x >= ps.x;
+  e.uwin1 = pu.y >= ps.y;
   const float2 lp = add2(make_float2(fmaxf(pu.x, ps.x), fmaxf(pu.y, ps.y)), bc2(g2.x));
-  e.alpha = make_float2(fminf(__expf(lp.x), k.amax), fminf(__expf(lp.y), k.amax));
+  const float og0 = __expf(lp.x), og1 = __expf(lp.y);
+  e.clamped0 = og0 > k.amax;
+  e.clamped1 = og1 > k.amax;
+  e.alpha = make_float2(fminf(og0, k.amax), fminf(og1, k.amax));
   e.contrib0 = e.alpha.x >= k.amin;
   e.contrib1 = e.alpha.y >= k.amin;
   return e;
@@ -423,7 +433,9 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
 // M = D - M' - w_m z_m with D the forward's depth plane, so M' - M = E + w_m z_m with
 // E = 2 M' - D carried along the walk.  The weight partial joins the splat's per-pixel value f.
 template <int TW, int TH, int BATCH, bool PERSIST, bool DIST>
-__global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
+// Five resident blocks (20 warps): the bound keeps every variant, the distortion's included, at
+// <= 102 registers without spills.
+__global__ void __launch_bounds__(TW * TH / 2, 5) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
   constexpr int NT = TW * TH / 2;
   constexpr int NW = NT / 32;
   static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are whole 8 x 8 warp blocks");
@@ -497,6 +509,16 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
       }
       c1[k] = 1.0f + T[k];
     }
+    // the two pixels side by side (.x, .y) for the paired FP32 arithmetic of the walk
+    float2 T2 = make_float2(T[0], T[1]), Sg2 = make_float2(Sg[0], Sg[1]), gD2 = make_float2(gD[0], gD[1]);
+    const float2 gAlT2 = make_float2(gAlT[0], gAlT[1]);
+    const float2 gR0 = make_float2(gR[0][0], gR[1][0]), gR1 = make_float2(gR[0][1], gR[1][1]),
+                 gR2 = make_float2(gR[0][2], gR[1][2]);
+    const float2 gN0 = make_float2(gN[0][0], gN[1][0]), gN1 = make_float2(gN[0][1], gN[1][1]),
+                 gN2 = make_float2(gN[0][2], gN[1][2]);
+    const float2 gDsv = make_float2(gDs2[0], gDs2[1]), c1v = make_float2(c1[0], c1[1]);
+    float2 Ev = make_float2(E[0], E[1]);
+    const float2 yy = make_float2(y[0], y[1]);
     // the group's last walked position (exclusive): its walk ends there
     uint32_t glast = max(lastp[0], lastp[1]);
     glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 1));
@@ -562,75 +584,76 @@ __global__ void __launch_bounds__(TW * TH / 2) raster_bwd_kernel(const __grid_co
           const int js = jj >= 0 ? jj : 0;
           const uint32_t j = b0 + (uint32_t)js;
           const float4 g0 = sg[js][0], g1 = sg[js][1], g2 = sg[js][2];
-          const PairEval e0 = eval_pair(g0, g1, g2, x, y[0], p.k);
-          const PairEval e1 = eval_pair(g0, g1, g2, x, y[1], p.k);
-          const bool c0p = jj >= 0 && j < lastp[0] && e0.contrib, c1p = jj >= 0 && j < lastp[1] && e1.contrib;
+          const PairEval2 e = eval_pair2(g0, g1, g2, x, yy, p.k);
+          const bool c0p = jj >= 0 && j < lastp[0] && e.contrib0, c1p = jj >= 0 && j < lastp[1] && e.contrib1;
           // the previous splat's group reduction overlaps this splat's arithmetic; it runs
           // unconditionally (sums that nothing wrote are zeros) so that it stays branch free
           flush(Gq, jq);
           const float4 f0 = sf[js][0];
           const float4 f1 = SUN ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : sf[js][1];
           // both pixels side by side.  A pair that does not contribute runs with alpha = 0, which
-          // leaves T and S unchanged and adds zeros.  The two pixels share their column
-          // (e0.dx == e1.dx), so the terms linear in dx and the centre's chain through Q are
-          // summed over the lane before they are formed.
-          float du[2], dv[2], dps[2];
-  #pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const PairEval& e = k == 0 ? e0 : e1;
-            const bool ck = k == 0 ? c0p : c1p;
-            const float a = ck ? e.alpha : 0.0f;
-            const float om = 1.0f - a;
-            const float rom = __fdividef(1.0f, om);  // om >= 1 - alpha_max
-            const float Ti = T[k] * rom;             // T in front of the splat
-            const float z = g2.w + f0.x * e.u + f0.y * e.v;
-            float gf = SUN ? gD[k] * z
-                           : gD[k] * z + gR[k][0] * f1.y + gR[k][1] * f1.z + gR[k][2] * f1.w +
-                                 gN[k][0] * f0.z + gN[k][1] * f0.w + gN[k][2] * f1.x;
-            const float w = a * Ti;
-            float dzd = 0.0f;  // the distortion's partial in z
-            if (DIST) {
-              const float dW = c1[k] - Ti - T[k];  // W - W'
-              const float wz = w * z;
-              gf = fmaf(gDs2[k], fmaf(z, dW, E[k] + wz), gf);
-              dzd = gDs2[k] * w * dW;
-              E[k] = fmaf(2.0f, wz, E[k]);
-            }
-            const float gs = gf - Sg[k];
-            T[k] = Ti;
-            Sg[k] = Sg[k] + a * gs;  // composite from this splat on: a f + (1 - a) S
-            if (SUN) {
-              Gc[GF_R] = Gc[GF_G] = Gc[GF_B] = Gc[GF_NX] = Gc[GF_NY] = Gc[GF_NZ] = 0.0f;
-            } else {
-              Gc[GF_R] = (k == 0 ? 0.0f : Gc[GF_R]) + w * gR[k][0];
-              Gc[GF_G] = (k == 0 ? 0.0f : Gc[GF_G]) + w * gR[k][1];
-              Gc[GF_B] = (k == 0 ? 0.0f : Gc[GF_B]) + w * gR[k][2];
-              Gc[GF_NX] = (k == 0 ? 0.0f : Gc[GF_NX]) + w * gN[k][0];
-              Gc[GF_NY] = (k == 0 ? 0.0f : Gc[GF_NY]) + w * gN[k][1];
-              Gc[GF_NZ] = (k == 0 ? 0.0f : Gc[GF_NZ]) + w * gN[k][2];
-            }
-            const float dz = w * gD[k] + dzd;
-            Gc[GF_ZC] = (k == 0 ? 0.0f : Gc[GF_ZC]) + dz;
-            Gc[GF_DZDU] = (k == 0 ? 0.0f : Gc[GF_DZDU]) + dz * e.u;
-            Gc[GF_DZDV] = (k == 0 ? 0.0f : Gc[GF_DZDV]) + dz * e.v;
-            // d / d ln(o G^) = alpha dL/dalpha, dL/dalpha = T_i (f - S) + d(alpha_out) T_final / (1 - alpha);
-            // zero when clamped (the exact adjoint of the clamp)
-            const float dal = Ti * gs + gAlT[k] * rom;
-            const float dpw = e.clamped ? 0.0f : dal * a;
-            Gc[GF_LNO] = (k == 0 ? 0.0f : Gc[GF_LNO]) + dpw;
-            const float dpu = e.uwin ? dpw : 0.0f;
-            dps[k] = e.uwin ? 0.0f : dpw * two_inv2s2;
-            // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
-            du[k] = dz * f0.x - dpu * e.u;
-            dv[k] = dz * f0.y - dpu * e.v;
+          // leaves T and S unchanged and adds zeros.  The two pixels share their column, so the
+          // terms linear in dx and the centre's chain through Q are summed over the lane before
+          // they are formed.
+          const float2 a = make_float2(c0p ? e.alpha.x : 0.0f, c1p ? e.alpha.y : 0.0f);
+          const float2 om = add2(bc2(1.0f), neg2(a));
+          const float2 rom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));  // om >= 1 - alpha_max
+          const float2 Ti = mul2(T2, rom);  // T in front of the splat
+          const float2 z = fma2(bc2(f0.y), e.v, fma2(bc2(f0.x), e.u, bc2(g2.w)));
+          float2 gf = mul2(gD2, z);
+          if (!SUN) {
+            gf = fma2(gR0, bc2(f1.y), gf);
+            gf = fma2(gR1, bc2(f1.z), gf);
+            gf = fma2(gR2, bc2(f1.w), gf);
+            gf = fma2(gN0, bc2(f0.z), gf);
+            gf = fma2(gN1, bc2(f0.w), gf);
+            gf = fma2(gN2, bc2(f1.x), gf);
           }
-          const float sdu = du[0] + du[1], sdv = dv[0] + dv[1];
-          Gc[GF_Q00] = sdu * e0.dx;
-          Gc[GF_Q01] = du[0] * e0.dy + du[1] * e1.dy;
-          Gc[GF_Q10] = sdv * e0.dx;
-          Gc[GF_Q11] = dv[0] * e0.dy + dv[1] * e1.dy;
-          Gc[GF_CX] = (dps[0] + dps[1]) * e0.dx - (g1.x * sdu + g1.z * sdv);
-          Gc[GF_CY] = dps[0] * e0.dy + dps[1] * e1.dy - (g1.y * sdu + g1.w * sdv);
+          const float2 w = mul2(a, Ti);
+          float2 dzd = bc2(0.0f);  // the distortion's partial in z
+          if (DIST) {
+            const float2 dW = add2(add2(c1v, neg2(Ti)), neg2(T2));  // W - W'
+            const float2 wz = mul2(w, z);
+            gf = fma2(gDsv, fma2(z, dW, add2(Ev, wz)), gf);
+            dzd = mul2(mul2(gDsv, w), dW);
+            Ev = fma2(bc2(2.0f), wz, Ev);
+          }
+          const float2 gs = add2(gf, neg2(Sg2));
+          T2 = Ti;
+          Sg2 = fma2(a, gs, Sg2);  // composite from this splat on: a f + (1 - a) S
+          auto hsum = [](float2 v) { return v.x + v.y; };
+          if (SUN) {
+            Gc[GF_R] = Gc[GF_G] = Gc[GF_B] = Gc[GF_NX] = Gc[GF_NY] = Gc[GF_NZ] = 0.0f;
+          } else {
+            Gc[GF_R] = hsum(mul2(w, gR0));
+            Gc[GF_G] = hsum(mul2(w, gR1));
+            Gc[GF_B] = hsum(mul2(w, gR2));
+            Gc[GF_NX] = hsum(mul2(w, gN0));
+            Gc[GF_NY] = hsum(mul2(w, gN1));
+            Gc[GF_NZ] = hsum(mul2(w, gN2));
+          }
+          const float2 dz = fma2(w, gD2, dzd);
+          Gc[GF_ZC] = hsum(dz);
+          Gc[GF_DZDU] = hsum(mul2(dz, e.u));
+          Gc[GF_DZDV] = hsum(mul2(dz, e.v));
+          // d / d ln(o G^) = alpha dL/dalpha, dL/dalpha = T_i (f - S) + d(alpha_out) T_final / (1 - alpha);
+          // zero when clamped (the exact adjoint of the clamp)
+          const float2 dal = fma2(Ti, gs, mul2(gAlT2, rom));
+          const float2 dpa = mul2(dal, a);
+          const float2 dpw = make_float2(e.clamped0 ? 0.0f : dpa.x, e.clamped1 ? 0.0f : dpa.y);
+          Gc[GF_LNO] = hsum(dpw);
+          const float2 dpu = make_float2(e.uwin0 ? dpw.x : 0.0f, e.uwin1 ? dpw.y : 0.0f);
+          const float2 dps = mul2(make_float2(e.uwin0 ? 0.0f : dpw.x, e.uwin1 ? 0.0f : dpw.y), bc2(two_inv2s2));
+          // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
+          const float2 du = fma2(dz, bc2(f0.x), neg2(mul2(dpu, e.u)));
+          const float2 dv = fma2(dz, bc2(f0.y), neg2(mul2(dpu, e.v)));
+          const float sdu = hsum(du), sdv = hsum(dv);
+          Gc[GF_Q00] = sdu * e.dx;
+          Gc[GF_Q01] = hsum(mul2(du, e.dy));
+          Gc[GF_Q10] = sdv * e.dx;
+          Gc[GF_Q11] = hsum(mul2(dv, e.dy));
+          Gc[GF_CX] = hsum(dps) * e.dx - (g1.x * sdu + g1.z * sdv);
+          Gc[GF_CY] = hsum(mul2(dps, e.dy)) - (g1.y * sdu + g1.w * sdv);
           jc = jj;
         };
         bool lastA = false;  // the last step wrote GA (else GB)
