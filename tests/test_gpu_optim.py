@@ -208,6 +208,14 @@ def test_optimiser_rejects_bad_arguments():
         L.mcmc_relocate(p, p, p, storage, 1000, L.default_mcmc_opts(), ws)
     with pytest.raises(L.SatSplatError):
         L.mcmc_relocate(p, p, p, storage, n, L.default_mcmc_opts(n_max=52), ws)
+    # no active splat: both calls succeed and change nothing
+    before = {k: to_np(v) for k, v in t.items()}
+    _, empty = _storage(0, n_pad, torch.float32)
+    L.adam_step(p, p, p, grads, empty, L.default_adam_opts())
+    assert L.mcmc_relocate(p, p, p, empty, n, L.default_mcmc_opts(), ws) == 0
+    torch.cuda.synchronize()
+    for k, v in t.items():
+        np.testing.assert_array_equal(to_np(v), before[k])
 
 
 def test_full_size_adam_and_relocation_1M():
