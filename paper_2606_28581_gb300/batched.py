@@ -18,7 +18,7 @@ from __future__ import annotations
 import hashlib
 import json
 import os
-from typing import List, Optional, Sequence
+from typing import Optional, Sequence
 
 import torch
 

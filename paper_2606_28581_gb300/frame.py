@@ -7,7 +7,6 @@ library.
 """
 from __future__ import annotations
 
-import ctypes
 import dataclasses
 from typing import List, Optional, Sequence
 

@@ -6,7 +6,7 @@ import torch
 import oracle
 import scenegen
 from paper_2606_28581_gb300 import _lib as L
-from paper_2606_28581_gb300.frame import Frame, n_pad_of, pad_planar, zero_grads
+from paper_2606_28581_gb300.frame import Frame, n_pad_of, pad_planar
 
 DEV = "cuda"
 FWD_TOL = 1e-5        # absolute, FP32 storage (all outputs)

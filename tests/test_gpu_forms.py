@@ -11,8 +11,8 @@ import scenegen
 from paper_2606_28581_gb300 import _lib as L
 from paper_2606_28581_gb300.autograd import render
 from paper_2606_28581_gb300.batched import BatchedStep, autotune
-from paper_2606_28581_gb300.frame import Frame, zero_grads
-from tests.gpu_util import MARGIN, DeviceScene, grad_close, oracle_forward, run_forward
+from paper_2606_28581_gb300.frame import Frame
+from tests.gpu_util import MARGIN, DeviceScene, grad_close, oracle_forward
 
 pytestmark = pytest.mark.gpu
 

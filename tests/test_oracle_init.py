@@ -4,7 +4,6 @@ jitter, the Gram-Schmidt basis, and the k-d tree kNN against brute force."""
 import math
 
 import numpy as np
-import pytest
 
 import scenegen
 from oracle import init as I

@@ -4,7 +4,6 @@ Independent checks: the sun position against the renderer's own sun camera (Supp
 the explicitly reconstructed 3-D receiver; closed forms for lit ground, a flat occluder and the
 ambient limit; texel-centre sampling; and the hand-written adjoint against central differences."""
 import numpy as np
-import pytest
 
 import oracle
 import scenegen

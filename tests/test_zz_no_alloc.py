@@ -4,7 +4,6 @@ workspace path's, call after call, although every call reuses the library's stat
 Collected last on purpose."""
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
