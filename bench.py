@@ -251,6 +251,16 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
+def loaded_clock_mhz():
+    """The median SM clock the machine's GPUs held under a seconds-long dense load
+    (MEASURED_PEAKS.json), else the fallback of 1485 MHz."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["clocks_under_load"]["sm_mhz_median"])
+    except Exception:
+        return 1485.0
+
+
 def measure_shade(torch, step, reps: int):
     """Forward and backward of the shading (K7) over every main view of the step, on the step's
     rasterized planes, with CUDA events; HBM roofline from the algorithmic bytes per main pixel
@@ -467,9 +477,10 @@ def measure_depth_normal(torch, step, reps: int):
 
 
 # ------------------------------------------------------------------------------ oracle arm
-def oracle_sample(scene, seconds_target: float, seed: int = 0):
+def oracle_sample(scene, seconds_target: float, seed: int = 0, parts: bool = False):
     """Time the FP64 oracle (forward + backward) on crops of view 0, growing the crop until
-    one sample takes about `seconds_target`.  Returns (Mpix/s, crop, seconds, threads)."""
+    one sample takes about `seconds_target`.  Returns (Mpix/s, crop, seconds, threads), and with
+    `parts` also the forward's own Mpix/s."""
     import oracle
     s64 = oracle.SceneF64.of(scene)
     cam = scene.cameras[0]
@@ -484,10 +495,12 @@ def oracle_sample(scene, seconds_target: float, seed: int = 0):
                  normal=rng.normal(size=(3, h, w)), alpha=rng.normal(size=(h, w)))
         t0 = time.perf_counter()
         oracle.render(s64, cam, crop=(x0, y0, w, h), color=cam.color)
+        t1 = time.perf_counter()
         oracle.backward(s64, cam, g, crop=(x0, y0, w, h), color=cam.color)
         dt = time.perf_counter() - t0
         if dt >= seconds_target or (w == cam.width and h == cam.height) or side >= 4096:
-            return (w * h) / dt / 1e6, (x0, y0, w, h), dt, oracle.num_threads()
+            r = ((w * h) / dt / 1e6, (x0, y0, w, h), dt, oracle.num_threads())
+            return r + ((w * h) / (t1 - t0) / 1e6,) if parts else r
         side = int(side * min(4.0, max(1.3, math.sqrt(seconds_target / max(dt, 1e-3)))))
 
 
@@ -615,7 +628,8 @@ def run_ours(args, dist):
         torch.cuda.synchronize()
         acc += [evs[i].elapsed_time(evs[i + 1]) for i in range(len(phases))]
     phase_ms = {n: float(a / k_steps) for n, a in zip(names, acc)}
-    clock_mhz = clocks["sm_mhz"] if clocks else 1485.0
+    loaded_mhz = loaded_clock_mhz()
+    clock_mhz = clocks["sm_mhz"] if clocks else loaded_mhz
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
     flops = {"rasterize_fwd": walked * FLOPS_FWD_PER_PAIR, "rasterize_bwd": walked * FLOPS_BWD_PER_PAIR}
     dom = max(("rasterize_fwd", "rasterize_bwd"), key=lambda k: phase_ms[k])
@@ -628,6 +642,8 @@ def run_ours(args, dist):
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz "
                               f"(median SM clock sampled during the timed region)",
                 "frac_at_max_clock": achieved / (sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12),
+                "loaded_clock_mhz": loaded_mhz,
+                "frac_at_loaded_clock": achieved / (sms * FP32_LANES_PER_SM * 2 * loaded_mhz * 1e6 / 1e12),
                 "phase_ms": phase_ms}
 
     # ---- sun visibility and image formation (K7), depth-gradient normals (K8), timed alone
@@ -722,10 +738,20 @@ def run_ours(args, dist):
     # ---- the oracle on the host cores (rank 0, one GPU only)
     cpu = None
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
-        v, crop, secs, threads = oracle_sample(scene, 12.0)
+        import oracle
+        v, crop, secs, threads, v_fwd = oracle_sample(scene, 12.0, parts=True)
+        # the same oracle on one host thread, on a smaller crop (about 3 s)
+        oracle.set_threads(1)
+        try:
+            v1, crop1, secs1, _, v1_fwd = oracle_sample(scene, 3.0, parts=True)
+        finally:
+            oracle.set_threads(threads)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"forward+backward of a {crop[2]}x{crop[3]} px crop of view 0 with all "
-                         f"{scene.n} splats ({secs:.1f} s)"}
+                         f"{scene.n} splats ({secs:.1f} s)",
+               "forward_only": v_fwd,
+               "one_thread": {"value": v1, "forward_only": v1_fwd,
+                              "sample": f"forward+backward of a {crop1[2]}x{crop1[3]} px crop ({secs1:.1f} s)"}}
 
     if dist.rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
