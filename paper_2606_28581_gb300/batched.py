@@ -159,11 +159,15 @@ class BatchedStep:
         if self._copy_stream is None:
             self._copy_stream = torch.cuda.Stream()
         side = self._copy_stream
+        # the upstream planes may be overwritten once the work already on the current stream
+        # (the previous step's backward) is done; they need not wait for this step's splat copies
+        prior = torch.cuda.Event()
+        prior.record(cur)
         for k, t in self.tensors.items():
             t.copy_(h_splats[k], non_blocking=True)
         self.dF.copy_(h_dF, non_blocking=True)
         self.color.copy_(h_color, non_blocking=True)
-        side.wait_stream(cur)  # the previous step's backward has read the upstream planes
+        side.wait_event(prior)
         with torch.cuda.stream(side):
             for du, hu in zip(self.upstream, h_upstream):
                 for k in du:
