@@ -1,8 +1,8 @@
 // Depth-gradient surface normal (K8), Sec. 3.2 Eq. surface_normal, and its adjoint.
 //
-// Blocks of 32 x 8 threads, one per pixel of a tile; every view in one launch (blockIdx.y = view),
-// and each block loops over tiles of its view, about as many blocks as the SMs hold at once
-// (one block per tile measured slower).  The point map
+// Blocks of 32 x 8 threads over tiles of 32 x 32 pixels; every view in one launch (blockIdx.y =
+// view), and each block loops over tiles of its view, about as many blocks as the SMs hold at
+// once (one block per tile measured slower).  The point map
 // p_s = (X, Y, h) is affine in the pixel and in the height, so its central differences are
 //   grad_x p_s = a1 + (h(i+1) - h(i-1)) G,  grad_y p_s = a2 + (h(j+1) - h(j-1)) G,
 // with per-view a1 = (2 A^-1 e1, 0), a2 = (2 A^-1 e2, 0), G = (-A^-1 B'[:, 2], 1), A = B'[:, 0:2].
@@ -62,16 +62,49 @@ __device__ __forceinline__ NormalCam normal_cam(const NormalParams& p, const Nor
   return c;
 }
 
-// Tiles of kNX x kNY pixels per block (one thread each).  The alpha-normalised depth z of the
-// tile and a halo is staged once in shared memory (NaN where there is no surface or no pixel), so
-// each pixel's z is formed once instead of once per neighbour that needs it.
-constexpr int kNX = 32, kNY = 8;
+// Tiles of kNX x kNY pixels per block of kNX x 8 threads, kRows rows per thread.  The
+// alpha-normalised depth z of the tile and a halo is staged in shared memory (NaN where there is
+// no surface or no pixel), so each pixel's z is formed once instead of once per neighbour that
+// needs it.  A thread issues all its staging loads of a phase (about five slots, alpha and
+// depth together) before it uses any: these passes are bound by the bytes each SM keeps in
+// flight, and a tile of 32 x 8 pixels with one load pair per thread kept too few.
+constexpr int kNX = 32, kNY = 32, kThreads = kNX * 8, kRows = kNY / 8;
+// resident blocks of the backward: its threads hold five slots of d_normal in registers
+constexpr int kNormalBwdBlocks = 4;
 
-__device__ __forceinline__ float z_at(const NormalParams& p, const NormalView& v, int x, int y) {
-  if (x < 0 || y < 0 || x >= v.W || y >= v.H) return __int_as_float(0x7fc00000);  // NaN: no pixel
-  const int64_t i = (int64_t)y * v.W + x;
-  const float a = v.io.alpha[i];
-  return a >= p.eps ? v.io.depth[i] / a : __int_as_float(0x7fc00000);
+template <int HALO>
+struct Slots {
+  static constexpr int W = kNX + 2 * HALO, N = (kNY + 2 * HALO) * W, PER = (N + kThreads - 1) / kThreads;
+};
+
+// z of the tile at (x0, y0) and its halo of HALO pixels into sz
+template <int HALO, int SX>
+__device__ __forceinline__ void stage_z(const NormalView& v, int x0, int y0, float eps, float (*sz)[SX]) {
+  constexpr int PER = Slots<HALO>::PER;
+  float a[PER], d[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int k = threadIdx.x + r * kThreads;
+    a[r] = 0.0f;  // no pixel: no surface
+    d[r] = 0.0f;
+    if (k < Slots<HALO>::N) {
+      const int ty = k / Slots<HALO>::W, tx = k - ty * Slots<HALO>::W;
+      const int x = x0 - HALO + tx, y = y0 - HALO + ty;
+      if (x >= 0 && y >= 0 && x < v.W && y < v.H) {
+        const int64_t i = (int64_t)y * v.W + x;
+        a[r] = v.io.alpha[i];
+        d[r] = v.io.depth[i];
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int k = threadIdx.x + r * kThreads;
+    if (k < Slots<HALO>::N) {
+      const int ty = k / Slots<HALO>::W, tx = k - ty * Slots<HALO>::W;
+      sz[ty][tx] = a[r] >= eps ? d[r] / a[r] : __int_as_float(0x7fc00000);
+    }
+  }
 }
 
 // u = grad_x p_s and v = grad_y p_s from the height differences dhx = z(i-1) - z(i+1) and
@@ -90,43 +123,45 @@ __device__ __forceinline__ NormalUV normal_uv(const NormalCam& c, float dhx, flo
   return r;
 }
 
-__global__ void __launch_bounds__(kNX * kNY) depth_normal_fwd_kernel(const __grid_constant__ NormalParams p) {
+__global__ void __launch_bounds__(kThreads) depth_normal_fwd_kernel(const __grid_constant__ NormalParams p) {
   __shared__ float sz[kNY + 2][kNX + 3];
   const int cam = blockIdx.y;
   const NormalView& v = p.v[cam];
   const int bxs = (v.W + kNX - 1) / kNX;
   const int ntiles = bxs * ((v.H + kNY - 1) / kNY);
   const NormalCam c = normal_cam(p, v, cam);
+  const int64_t hw = (int64_t)v.W * v.H;
+  const int tx = threadIdx.x % kNX, ty0 = threadIdx.x / kNX;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-  const int by = tile / bxs, bx = tile - by * bxs;
-  const int x0 = bx * kNX, y0 = by * kNY;
-  __syncthreads();  // the previous tile's reads of sz are done
-  for (int k = threadIdx.x; k < (kNY + 2) * (kNX + 2); k += kNX * kNY) {
-    const int ty = k / (kNX + 2), tx = k - ty * (kNX + 2);
-    sz[ty][tx] = z_at(p, v, x0 - 1 + tx, y0 - 1 + ty);
-  }
-  __syncthreads();
-  const int tx = threadIdx.x % kNX, ty = threadIdx.x / kNX;
-  const int px = x0 + tx, py = y0 + ty;
-  if (px >= v.W || py >= v.H) continue;
-  const float zc = sz[ty + 1][tx + 1], zl = sz[ty + 1][tx], zr = sz[ty + 1][tx + 2], zu = sz[ty][tx + 1],
-              zd = sz[ty + 2][tx + 1];
-  float n[3] = {0.0f, 0.0f, 0.0f};
-  // a NaN (no surface, or outside the view) anywhere leaves the normal at 0
-  if (!(isnan(zc) || isnan(zl) || isnan(zr) || isnan(zu) || isnan(zd))) {
-    const NormalUV q = normal_uv(c, zl - zr, zu - zd);
-    n[0] = q.uy * q.vz - q.uz * q.vy;
-    n[1] = q.uz * q.vx - q.ux * q.vz;
-    n[2] = q.ux * q.vy - q.uy * q.vx;
-    const float s = c.sgn * rsqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    n[0] *= s;
-    n[1] *= s;
-    n[2] *= s;
-  }
-  const int64_t hw = (int64_t)v.W * v.H, pix = (int64_t)py * v.W + px;
+    const int by = tile / bxs, bx = tile - by * bxs;
+    const int x0 = bx * kNX, y0 = by * kNY;
+    __syncthreads();  // the previous tile's reads of sz are done
+    stage_z<1>(v, x0, y0, p.eps, sz);
+    __syncthreads();
 #pragma unroll
-  for (int k = 0; k < 3; ++k) v.io.normal[k * hw + pix] = n[k];
-  }  // tiles
+    for (int j = 0; j < kRows; ++j) {
+      const int ty = ty0 + 8 * j;
+      const int px = x0 + tx, py = y0 + ty;
+      if (px >= v.W || py >= v.H) continue;
+      const float zc = sz[ty + 1][tx + 1], zl = sz[ty + 1][tx], zr = sz[ty + 1][tx + 2], zu = sz[ty][tx + 1],
+                  zd = sz[ty + 2][tx + 1];
+      float n[3] = {0.0f, 0.0f, 0.0f};
+      // a NaN (no surface, or outside the view) anywhere leaves the normal at 0
+      if (!(isnan(zc) || isnan(zl) || isnan(zr) || isnan(zu) || isnan(zd))) {
+        const NormalUV q = normal_uv(c, zl - zr, zu - zd);
+        n[0] = q.uy * q.vz - q.uz * q.vy;
+        n[1] = q.uz * q.vx - q.ux * q.vz;
+        n[2] = q.ux * q.vy - q.uy * q.vx;
+        const float sc = c.sgn * rsqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        n[0] *= sc;
+        n[1] *= sc;
+        n[2] *= sc;
+      }
+      const int64_t pix = (int64_t)py * v.W + px;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v.io.normal[k * hw + pix] = n[k];
+    }
+  }
 }
 
 // Gather form of the backward: a pixel's depth enters the normals of its four neighbours
@@ -135,11 +170,11 @@ __global__ void __launch_bounds__(kNX * kNY) depth_normal_fwd_kernel(const __gri
 // and a halo of one pixel (from z staged with a halo of two), then every pixel gathers.  Each
 // block loops over several tiles of its view (blockIdx.x, + gridDim.x, ...) and adds its
 // per-view sums to the camera gradient once.
-// eight blocks per SM (32 registers) measured 20 % faster than the six of its natural register count
-__global__ void __launch_bounds__(kNX * kNY, 8) depth_normal_bwd_kernel(const __grid_constant__ NormalParams p) {
+__global__ void __launch_bounds__(kThreads, kNormalBwdBlocks) depth_normal_bwd_kernel(
+    const __grid_constant__ NormalParams p) {
   __shared__ float sz[kNY + 4][kNX + 5];
   __shared__ float sdx[kNY + 2][kNX + 3], sdy[kNY + 2][kNX + 3];
-  __shared__ float red[kNX * kNY / 32][8];
+  __shared__ float red[kThreads / 32][8];
   const int cam = blockIdx.y;
   const NormalView& v = p.v[cam];
   const int bxs = (v.W + kNX - 1) / kNX;
@@ -152,14 +187,31 @@ __global__ void __launch_bounds__(kNX * kNY, 8) depth_normal_bwd_kernel(const __
   const int by = tile / bxs, bx = tile - by * bxs;
   const int x0 = bx * kNX, y0 = by * kNY;
   __syncthreads();  // the previous tile's reads of the shared planes are done
-  for (int k = threadIdx.x; k < (kNY + 4) * (kNX + 4); k += kNX * kNY) {
-    const int ty = k / (kNX + 4), tx = k - ty * (kNX + 4);
-    sz[ty][tx] = z_at(p, v, x0 - 2 + tx, y0 - 2 + ty);
+  // d_normal at the thread's halo-1 positions, issued with the staging loads below (both are
+  // in flight together) and loaded before any is used
+  constexpr int PER1 = Slots<1>::PER;
+  float dn[PER1][3];
+#pragma unroll
+  for (int r = 0; r < PER1; ++r) {
+    const int k = threadIdx.x + r * kThreads;
+    dn[r][0] = dn[r][1] = dn[r][2] = 0.0f;
+    if (k < Slots<1>::N) {
+      const int ty = k / Slots<1>::W, tx = k - ty * Slots<1>::W;
+      const int px = x0 - 1 + tx, py = y0 - 1 + ty;
+      if (px >= 0 && py >= 0 && px < v.W && py < v.H) {
+        const int64_t pix = (int64_t)py * v.W + px;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dn[r][j] = v.io.d_normal[j * hw + pix];
+      }
+    }
   }
+  stage_z<2>(v, x0, y0, p.eps, sz);
   __syncthreads();
-  for (int k = threadIdx.x; k < (kNY + 2) * (kNX + 2); k += kNX * kNY) {
-    const int ty = k / (kNX + 2), tx = k - ty * (kNX + 2);  // halo-1 coordinates
-    const int px = x0 - 1 + tx, py = y0 - 1 + ty;
+#pragma unroll
+  for (int r = 0; r < PER1; ++r) {
+    const int k = threadIdx.x + r * kThreads;
+    if (k >= Slots<1>::N) break;
+    const int ty = k / Slots<1>::W, tx = k - ty * Slots<1>::W;  // halo-1 coordinates
     const float zc = sz[ty + 1][tx + 1], zl = sz[ty + 1][tx], zr = sz[ty + 1][tx + 2], zu = sz[ty][tx + 1],
                 zd = sz[ty + 2][tx + 1];
     float ddhx = 0.0f, ddhy = 0.0f;
@@ -169,10 +221,7 @@ __global__ void __launch_bounds__(kNX * kNY, 8) depth_normal_bwd_kernel(const __
       const float n[3] = {q.uy * q.vz - q.uz * q.vy, q.uz * q.vx - q.ux * q.vz, q.ux * q.vy - q.uy * q.vx};
       const float inv = rsqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
       const float N[3] = {n[0] * inv, n[1] * inv, n[2] * inv};  // unsigned unit normal
-      const int64_t pix = (int64_t)py * v.W + px;
-      float dN[3];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) dN[j] = v.io.d_normal[j * hw + pix];
+      const float* dN = dn[r];
       // N_out = sgn n / |n|: dn = sgn (dN - N (N . dN)) / |n|
       const float nd = N[0] * dN[0] + N[1] * dN[1] + N[2] * dN[2];
       float dc[3];
@@ -201,17 +250,34 @@ __global__ void __launch_bounds__(kNX * kNY, 8) depth_normal_bwd_kernel(const __
   }
   __syncthreads();
   {
-    const int tx = threadIdx.x % kNX, ty = threadIdx.x / kNX;
-    const int px = x0 + tx, py = y0 + ty;
-    if (px < v.W && py < v.H) {
-      const float dz = sdx[ty + 1][tx + 2] - sdx[ty + 1][tx] + sdy[ty + 2][tx + 1] - sdy[ty][tx + 1];
-      if (dz != 0.0f) {
+    // the thread's kRows pixels: every load first, then the read-modify-writes (a store could
+    // alias a later row's loads, so loads interleaved with stores would wait on each other)
+    const int tx = threadIdx.x % kNX, ty0 = threadIdx.x / kNX;
+    float dz[kRows], a[kRows], D[kRows], gd[kRows], ga[kRows];
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+      const int ty = ty0 + 8 * j;
+      const int px = x0 + tx, py = y0 + ty;
+      dz[j] = 0.0f;
+      if (px < v.W && py < v.H)
+        dz[j] = sdx[ty + 1][tx + 2] - sdx[ty + 1][tx] + sdy[ty + 2][tx + 1] - sdy[ty][tx + 1];
+      a[j] = 1.0f;
+      D[j] = gd[j] = ga[j] = 0.0f;
+      if (dz[j] != 0.0f) {
         // z = D / alpha (a pixel that feeds a normal has a surface)
         const int64_t pix = (int64_t)py * v.W + px;
-        const float a = v.io.alpha[pix], D = v.io.depth[pix];
-        if (v.io.d_depth) v.io.d_depth[pix] += dz / a;
-        if (v.io.d_alpha) v.io.d_alpha[pix] += -dz * D / (a * a);
+        a[j] = v.io.alpha[pix];
+        D[j] = v.io.depth[pix];
+        if (v.io.d_depth) gd[j] = v.io.d_depth[pix];
+        if (v.io.d_alpha) ga[j] = v.io.d_alpha[pix];
       }
+    }
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+      if (dz[j] == 0.0f) continue;
+      const int64_t pix = (int64_t)(y0 + ty0 + 8 * j) * v.W + x0 + tx;
+      if (v.io.d_depth) v.io.d_depth[pix] = gd[j] + dz[j] / a[j];
+      if (v.io.d_alpha) v.io.d_alpha[pix] = ga[j] + -dz[j] * D[j] / (a[j] * a[j]);
     }
   }
   }  // tiles
@@ -293,7 +359,7 @@ template <class K>
 dim3 normal_loop_grid(const ss_camera* cams, int32_t n_cams, K kernel, int& per_sm) {
   if (per_sm == 0) {
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kNX * kNY, 0) != cudaSuccess || v < 1) v = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kThreads, 0) != cudaSuccess || v < 1) v = 1;
     per_sm = v;
   }
   const dim3 full = normal_grid(cams, n_cams);
@@ -315,7 +381,7 @@ ss_status ss_depth_normal_fwd(const ss_camera* cams, int32_t n_cams, const float
   if (e != SS_OK) return e;
   count_launch();
   static int per_sm = 0;
-  depth_normal_fwd_kernel<<<normal_loop_grid(cams, n_cams, depth_normal_fwd_kernel, per_sm), kNX * kNY, 0,
+  depth_normal_fwd_kernel<<<normal_loop_grid(cams, n_cams, depth_normal_fwd_kernel, per_sm), kThreads, 0,
                             (cudaStream_t)stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }
@@ -328,7 +394,7 @@ ss_status ss_depth_normal_bwd(const ss_camera* cams, int32_t n_cams, const float
   p.d_dF = d_dF;
   count_launch();
   static int per_sm = 0;
-  depth_normal_bwd_kernel<<<normal_loop_grid(cams, n_cams, depth_normal_bwd_kernel, per_sm), kNX * kNY, 0,
+  depth_normal_bwd_kernel<<<normal_loop_grid(cams, n_cams, depth_normal_bwd_kernel, per_sm), kThreads, 0,
                             (cudaStream_t)stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }

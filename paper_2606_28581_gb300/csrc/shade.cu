@@ -127,8 +127,9 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float x) {
   if (k == 0) v.x = x; else if (k == 1) v.y = x; else if (k == 2) v.z = x; else v.w = x;
 }
 
-// Both shading kernels are latency-bound: eight blocks per SM (32 registers, a few spilled) measured
-// 15-20 % faster than the four that their natural register count allows.
+// Both shading kernels are latency-bound: the forward at eight blocks per SM (32 registers, a few
+// spilled) measured 15-20 % faster than the four that its natural register count allows; the
+// backward, which loads all of a pixel's planes before its stores, is fastest at six.
 __global__ void __launch_bounds__(256, 8) shade_fwd_kernel(const __grid_constant__ ShadeParams p) {
   const int cam = blockIdx.y;
   const ShadeView& v = p.v[cam];
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256, 8) shade_fwd_kernel(const __grid_constant
 }
 
 // One pixel per thread: four per thread measured slower here (its sun-view atomics serialise).
-__global__ void __launch_bounds__(256, 8) shade_bwd_kernel(const __grid_constant__ ShadeParams p) {
+__global__ void __launch_bounds__(256, 6) shade_bwd_kernel(const __grid_constant__ ShadeParams p) {
   __shared__ float red[8][10];
   const int cam = blockIdx.y;
   const ShadeView& v = p.v[cam];
@@ -176,16 +177,30 @@ __global__ void __launch_bounds__(256, 8) shade_bwd_kernel(const __grid_constant
   float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (pix < hw) {
     const int py = (int)(pix / v.W), px = (int)(pix - (int64_t)py * v.W);
-    const ShadeGeom g = shade_geom(p, v, cam, px, py, v.io.alpha[pix], v.io.depth[pix]);
+    // every plane value of the pixel is loaded before any gradient is stored: a store could alias
+    // a later load, so loads interleaved with the read-modify-writes would wait on each other
+    const float alpha = v.io.alpha[pix], depth = v.io.depth[pix];
+    float dI[3], R[3], gR[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dI[c] = v.io.d_image[c * hw + pix];
+      R[c] = v.io.rgb[c * hw + pix];
+      if (v.io.d_rgb) gR[c] = v.io.d_rgb[c * hw + pix];
+    }
+    // the depth and alpha gradients of a pixel with a surface (only those can be in shadow)
+    float gz = 0.0f, ga = 0.0f;
+    if (alpha >= p.eps) {
+      if (v.io.d_depth) gz = v.io.d_depth[pix];
+      if (v.io.d_alpha) ga = v.io.d_alpha[pix];
+    }
+    const ShadeGeom g = shade_geom(p, v, cam, px, py, alpha, depth);
     float dV = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float La = p.La[3 * cam + c];
-      const float dI = v.io.d_image[c * hw + pix];
-      const float R = v.io.rgb[c * hw + pix];
-      if (v.io.d_rgb) v.io.d_rgb[c * hw + pix] += dI * (La + g.V * (1.0f - La));
-      dV = fmaf(dI * R, 1.0f - La, dV);
-      acc[c] = dI * R * (1.0f - g.V);
+      if (v.io.d_rgb) v.io.d_rgb[c * hw + pix] = gR[c] + dI[c] * (La + g.V * (1.0f - La));
+      dV = fmaf(dI[c] * R[c], 1.0f - La, dV);
+      acc[c] = dI[c] * R[c] * (1.0f - g.V);
     }
     if (g.shadowed) {
       // V = exp(-k delta), delta = z - z_o - bias
@@ -212,8 +227,8 @@ __global__ void __launch_bounds__(256, 8) shade_bwd_kernel(const __grid_constant
       }
       // h = max_alt - z, z = D / alpha
       const float dz = d_delta - dh;
-      if (v.io.d_depth) v.io.d_depth[pix] += dz / g.a;
-      if (v.io.d_alpha) v.io.d_alpha[pix] += -dz * g.D / (g.a * g.a);
+      if (v.io.d_depth) v.io.d_depth[pix] = gz + dz / g.a;
+      if (v.io.d_alpha) v.io.d_alpha[pix] = ga + -dz * g.D / (g.a * g.a);
     }
   }
   // block sums, one atomic per field and block
