@@ -295,8 +295,10 @@ __global__ void __launch_bounds__(256, 3) project_kernel(ProjectParams p) {
 template <typename Tst>
 __global__ void __launch_bounds__(256, 3) project_bwd_kernel(ProjectBwdParams p) {
   __shared__ TargetCam scam[kMaxTargets];
-  __shared__ float red[8][17];
+  // the block's camera-delta and colour sums per target: d/d[B' | b'] (8) and d/dC (9)
+  __shared__ float sred[kMaxTargets][17];
   for (int t = threadIdx.x; t < p.c.n_targets; t += blockDim.x) scam[t] = p.c.tcams[t];
+  for (int i = threadIdx.x; i < p.c.n_targets * 17; i += blockDim.x) (&sred[0][0])[i] = 0.0f;
   __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = k < p.c.n;
@@ -306,17 +308,18 @@ __global__ void __launch_bounds__(256, 3) project_bwd_kernel(ProjectBwdParams p)
   float dp[3] = {0, 0, 0}, dsu = 0, dsv = 0, dlno = 0, drgb[3] = {0, 0, 0};
   float dR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   const int64_t np = p.c.n_pad;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  // the next target's tile count is loaded one target ahead, so that a target's gradient record
+  // is requested without first waiting for its count
+  uint32_t count_next = alive ? p.rect[k].w : 0u;
   for (int t = 0; t < p.c.n_targets; ++t) {
     const TargetCam& cam = scam[t];
     // per target: d/d[B' | b'] (8) and d/dC of the colour correction's 3x3 block (9)
     float dBp[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     float dC22 = 0.0f;
     const int64_t rec = (int64_t)t * np + k;
-    bool live = false;
-    if (alive) {
-      live = p.rect[rec].w > 0u;  // the pair was emitted to at least one tile
-    }
+    const bool live = count_next > 0u;  // the pair was emitted to at least one tile
+    if (alive && t + 1 < p.c.n_targets) count_next = p.rect[rec + np].w;
     if (live) {
       const float4* gp = reinterpret_cast<const float4*>(p.grad + rec * kGradFields);
       const float4 a = gp[0], b = gp[1], c = gp[2], d = gp[3];
@@ -406,30 +409,29 @@ __global__ void __launch_bounds__(256, 3) project_bwd_kernel(ProjectBwdParams p)
         dC22 = H[2] * s.rgb[2];
       }
     }
-    // camera-delta and colour gradients of this target: block reduction, one atomic per field
-    const bool want_dF = p.d_dF != nullptr, want_dC = p.d_color != nullptr && !cam.sun;
-    if (want_dF || want_dC) {
+    // camera-delta and colour gradients of this target: warp sums into the block's per-target
+    // sums (no block barrier per target)
+    if (p.d_dF != nullptr || (p.d_color != nullptr && !cam.sun)) {
       const float tot = warp_reduce16_transposed(dBp);
       float t22 = dC22;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t22 += __shfl_xor_sync(0xffffffffu, t22, o);
-      if (!(lane & 1)) red[warp][lane >> 1] = tot;
-      if (lane == 0) red[warp][16] = t22;
-      __syncthreads();
-      if (threadIdx.x < 17) {
-        float acc = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
-        const int f = threadIdx.x;
-        if (acc != 0.0f) {
-          if (f < 8) {
-            if (want_dF) atomicAdd(p.d_dF + cam.cam * 8 + f, acc);
-          } else if (want_dC) {
-            const int ij = f - 8, i = ij / 3, j = ij % 3;  // dC[i][j], row-major [C | c]
-            atomicAdd(p.d_color + cam.cam * 12 + 4 * i + j, acc);
-          }
-        }
-      }
-      __syncthreads();
+      if (!(lane & 1) && tot != 0.0f) atomicAdd(&sred[t][lane >> 1], tot);
+      if (lane == 0 && t22 != 0.0f) atomicAdd(&sred[t][16], t22);
+    }
+  }
+  // one atomic per target and field for the block
+  __syncthreads();
+  for (int i = threadIdx.x; i < p.c.n_targets * 17; i += blockDim.x) {
+    const int t = i / 17, f = i - t * 17;
+    const float acc = sred[t][f];
+    if (acc == 0.0f) continue;
+    const TargetCam& cam = scam[t];
+    if (f < 8) {
+      if (p.d_dF) atomicAdd(p.d_dF + cam.cam * 8 + f, acc);
+    } else if (p.d_color && !cam.sun) {
+      const int ij = f - 8, i2 = ij / 3, j = ij % 3;  // dC[i2][j], row-major [C | c]
+      atomicAdd(p.d_color + cam.cam * 12 + 4 * i2 + j, acc);
     }
   }
   if (!alive) return;
