@@ -143,15 +143,19 @@ __global__ void __launch_bounds__(256, 8) shade_fwd_kernel(const __grid_constant
 #pragma unroll
   for (int c = 0; c < 3; ++c) rgb4[c] = ld4(v.io.rgb, c * hw + pix0, vec, hw);
   float4 V4;
+  // the first pixel's row and column (a view has fewer than 2^31 pixels: 32-bit division), then
+  // step along the row
+  int py = (int)((uint32_t)pix0 / (uint32_t)v.W), px = (int)pix0 - py * v.W;
 #pragma unroll
   for (int k = 0; k < kShadePix; ++k) {
     const int64_t pix = pix0 + k;
     float Vk = 1.0f;
-    if (pix < hw) {
-      const int py = (int)(pix / v.W), px = (int)(pix - (int64_t)py * v.W);
-      Vk = shade_geom(p, v, cam, px, py, comp(a4, k), comp(d4, k)).V;
-    }
+    if (pix < hw) Vk = shade_geom(p, v, cam, px, py, comp(a4, k), comp(d4, k)).V;
     set_comp(V4, k, Vk);
+    if (++px == v.W) {
+      px = 0;
+      ++py;
+    }
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(256, 6) shade_bwd_kernel(const __grid_constant
   // per-view sums: d La (3) and d B'[:, 0:3] (6); threads past the view add zeros
   float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (pix < hw) {
-    const int py = (int)(pix / v.W), px = (int)(pix - (int64_t)py * v.W);
+    const int py = (int)((uint32_t)pix / (uint32_t)v.W), px = (int)pix - py * v.W;  // fewer than 2^31 pixels
     // every plane value of the pixel is loaded before any gradient is stored: a store could alias
     // a later load, so loads interleaved with the read-modify-writes would wait on each other
     const float alpha = v.io.alpha[pix], depth = v.io.depth[pix];
@@ -215,8 +219,10 @@ __global__ void __launch_bounds__(256, 6) shade_bwd_kernel(const __grid_constant
       for (int t = 0; t < 4; ++t) {
         // z_s = D_s / alpha_s
         const float dzs = w[t] * dzo;
-        if (v.io.d_sun_depth) atomicAdd(v.io.d_sun_depth + tap[t], dzs / g.as[t]);
-        if (v.io.d_sun_alpha) atomicAdd(v.io.d_sun_alpha + tap[t], -dzs * g.Ds[t] / (g.as[t] * g.as[t]));
+        // gradient-only quotients: the fast division (within 2 ulp; alpha_s >= eps)
+        const float dD = __fdividef(dzs, g.as[t]);
+        if (v.io.d_sun_depth) atomicAdd(v.io.d_sun_depth + tap[t], dD);
+        if (v.io.d_sun_alpha) atomicAdd(v.io.d_sun_alpha + tap[t], -dD * g.zs[t]);
       }
       // u = S (x - h B' s): du/dh = -S B' s, du/dB'_ij = -S h s_j
       const float dh = -v.S * (dux * g.Bs0 + duy * g.Bs1);
@@ -227,18 +233,21 @@ __global__ void __launch_bounds__(256, 6) shade_bwd_kernel(const __grid_constant
       }
       // h = max_alt - z, z = D / alpha
       const float dz = d_delta - dh;
-      if (v.io.d_depth) v.io.d_depth[pix] = gz + dz / g.a;
-      if (v.io.d_alpha) v.io.d_alpha[pix] = ga + -dz * g.D / (g.a * g.a);
+      const float dDp = __fdividef(dz, g.a);  // gradient only; alpha >= eps
+      if (v.io.d_depth) v.io.d_depth[pix] = gz + dDp;
+      if (v.io.d_alpha) v.io.d_alpha[pix] = ga + -dDp * g.z;
     }
   }
   // block sums, one atomic per field and block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    // the nine warp sums by the transposed butterfly (15 shuffles instead of 45): even lane 2f
+    // ends with field f
+    float v16[16];
 #pragma unroll
-  for (int f = 0; f < 9; ++f) {
-    float x = acc[f];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) red[warp][f] = x;
+    for (int f = 0; f < 16; ++f) v16[f] = f < 9 ? acc[f] : 0.0f;
+    const float tot = warp_reduce16_transposed(v16);
+    if (!(lane & 1) && (lane >> 1) < 9) red[warp][lane >> 1] = tot;
   }
   __syncthreads();
   if (threadIdx.x < 9) {
