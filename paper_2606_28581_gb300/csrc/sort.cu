@@ -327,18 +327,20 @@ cudaError_t launch_height_keys(const void* means, int dtype, int64_t n, int64_t 
 // y = x1 | y1 << 16 (tile rectangle), z = bitmask of the tiles of the rectangle, in row-major
 // order, that the footprint touches (all ones when the rectangle has more than 32 tiles),
 // w = number of tiles kept (0: culled).
+// Both binning kernels run on a grid of (splats, targets): blockIdx.y is the target, so no
+// thread divides its flat index.
 __global__ void counts_kernel(BinParams p) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)p.n_targets * p.n) return;
-  const int64_t t = idx / p.n, r = idx - t * p.n;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y;
+  if (r >= p.n) return;
+  const int64_t idx = t * p.n + r;
   const uint32_t k = p.order[r];
   p.counts[idx] = p.rect[t * p.n_pad + k].w;
 }
 
 __global__ void emit_kernel(BinParams p) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)p.n_targets * p.n) return;
-  const int64_t t = idx / p.n, r = idx - t * p.n;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, t = blockIdx.y;
+  if (r >= p.n) return;
+  const int64_t idx = t * p.n + r;
   const uint32_t k = p.order[r];
   const uint4 rc = p.rect[t * p.n_pad + k];
   if (rc.w == 0u) return;
@@ -361,7 +363,7 @@ cudaError_t launch_counts(const BinParams& p, cudaStream_t st) {
   const int64_t m = (int64_t)p.n_targets * p.n;
   if (m == 0) return cudaSuccess;
   count_launch();
-  counts_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p);
+  counts_kernel<<<dim3((unsigned)((p.n + 255) / 256), (unsigned)p.n_targets), 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -369,7 +371,7 @@ cudaError_t launch_emit(const BinParams& p, cudaStream_t st) {
   const int64_t m = (int64_t)p.n_targets * p.n;
   if (m == 0) return cudaSuccess;
   count_launch();
-  emit_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p);
+  emit_kernel<<<dim3((unsigned)((p.n + 255) / 256), (unsigned)p.n_targets), 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
