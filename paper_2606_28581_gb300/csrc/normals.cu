@@ -77,9 +77,10 @@ struct Slots {
   static constexpr int W = kNX + 2 * HALO, N = (kNY + 2 * HALO) * W, PER = (N + kThreads - 1) / kThreads;
 };
 
-// z of the tile at (x0, y0) and its halo of HALO pixels into sz
+// z of the tile at (x0, y0) and its halo of HALO pixels into sz (and alpha into sa when given)
 template <int HALO, int SX>
-__device__ __forceinline__ void stage_z(const NormalView& v, int x0, int y0, float eps, float (*sz)[SX]) {
+__device__ __forceinline__ void stage_z(const NormalView& v, int x0, int y0, float eps, float (*sz)[SX],
+                                        float (*sa)[SX] = nullptr) {
   constexpr int PER = Slots<HALO>::PER;
   float a[PER], d[PER];
 #pragma unroll
@@ -103,6 +104,7 @@ __device__ __forceinline__ void stage_z(const NormalView& v, int x0, int y0, flo
     if (k < Slots<HALO>::N) {
       const int ty = k / Slots<HALO>::W, tx = k - ty * Slots<HALO>::W;
       sz[ty][tx] = a[r] >= eps ? d[r] / a[r] : __int_as_float(0x7fc00000);
+      if (sa) sa[ty][tx] = a[r];
     }
   }
 }
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) depth_normal_fwd_kernel(const __grid
 // per-view sums to the camera gradient once.
 __global__ void __launch_bounds__(kThreads, kNormalBwdBlocks) depth_normal_bwd_kernel(
     const __grid_constant__ NormalParams p) {
-  __shared__ float sz[kNY + 4][kNX + 5];
+  __shared__ float sz[kNY + 4][kNX + 5], sa[kNY + 4][kNX + 5];
   __shared__ float sdx[kNY + 2][kNX + 3], sdy[kNY + 2][kNX + 3];
   __shared__ float red[kThreads / 32][8];
   const int cam = blockIdx.y;
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, kNormalBwdBlocks) depth_normal_bwd_k
       }
     }
   }
-  stage_z<2>(v, x0, y0, p.eps, sz);
+  stage_z<2>(v, x0, y0, p.eps, sz, sa);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < PER1; ++r) {
@@ -251,9 +253,11 @@ __global__ void __launch_bounds__(kThreads, kNormalBwdBlocks) depth_normal_bwd_k
   __syncthreads();
   {
     // the thread's kRows pixels: every load first, then the read-modify-writes (a store could
-    // alias a later row's loads, so loads interleaved with stores would wait on each other)
+    // alias a later row's loads, so loads interleaved with stores would wait on each other).
+    // z = D / alpha (a pixel that feeds a normal has a surface): dD = dz / alpha and
+    // d alpha = -dz D / alpha^2 = -dD z, with alpha and z from the staged tile
     const int tx = threadIdx.x % kNX, ty0 = threadIdx.x / kNX;
-    float dz[kRows], a[kRows], D[kRows], gd[kRows], ga[kRows];
+    float dz[kRows], gd[kRows], ga[kRows];
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
       const int ty = ty0 + 8 * j;
@@ -261,13 +265,9 @@ __global__ void __launch_bounds__(kThreads, kNormalBwdBlocks) depth_normal_bwd_k
       dz[j] = 0.0f;
       if (px < v.W && py < v.H)
         dz[j] = sdx[ty + 1][tx + 2] - sdx[ty + 1][tx] + sdy[ty + 2][tx + 1] - sdy[ty][tx + 1];
-      a[j] = 1.0f;
-      D[j] = gd[j] = ga[j] = 0.0f;
+      gd[j] = ga[j] = 0.0f;
       if (dz[j] != 0.0f) {
-        // z = D / alpha (a pixel that feeds a normal has a surface)
         const int64_t pix = (int64_t)py * v.W + px;
-        a[j] = v.io.alpha[pix];
-        D[j] = v.io.depth[pix];
         if (v.io.d_depth) gd[j] = v.io.d_depth[pix];
         if (v.io.d_alpha) ga[j] = v.io.d_alpha[pix];
       }
@@ -275,9 +275,11 @@ __global__ void __launch_bounds__(kThreads, kNormalBwdBlocks) depth_normal_bwd_k
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
       if (dz[j] == 0.0f) continue;
-      const int64_t pix = (int64_t)(y0 + ty0 + 8 * j) * v.W + x0 + tx;
-      if (v.io.d_depth) v.io.d_depth[pix] = gd[j] + dz[j] / a[j];
-      if (v.io.d_alpha) v.io.d_alpha[pix] = ga[j] + -dz[j] * D[j] / (a[j] * a[j]);
+      const int ty = ty0 + 8 * j;
+      const int64_t pix = (int64_t)(y0 + ty) * v.W + x0 + tx;
+      const float dD = __fdividef(dz[j], sa[ty + 2][tx + 2]);  // gradient only; alpha >= eps
+      if (v.io.d_depth) v.io.d_depth[pix] = gd[j] + dD;
+      if (v.io.d_alpha) v.io.d_alpha[pix] = ga[j] + -dD * sz[ty + 2][tx + 2];
     }
   }
   }  // tiles
