@@ -281,9 +281,11 @@ __device__ __forceinline__ int compact_candidates(uint32_t mk, uint8_t* list) {
 // K3 forward
 // ------------------------------------------------------------------------------------------
 // DIST: the distortion of the blending weights along each ray is accumulated beside the planes:
-// each composited splat i adds w_i (z_i (1 - T_i) - D_i) = sum_{j<i} w_i w_j (z_i - z_j), with
-// 1 - T_i and D_i the weight and the weighted depth composited in front of it; the sum is
-// doubled when it is written.
+// each composited splat i adds w_i (zs_i (1 - T_i) - D'_i) = sum_{j<i} w_i w_j (z_i - z_j), with
+// 1 - T_i the weight composited in front of it and D'_i the weighted depth in front of it, both
+// taken relative to the depth z0 of the pixel's first composited splat (zs = z - z0).  The sum is
+// unchanged by that common shift, and with it the terms are of the size of the depth differences
+// rather than of the depths.  The sum is doubled when it is written.
 template <int TW, int TH, int BATCH, bool PERSIST, bool DIST>
 __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
   constexpr int NT = TW * TH / 2;
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
 
     // the lane's two pixels (rows py0 and py0 + 2) side by side: .x and .y
     float2 T = bc2(1.0f), D = bc2(0.0f), A0 = bc2(0.0f), A1 = bc2(0.0f), A2 = bc2(0.0f), N0 = bc2(0.0f),
-           N1 = bc2(0.0f), N2 = bc2(0.0f), Dst = bc2(0.0f);
+           N1 = bc2(0.0f), N2 = bc2(0.0f), Dst = bc2(0.0f), Dsh = bc2(0.0f), Z0f = bc2(0.0f);
     const float2 y = make_float2((float)lg.py0 + 0.5f, (float)(lg.py0 + 2) + 0.5f);
     uint32_t last0 = range.x, last1 = range.x;
     bool done0 = !(lg.px < cam.W && lg.py0 < cam.H), done1 = !(lg.px < cam.W && lg.py0 + 2 < cam.H);
@@ -353,7 +355,13 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
           const float2 aT = mul2(e.alpha, T);
           const float2 w = make_float2(take0 ? aT.x : 0.0f, take1 ? aT.y : 0.0f);
           const float2 z = fma2(bc2(f0.y), e.v, fma2(bc2(f0.x), e.u, bc2(g2.w)));
-          if (DIST) Dst = fma2(w, add2(fma2(neg2(z), T, z), neg2(D)), Dst);
+          if (DIST) {
+            // z0: T is exactly 1 until the first splat is composited (alpha >= alpha_min)
+            Z0f = make_float2(T.x == 1.0f ? z.x : Z0f.x, T.y == 1.0f ? z.y : Z0f.y);
+            const float2 zs = add2(z, neg2(Z0f));
+            Dst = fma2(w, add2(fma2(neg2(zs), T, zs), neg2(Dsh)), Dst);
+            Dsh = fma2(w, zs, Dsh);
+          }
           D = fma2(w, z, D);
           if (!SUN) {
             A0 = fma2(w, bc2(f1.y), A0);
@@ -426,12 +434,17 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
 // ------------------------------------------------------------------------------------------
 // K4 backward
 // ------------------------------------------------------------------------------------------
-// DIST: the adjoint of the distortion.  Its partial in the weight of splat m is
-// 2 (z_m W_m - M_m) + 2 (M'_m - z_m W'_m) and in its depth 2 w_m (W_m - W'_m), where W, M are the
-// weight and the weighted depth composited in front of m and W', M' those behind it.  In the
-// reverse walk W = 1 - T_m and W' = T_{m+1} - T_final, so W - W' = (1 + T_final) - T_m - T_{m+1};
-// M = D - M' - w_m z_m with D the forward's depth plane, so M' - M = E + w_m z_m with
-// E = 2 M' - D carried along the walk.  The weight partial joins the splat's per-pixel value f.
+// DIST: the adjoint of the distortion.  With W, M the weight and the weighted depth composited
+// in front of splat m and W', M' those behind it, its partial in the weight of m is
+// 2 (z_m W_m - M_m) + 2 (M'_m - z_m W'_m) and in its depth 2 w_m (W_m - W'_m).  The distortion is
+// unchanged by a common shift of a pixel's depths, so the walk carries them relative to the
+// pixel's alpha-normalised depth z0 = D / alpha_out: every term is then of the size of the depth
+// differences, not of the depths, and no difference of absolute depths is formed.  With
+// W_m = alpha_out - W'_m - w_m and M_m = D' - M'_m - w_m zs_m (zs = z - z0, D' = D - z0 alpha_out)
+// the weight partial is 2 (zs_m U_m + E_m) and the depth partial 2 w_m (U_m - w_m), where
+// U = alpha_out - 2 W' and E = 2 M' - D' are carried along the reverse walk from the weights
+// themselves (not from differences of recovered transmittances).  The weight partial joins the
+// splat's per-pixel value f.
 template <int TW, int TH, int BATCH, bool PERSIST, bool DIST>
 // Five resident blocks (20 warps): the bound keeps every variant, the distortion's included, at
 // <= 102 registers without spills.
@@ -470,7 +483,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 5) raster_bwd_kernel(const __grid
 
     // per pixel: T (recovered backwards), the composite behind (as g . S), the upstream
     float T[2], y[2], Sg[2], gD[2], gAlT[2], gR[2][3], gN[2][3];  // gAlT: d(alpha_out) T_final
-    float gDs2[2], c1[2], E[2];  // distortion: twice its upstream, 1 + T_final, 2 M' - D
+    float gDs2[2], U0[2], E[2], Z0[2];  // distortion: twice its upstream, alpha_out - 2 W', 2 M' - D', z0
     uint32_t lastp[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -479,7 +492,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 5) raster_bwd_kernel(const __grid
       y[k] = (float)py + 0.5f;
       T[k] = 1.0f;
       Sg[k] = gD[k] = gAlT[k] = 0.0f;
-      gDs2[k] = E[k] = 0.0f;
+      gDs2[k] = E[k] = Z0[k] = 0.0f;
       lastp[k] = range.x;
 #pragma unroll
       for (int c = 0; c < 3; ++c) gR[k][c] = gN[k][c] = 0.0f;
@@ -503,11 +516,13 @@ __global__ void __launch_bounds__(TW * TH / 2, 5) raster_bwd_kernel(const __grid
         if (io.d_alpha) gAlT[k] = io.d_alpha[pix] * T[k];
         if (DIST && io.d_distort) {
           gDs2[k] = 2.0f * io.d_distort[pix];
-          E[k] = -io.depth[pix];
+          const float D = io.depth[pix], aout = 1.0f - T[k];
+          Z0[k] = aout > 0.0f ? D / aout : 0.0f;
+          E[k] = -__fmaf_rn(-Z0[k], aout, D);
         }
         if (lastp[k] > range.x) atomicMax(&s_hi[hp], lastp[k]);
       }
-      c1[k] = 1.0f + T[k];
+      U0[k] = 1.0f - T[k];
     }
     // the two pixels side by side (.x, .y) for the paired FP32 arithmetic of the walk
     float2 T2 = make_float2(T[0], T[1]), Sg2 = make_float2(Sg[0], Sg[1]), gD2 = make_float2(gD[0], gD[1]);
@@ -516,8 +531,8 @@ __global__ void __launch_bounds__(TW * TH / 2, 5) raster_bwd_kernel(const __grid
                  gR2 = make_float2(gR[0][2], gR[1][2]);
     const float2 gN0 = make_float2(gN[0][0], gN[1][0]), gN1 = make_float2(gN[0][1], gN[1][1]),
                  gN2 = make_float2(gN[0][2], gN[1][2]);
-    const float2 gDsv = make_float2(gDs2[0], gDs2[1]), c1v = make_float2(c1[0], c1[1]);
-    float2 Ev = make_float2(E[0], E[1]);
+    const float2 gDsv = make_float2(gDs2[0], gDs2[1]), z0v = make_float2(Z0[0], Z0[1]);
+    float2 Ev = make_float2(E[0], E[1]), Uv = make_float2(U0[0], U0[1]);
     const float2 yy = make_float2(y[0], y[1]);
     // the group's last walked position (exclusive): its walk ends there
     uint32_t glast = max(lastp[0], lastp[1]);
@@ -612,11 +627,12 @@ __global__ void __launch_bounds__(TW * TH / 2, 5) raster_bwd_kernel(const __grid
           const float2 w = mul2(a, Ti);
           float2 dzd = bc2(0.0f);  // the distortion's partial in z
           if (DIST) {
-            const float2 dW = add2(add2(c1v, neg2(Ti)), neg2(T2));  // W - W'
-            const float2 wz = mul2(w, z);
-            gf = fma2(gDsv, fma2(z, dW, add2(Ev, wz)), gf);
-            dzd = mul2(mul2(gDsv, w), dW);
-            Ev = fma2(bc2(2.0f), wz, Ev);
+            const float2 zs = add2(z, neg2(z0v));  // depth relative to z0
+            gf = fma2(gDsv, fma2(zs, Uv, Ev), gf);
+            dzd = mul2(mul2(gDsv, w), add2(Uv, neg2(w)));  // W - W' = U - w
+            const float2 w2 = mul2(bc2(2.0f), w);
+            Uv = add2(Uv, neg2(w2));
+            Ev = fma2(w2, zs, Ev);
           }
           const float2 gs = add2(gf, neg2(Sg2));
           T2 = Ti;
