@@ -110,23 +110,27 @@ typedef struct {
 /* Rasterizer options.  ss_default_opts() fills the defaults in brackets. */
 typedef struct {
   int32_t tile_w, tile_h; /* screen tile [16 x 16]; also 32 x 8 and 8 x 32 */
-  int32_t batch;          /* splats staged per block in shared memory [256]; 128 or 256 (the
-                             backward stages 224 when 256 is asked) */
-  int32_t persistent;     /* [0] one block per tile; 1: one persistent launch that pulls
-                             (target, tile) work items from a queue */
+  int32_t batch;          /* splats a warp stages in shared memory per batch [64], the only
+                             value; each warp double-buffers its batches with cp.async copies */
+  int32_t persistent;     /* [0] one block (one warp) per work item, a 128-pixel half of a tile;
+                             1: one persistent launch whose warps pull work items from a queue */
   float sigma_px;         /* screen-space low-pass sigma, pixels [1/sqrt(2)] */
   float det_eps;          /* |det M| threshold, px^2 [1e-6] */
   float alpha_min;        /* a splat contributes iff alpha >= alpha_min [1/255] */
   float alpha_max;        /* alpha = min(alpha_max, o G^) [0.99] */
   float t_min;            /* stop before the splat that takes T below t_min [1e-4] */
-  int32_t pixels_per_thread; /* [2], the only value: each lane owns two pixels of a 4 x 4
-                                sub-block.  Tile shape, batch and persistence never change an
-                                output. */
+  int32_t pixels_per_thread; /* [4], the only value: each lane owns one column of four pixels
+                                of a 4 x 4 sub-block.  Tile shape, batch and persistence never
+                                change an output. */
   int32_t subblock_cull;  /* [1] each group of lanes walks only the staged splats whose support
                              can reach its 4 x 4 sub-block; 0 walks every staged splat in every
                              sub-block.  The outputs are identical (the test is conservative);
                              0 is slower and serves to check that. */
-  int32_t reserved;
+  int32_t count_pairs;    /* [0] 1: ss_rasterize_fwd also counts the walked (pixel, splat) pairs
+                             (alpha >= alpha_min, up to and including the stopping one) into the
+                             frame status (ss_frame_status `walked`); 0 leaves that count at 0.
+                             The count is the algorithmic work of the roofline; it costs one
+                             reduction per warp and is left out of training steps. */
 } ss_raster_opts;
 
 /* Per render target I/O (device pointers; row-major [H][W] planes of the
@@ -240,9 +244,10 @@ ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32
 /* Backward (K4, then K5 unless grads is NULL): the adjoint of ss_rasterize_fwd
  * and ss_project_splats for the same frame.  Per pixel the walk runs in reverse
  * from `last`, recovering the transmittance from T_final (Sec. 3.2
- * Eq. rasterization, differentiated); per-splat partials are reduced across
- * each warp and block before global atomics into per-(target, splat) records
- * in the workspace, which K5 (ss_project_bwd) chains through the projection.
+ * Eq. rasterization, differentiated); per-splat partials are summed over each
+ * lane's four pixels and reduced across the four lanes of a 4 x 4 sub-block,
+ * then added into per-(target, splat) records in the workspace with vector
+ * reductions in L2; K5 (ss_project_bwd) chains them through the projection.
  * Call it once per ss_project_splats: the records start from zero there.
  *   grads:   accumulated splat gradients; NULL runs K4 only, and a later
  *            ss_project_bwd for the same frame finishes the backward.
@@ -512,7 +517,8 @@ ss_status ss_dsm_init(const ss_dsm* dsm, const ss_init_opts* opts, const ss_spla
  *   needed:    intersections the last ss_bin_and_sort needed
  *   nonfinite: splats culled for non-finite values by the last projection
  *   walked:    (pixel, splat) pairs with alpha >= alpha_min that the forward passes since
- *              the last projection walked, the stopping pair included (algorithmic work)
+ *              the last projection walked, the stopping pair included (algorithmic work);
+ *              counted only by forward passes run with opts->count_pairs = 1, else 0
  *   flags:     bit 0 = intersection overflow, bit 1 = a bounded wait timed out
  * Any output pointer may be NULL.
  * Returns SS_ERR_CAPACITY / SS_ERR_TIMEOUT / SS_ERR_NONFINITE when set, else SS_OK. */
@@ -524,8 +530,7 @@ ss_status ss_frame_status(const void* ws, size_t ws_bytes, int64_t* needed, int6
 int32_t ss_device_info(int32_t* num_sms, int32_t* arch);
 
 /* Allocation-free forward render of ONE main view (no counterpart in the paper: a
- * deployment aid).  Some callers cannot call cudaMalloc: code running inside a CUDA
- * stream capture, where an allocation would break the capture; host applications that
+ * deployment aid).  Some callers cannot call cudaMalloc: host applications that
  * reserve their device memory once at start-up (a real-time viewer, an inference
  * service under a fixed memory budget); plug-ins handed a stream but no allocator.
  * This call needs no caller workspace: it runs ss_project_splats, ss_bin_and_sort and
@@ -536,8 +541,9 @@ int32_t ss_device_info(int32_t* num_sms, int32_t* arch);
  *     (HOST array of 1 ss_target_io): as for the calls above.
  *   needed: HOST out (may be NULL): intersections the view needed.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.  The call
- * synchronises `stream` to read the intersection count.  Every call shares the array and
+ * with that device current); make that first call before any stream capture.  Every
+ * call synchronises `stream` once, to read the intersection count.  Do not call it on a
+ * device again after a cudaDeviceReset of that device in the same process.  Every call shares the array and
  * keeps the last call's contents (the status block and tile ranges are cleared on each
  * call); calls that overlap on the GPU race on it.
  * Errors: SS_ERR_INVALID_ARG when the splats (or the view's intersection lists) cannot fit

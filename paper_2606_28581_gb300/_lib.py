@@ -42,7 +42,7 @@ class ss_raster_opts(ctypes.Structure):
                 ("det_eps", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("pixels_per_thread", ctypes.c_int32), ("subblock_cull", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("count_pairs", ctypes.c_int32)]
 
 
 class ss_target_io(ctypes.Structure):

@@ -26,8 +26,7 @@ from . import _lib as L
 from .frame import Frame, Outputs, grads_struct
 
 # (tile_w, tile_h, batch, pixels per thread)
-TILE_CANDIDATES = [(16, 16, 256, 2), (16, 16, 128, 2), (32, 8, 256, 2), (32, 8, 128, 2), (8, 32, 256, 2),
-                   (8, 32, 128, 2)]
+TILE_CANDIDATES = [(16, 16, 64, 4), (32, 8, 64, 4), (8, 32, 64, 4)]
 
 
 def _opts(c):
@@ -183,9 +182,25 @@ class BatchedStep:
             h_d_color.copy_(self.d_color, non_blocking=True)
 
     def check(self):
-        """Synchronise and read the status block: (status, needed, walked, flags)."""
+        """Synchronise and read the status block: (status, needed, walked, flags).  ``walked``
+        is 0 unless the last forward counted its pairs (``count_walked``)."""
         st, needed, _, walked, flags = self.frame.status()
         return st, needed, walked, flags
+
+    def count_walked(self, stream=None) -> int:
+        """Runs the forward part once eagerly with the walked-pair count (outside the graphs,
+        which run without it) and returns the number of (pixel, splat) pairs walked: those with
+        alpha >= alpha_min up to and including each pixel's stopping one."""
+        f = self.frame
+        o = L.ss_raster_opts.from_buffer_copy(f.opts)
+        o.count_pairs = 1
+        self.project(stream)
+        self.bin(stream)
+        L.rasterize_fwd(self.splats, f.cams, f.n_cams, f.passes, o, self._io_f, f.ws, f.ws_bytes, f.capacity, stream)
+        st, _, walked, _ = self.check()
+        if st != L.SS_OK:
+            raise L.SatSplatError(st, "count_walked")
+        return walked
 
     @property
     def main_pixels(self) -> int:
@@ -205,7 +220,7 @@ def _cache_path() -> str:
 
 def workload_key(cameras: Sequence, n: int, dtype, passes: int) -> str:
     h = hashlib.sha256()
-    h.update(f"{n}|{dtype}|{passes}".encode())
+    h.update(f"warp-items|{n}|{dtype}|{passes}".encode())
     for c in cameras:
         h.update(f"{c.width}x{c.height}|{c.shadow_w}x{c.shadow_h}".encode())
     name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"

@@ -55,8 +55,9 @@ ss_status check_opts(const ss_raster_opts* o) {
   const bool shape = (o->tile_w == 16 && o->tile_h == 16) || (o->tile_w == 32 && o->tile_h == 8) ||
                      (o->tile_w == 8 && o->tile_h == 32);
   if (!shape) return SS_ERR_INVALID_ARG;
-  if (o->batch != 128 && o->batch != 256) return SS_ERR_INVALID_ARG;
-  if (o->pixels_per_thread != 2) return SS_ERR_INVALID_ARG;
+  if (o->batch != 64) return SS_ERR_INVALID_ARG;
+  if (o->pixels_per_thread != 4) return SS_ERR_INVALID_ARG;
+  if (o->count_pairs != 0 && o->count_pairs != 1) return SS_ERR_INVALID_ARG;
   if (o->persistent != 0 && o->persistent != 1) return SS_ERR_INVALID_ARG;
   if (o->subblock_cull != 0 && o->subblock_cull != 1) return SS_ERR_INVALID_ARG;
   if (!finite(o->sigma_px) || !(o->sigma_px > 0.0f)) return SS_ERR_INVALID_ARG;
@@ -255,12 +256,15 @@ ss_status fill_raster(RasterParams& rp, const ss_splats* s, const Layout& L, con
   rp.total_tiles = (int32_t)L.total_tiles;
   const float sig = o->sigma_px;
   rp.k.inv2s2 = 1.0f / (2.0f * sig * sig);
+  rp.k.c_uv = -0.5f * kLog2e;
+  rp.k.c_xy = -kLog2e * rp.k.inv2s2;
   rp.k.amin = o->alpha_min;
   rp.k.amax = o->alpha_max;
   rp.cull.ln_amin = logf(o->alpha_min);
   rp.cull.sigma2 = sig * sig;
   rp.t_min = o->t_min;
   rp.subblock_cull = o->subblock_cull;
+  rp.count_pairs = bwd ? 0 : o->count_pairs;
   return SS_OK;
 }
 
@@ -299,15 +303,16 @@ void ss_default_opts(ss_raster_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->tile_w = 16;
   o->tile_h = 16;
-  o->batch = 256;
+  o->batch = 64;
   o->persistent = 0;
   o->sigma_px = 0.70710678f;
   o->det_eps = 1e-6f;
   o->alpha_min = 1.0f / 255.0f;
   o->alpha_max = 0.99f;
   o->t_min = 1e-4f;
-  o->pixels_per_thread = 2;
+  o->pixels_per_thread = 4;
   o->subblock_cull = 1;
+  o->count_pairs = 0;
 }
 
 const char* ss_status_string(ss_status s) {

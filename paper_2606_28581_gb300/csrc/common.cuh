@@ -162,7 +162,25 @@ struct PairEval {
 struct EvalConsts {
   float inv2s2;   // 1 / (2 sigma^2)
   float amin, amax;
+  float c_uv;     // -log2(e) / 2: log2 G(u) = c_uv |u|^2
+  float c_xy;     // -log2(e) / (2 sigma^2): log2 of the screen-space term = c_xy |x - c|^2
 };
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// 2^x and 1/x on the MUFU unit (PTX ex2.approx.ftz / rcp.approx.ftz, a few ulp): o G^ is formed
+// as 2^(log2 o + log2 G^), using e^y = 2^(y log2 e); subnormal results flush to zero, far below
+// alpha_min.  The reciprocal is taken of 1 - alpha in [1 - alpha_max, 1].
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 __device__ __forceinline__ PairEval eval_pair(const float4 g0, const float4 g1, const float4 g2,
                                               float x, float y, const EvalConsts& k) {
@@ -171,14 +189,15 @@ __device__ __forceinline__ PairEval eval_pair(const float4 g0, const float4 g1, 
   e.dy = __fsub_rn(__fsub_rn(y, g0.y), g0.w);
   e.u = __fmaf_rn(g1.y, e.dy, __fmul_rn(g1.x, e.dx));
   e.v = __fmaf_rn(g1.w, e.dy, __fmul_rn(g1.z, e.dx));
-  const float pu = __fmul_rn(-0.5f, __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v)));
-  const float ps = __fmul_rn(-__fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)), k.inv2s2);
+  // log2 of the two Gaussians of the lower-bounded max
+  const float pu = __fmul_rn(k.c_uv, __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v)));
+  const float ps = __fmul_rn(k.c_xy, __fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)));
   e.uwin = pu >= ps;  // only the backward reads it
-  const float lp = __fadd_rn(fmaxf(pu, ps), g2.x);  // ln(o G^) <= ln(o) <= 0
-  // branch free: the kernels evaluate several pairs side by side.  __expf is accurate to a
-  // few ulp, so alpha >= alpha_min decides the same as ln(o G^) >= ln(alpha_min) except within
-  // that error of the threshold, and both kernels take the decision from this same value.
-  const float og = __expf(lp);
+  const float lp = __fadd_rn(fmaxf(pu, ps), __fmul_rn(g2.x, kLog2e));  // log2(o G^) <= 0
+  // branch free: the kernels evaluate several pairs side by side.  ex2 is accurate to a few ulp,
+  // so alpha >= alpha_min decides the same as log2(o G^) >= log2(alpha_min) except within that
+  // error of the threshold, and both kernels take the decision from this same value.
+  const float og = ex2_ftz(lp);
   e.clamped = og > k.amax;  // only the backward reads it
   e.alpha = fminf(og, k.amax);
   e.contrib = e.alpha >= k.amin;

@@ -89,6 +89,7 @@ struct RasterParams {
   float t_min;
   int32_t subblock_cull;   // 0: every staged splat is a candidate of every sub-block
   int32_t distort;         // some target writes (forward) or back-propagates (backward) the distortion
+  int32_t count_pairs;     // the forward also counts its walked pairs into the status block
   TargetIO io[kMaxTargets];
 };
 

@@ -1,0 +1,6 @@
+// Rasterizer bwd kernels for 8 x 32 pixel tiles (see raster_impl.cuh).
+#include "raster_impl.cuh"
+
+namespace ss {
+SS_RASTER_BWD_DISPATCH(8, 32)
+}  // namespace ss

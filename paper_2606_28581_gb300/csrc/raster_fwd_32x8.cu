@@ -1,0 +1,6 @@
+// Rasterizer fwd kernels for 32 x 8 pixel tiles (see raster_impl.cuh).
+#include "raster_impl.cuh"
+
+namespace ss {
+SS_RASTER_FWD_DISPATCH(32, 8)
+}  // namespace ss

@@ -1,23 +1,27 @@
 // Forward (K3) and backward (K4) rasterization, Sec. 3.2 Eq. rasterization.
 //
-// One block renders one screen tile of one target and stages the tile's sorted splat list,
-// batch by batch, in shared memory.  Each warp owns an 8 x 8 pixel block made of four 4 x 4
-// sub-blocks; the 8 lanes of a group own one sub-block, two pixels per lane (rows r, r + 2).
-// The thread that stages a splat also forms the set of the tile's 16 sub-blocks its support can
-// reach (`subblock_mask`); each group walks only the staged splats that reach its sub-block, in
-// list order (forward) or reverse list order (backward), independently of the other groups.  A pixel's walk is therefore exactly
-// the per-pixel definition, whatever the tile shape or schedule.  With PERSIST one launch
-// sized to the GPU pulls (target, tile) items from a queue, so views of uneven size and sun
-// views share a single launch.
+// Work decomposition.  A screen tile (16 x 16, 32 x 8 or 8 x 32 px) is split into 4 x 4 pixel
+// sub-blocks.  One warp renders 128 pixels of a tile (a 16 x 8 half, or an 8 x 16 half of an
+// 8 x 32 tile): eight sub-blocks, one per group of four lanes.  Lane l of a group owns column l of
+// its sub-block, four pixels, kept as two pairs (rows 0-1 and 2-3) so that the paired FP32
+// instructions of sm_100-family GPUs compute two pixels in one issue.  A warp is a work item of
+// its own: it stages the tile's sorted splat list in its own shared memory, batch by batch, with
+// cp.async copies double-buffered against the walk, and needs no block-wide barrier.
+//
+// The thread that stages a splat forms the set of the tile's 16 sub-blocks its support can reach
+// (`subblock_mask`); each group walks only the staged splats that reach its sub-block, in list
+// order (forward) or reverse list order (backward).  A pixel's walk is therefore exactly the
+// per-pixel definition, whatever the tile shape or schedule, and every pixel runs the same FP32
+// operations in both kernels, so the backward retraces the forward's alpha decisions bit for bit.
 //
 // Backward: with T_i the transmittance in front of splat i and S_i the composite behind it
 // (normalised to T_{i+1}), d f / d alpha_i = T_i (f_i - S_i); the alpha output adds
-// T_final / (1 - alpha_i).  T_i is recovered as T_{i+1} / (1 - alpha_i) from the saved
-// T_final (alpha <= alpha_max < 1 keeps the division safe); only T_final and the end of the
-// walk are stored per pixel.  A lane first sums its two pixels' gradient contributions, the
-// 8 lanes of a group reduce the 16 fields with a transposed butterfly (14 shuffles, each lane
-// ends with 2 fields), groups meet in shared memory, and one global atomic per (tile, splat,
-// field) leaves the block.
+// T_final / (1 - alpha_i).  T_i is recovered as T_{i+1} / (1 - alpha_i) from the saved T_final
+// (alpha <= alpha_max < 1 keeps the division safe); only T_final and the end of the walk are
+// stored per pixel.  A lane sums its four pixels' contributions to the 16 gradient fields of the
+// splat, the four lanes of the group reduce them with a transposed butterfly (each lane ends with
+// four fields), and each lane adds its four fields to the (target, splat) gradient record with one
+// vector reduction in L2 (red.global.add.v4.f32).
 #pragma once
 
 #include <type_traits>
@@ -26,7 +30,8 @@
 
 namespace ss {
 
-constexpr int kSaccStride = kGradFields + 1;  // padded rows: groups on different splats hit different banks
+constexpr int kWarpPixels = 128;  // pixels of one warp work item
+constexpr int kItemsPerTile = 2;  // every tile shape holds 256 pixels
 
 __device__ __forceinline__ int find_target(const TargetCam* tc, int n_targets, int tile) {
   int lo = 0, hi = n_targets - 1;
@@ -38,19 +43,20 @@ __device__ __forceinline__ int find_target(const TargetCam* tc, int n_targets, i
 }
 
 // ---------------------------------------------------------------- paired FP32 arithmetic
-// A lane's two pixels share every operation, so the forward keeps their state in float2 and
-// uses the paired FP32 instructions (one issue, two IEEE round-to-nearest results), each lane
-// bitwise equal to the scalar operation.
+// Two pixels share every operation: their state is a float2 and the paired FP32 instructions
+// (one issue, two IEEE round-to-nearest results) compute both halves, each bitwise equal to the
+// scalar operation.
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float hsum(float2 v) { return v.x + v.y; }
 
-// eval_pair (common.cuh) of one splat at a lane's two pixels (x, y.x) and (x, y.y), with the
-// same operations in the same order: bitwise the same alpha and decisions as two scalar calls.
+// eval_pair (common.cuh) of one splat at two pixels (x, y.x) and (x, y.y) of one column, with
+// the same operations in the same order: bitwise the same alpha and decisions as two scalar calls.
 struct PairEval2 {
-  float dx;                   // x - c (the lane's pixels share a column)
+  float dx;                   // x - c (the two pixels share a column)
   float2 dy, u, v, alpha;
   bool contrib0, contrib1;    // alpha >= alpha_min
   bool uwin0, uwin1;          // the uv Gaussian won the max (ties: uv)
@@ -66,12 +72,12 @@ __device__ __forceinline__ PairEval2 eval_pair2(const float4 g0, const float4 g1
   e.dy = dy;
   e.u = fma2(bc2(g1.y), dy, bc2(__fmul_rn(g1.x, dx)));
   e.v = fma2(bc2(g1.w), dy, bc2(__fmul_rn(g1.z, dx)));
-  const float2 pu = mul2(bc2(-0.5f), fma2(e.u, e.u, mul2(e.v, e.v)));
-  const float2 ps = mul2(neg2(fma2(bc2(dx), bc2(dx), mul2(dy, dy))), bc2(k.inv2s2));
+  const float2 pu = mul2(bc2(k.c_uv), fma2(e.u, e.u, mul2(e.v, e.v)));
+  const float2 ps = mul2(bc2(k.c_xy), fma2(bc2(dx), bc2(dx), mul2(dy, dy)));
   e.uwin0 = pu.x >= ps.x;
   e.uwin1 = pu.y >= ps.y;
-  const float2 lp = add2(make_float2(fmaxf(pu.x, ps.x), fmaxf(pu.y, ps.y)), bc2(g2.x));
-  const float og0 = __expf(lp.x), og1 = __expf(lp.y);
+  const float2 lp = add2(make_float2(fmaxf(pu.x, ps.x), fmaxf(pu.y, ps.y)), bc2(__fmul_rn(g2.x, kLog2e)));
+  const float og0 = ex2_ftz(lp.x), og1 = ex2_ftz(lp.y);
   e.clamped0 = og0 > k.amax;
   e.clamped1 = og1 > k.amax;
   e.alpha = make_float2(fminf(og0, k.amax), fminf(og1, k.amax));
@@ -80,89 +86,83 @@ __device__ __forceinline__ PairEval2 eval_pair2(const float4 g0, const float4 g1
   return e;
 }
 
-// Transposed reduction of 16 values over the 8 lanes of a group: lane gl of the group ends
-// with the group sums of fields 2 gl and 2 gl + 1 (in v[0], v[1]).
-__device__ __forceinline__ void group_reduce16(float v[16]) {
+// Transposed reduction of 16 values over the 4 lanes of a group: lane gl of the group ends with
+// the group sums of fields 4 gl .. 4 gl + 3 (12 shuffles; each exchange sends the half of the
+// values that the partner keeps).
+__device__ __forceinline__ float4 group_reduce16(float v[16]) {
   const int lane = threadIdx.x & 31;
+  const bool up2 = lane & 2, up1 = lane & 1;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const bool up = lane & 4;
-    const float send = up ? v[i] : v[i + 8];
-    const float keep = up ? v[i + 8] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const bool up = lane & 2;
-    const float send = up ? v[i] : v[i + 4];
-    const float keep = up ? v[i + 4] : v[i];
+    const float send = up2 ? v[i] : v[i + 8];
+    const float keep = up2 ? v[i + 8] : v[i];
     v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool up = lane & 1;
-    const float send = up ? v[i] : v[i + 2];
-    const float keep = up ? v[i + 2] : v[i];
+  for (int i = 0; i < 4; ++i) {
+    const float send = up1 ? v[i] : v[i + 4];
+    const float keep = up1 ? v[i + 4] : v[i];
     v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
   }
+  return make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// Work item of a block (forward): one block per tile, or the next item of the persistent queue.
-template <bool PERSIST>
-__device__ __forceinline__ bool next_item(const RasterParams& p, unsigned int* counter, int& tile, int& s_item) {
-  if (!PERSIST) {
-    tile = blockIdx.x;
-    return true;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
-  __syncthreads();
-  const int it = s_item;
-  if (it >= p.total_tiles) return false;
-  tile = p.items ? (int)p.items[it] : it;
-  return true;
+// One vector reduction of four floats into global memory (16-byte aligned), performed in L2.
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
 }
 
-// Work items of a block (backward).  A persistent block claims its next (target, tile) item
-// while it works on the current one (s_item[cur ^ 1]), so claiming needs no barrier of its own:
-// the one barrier at the top of each iteration frees the shared buffers of the previous tile,
-// publishes the claim made during it, and orders the claim's overwrite after every read of the
-// slot.
-template <bool PERSIST>
-__device__ __forceinline__ bool begin_item(const RasterParams& p, unsigned int* counter, int* s_item, int& cur,
-                                           int iter, int& tile) {
-  __syncthreads();
-  if (!PERSIST) {
-    tile = blockIdx.x;
-    return iter == 0;
-  }
-  const int it = s_item[cur];
-  if (it >= p.total_tiles) return false;
-  if (threadIdx.x == 0) s_item[cur ^ 1] = (int)atomicAdd(counter, 1u);
-  cur ^= 1;
-  tile = p.items ? (int)p.items[it] : it;
-  return true;
+// ---------------------------------------------------------------- asynchronous staging
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Pixels of this lane, and the tile's origin.
+// Shared memory of one warp: two buffers of B staged records (geometry 48 B, features 32 B, the
+// splat index), the sub-block masks of the current batch and each group's candidate list.
+template <int B>
+struct WarpStage {
+  float4 g[2][B][3];
+  float4 f[2][B][2];
+  uint32_t k[2][B];
+  uint32_t mask[B];
+  uint8_t list[8][B + 4];  // per group its candidates' slots (buffer * B + index); rows padded so that
+                           // the groups read at one position from different banks
+};
+
+// Pixels of this lane and the tile's origin.  The warp's half of the tile is 16 x 8 (8 x 16 for
+// 8-wide tiles); its eight 4 x 4 sub-blocks go to the eight groups in row-major order.
 struct LaneGeom {
   int px;        // pixel column
-  int py0;       // first pixel row; the second is py0 + 2
+  int py0;       // first of the lane's four pixel rows
+  int sub;       // bit of the lane's sub-block in the tile's 16-bit sub-block mask
   float x0, y0;  // the tile's first pixel column and row
 };
 
 template <int TW, int TH>
-__device__ __forceinline__ LaneGeom lane_geom(const TargetCam& cam, int tile) {
-  constexpr int WBX = TW / 8;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int grp = lane >> 3, gl = lane & 7;
+__device__ __forceinline__ int group_sub(int half, int grp) {
+  constexpr int WW = TW >= 16 ? 16 : 8, WH = kWarpPixels / WW;
+  constexpr int WX = TW / WW, GX = WW / 4, SBX = TW / 4;
+  const int wx = half % WX, wy = half / WX;
+  const int sbx = wx * GX + grp % GX, sby = wy * (WH / 4) + grp / GX;
+  return sby * SBX + sbx;
+}
+
+template <int TW, int TH>
+__device__ __forceinline__ LaneGeom lane_geom(const TargetCam& cam, int tile, int half) {
+  constexpr int SBX = TW / 4;
+  const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3;
   const int local = tile - cam.tile_base;
   const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
-  const int sbx = tx * TW + (warp % WBX) * 8 + (grp & 1) * 4;
-  const int sby = ty * TH + (warp / WBX) * 8 + (grp >> 1) * 4;
   LaneGeom g;
-  g.px = sbx + (gl & 3);
-  g.py0 = sby + (gl >> 2);
+  g.sub = group_sub<TW, TH>(half, grp);
+  const int sby = g.sub / SBX, sbx = g.sub - sby * SBX;
+  g.px = tx * TW + sbx * 4 + gl;
+  g.py0 = ty * TH + sby * 4;
   g.x0 = (float)(tx * TW);
   g.y0 = (float)(ty * TH);
   return g;
@@ -226,56 +226,131 @@ __device__ __forceinline__ uint32_t subblock_mask(const float4 g0, const float4 
   return mask;
 }
 
-// Candidate masks of a whole staged batch from the per-splat sub-block masks: lane gl of a
-// group ends with the group's mask of chunk gl (staged splats [32 gl, 32 gl + 32)).  Holding
-// every chunk at once lets a group walk its candidates across chunk boundaries, so the groups
-// of a warp stay busy until the warp's total work, not each chunk's largest group, is done.
-template <int TW, int BATCH>
-__device__ __forceinline__ uint32_t batch_masks(const uint32_t* smask, int nb) {
-  static_assert(BATCH % 32 == 0 && BATCH / 32 <= 8, "one chunk per lane of a group");
-  constexpr int WBX = TW / 8, SBX = TW / 4;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, gl = lane & 7;
-  // bit of this warp's first sub-block; its groups add 0, 1, SBX, SBX + 1
-  const int base = (warp / WBX) * 2 * SBX + (warp % WBX) * 2;
+// Candidate masks of a staged batch: lane gl of a group ends with the group's mask of chunk gl
+// (staged splats [32 gl, 32 gl + 32)).  Holding every chunk at once lets a group walk its
+// candidates across chunk boundaries.
+template <int TW, int TH, int B>
+__device__ __forceinline__ uint32_t batch_masks(const uint32_t* smask, int nb, int half) {
+  static_assert(B % 32 == 0 && B / 32 <= 4, "one chunk per lane of a group");
+  const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3;
   uint32_t mk = 0;
-#pragma unroll 1
-  for (int c0 = 0; c0 < nb; c0 += 32) {
-    const int i = c0 + lane;
-    const uint32_t v = i < nb ? smask[i] >> base : 0u;
-    const uint32_t m0 = __ballot_sync(0xffffffffu, v & 1u);
-    const uint32_t m1 = __ballot_sync(0xffffffffu, (v >> 1) & 1u);
-    const uint32_t m2 = __ballot_sync(0xffffffffu, (v >> SBX) & 1u);
-    const uint32_t m3 = __ballot_sync(0xffffffffu, (v >> (SBX + 1)) & 1u);
-    const uint32_t mine = grp == 0 ? m0 : grp == 1 ? m1 : grp == 2 ? m2 : m3;
-    mk = (gl == (c0 >> 5)) ? mine : mk;
+#pragma unroll
+  for (int c = 0; c < B / 32; ++c) {
+    if (c * 32 >= nb) break;  // warp-uniform
+    const int i = c * 32 + lane;
+    const uint32_t v = i < nb ? smask[i] : 0u;
+#pragma unroll
+    for (int gg = 0; gg < 8; ++gg) {
+      const uint32_t m = __ballot_sync(0xffffffffu, (v >> group_sub<TW, TH>(half, gg)) & 1u);
+      mk = (grp == gg && gl == c) ? m : mk;
+    }
   }
   return mk;
 }
 
-// Writes a group's candidates (the set bits of its chunk masks, lane gl holding chunk gl) to the
-// group's list of staged-splat indices, in list order, and returns their number.  The walk then
-// reads its next splat from the list at a position that depends on the step count alone, so no
-// step waits on the previous one to find its splat.  Every lane of the warp takes part.
-__device__ __forceinline__ int compact_candidates(uint32_t mk, uint8_t* list) {
-  const int gl = threadIdx.x & 7;
+// Writes a group's candidates of a staged batch (the set bits of its chunk masks, lane gl holding
+// chunk gl) to the group's list as shared-memory slots (slot_base + index), in list order or, with
+// `desc`, in reverse list order, and returns their number.  The walk then reads its next splat
+// from the list at a position that depends on the step count alone, so no step waits on the
+// previous one to find its splat.  Every lane of the warp takes part.
+__device__ __forceinline__ int compact_candidates(uint32_t mk, uint8_t* list, int slot_base, bool desc) {
+  const int gl = threadIdx.x & 3;
   const int c = __popc(mk);
   int inc = c;
-#pragma unroll
-  for (int o = 1; o < 8; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, inc, o, 8);
-    if (gl >= o) inc += t;
-  }
-  const int total = __shfl_sync(0xffffffffu, inc, 7, 8);
-  int pos = inc - c;
+  int t = __shfl_up_sync(0xffffffffu, inc, 1, 4);
+  if (gl >= 1) inc += t;
+  t = __shfl_up_sync(0xffffffffu, inc, 2, 4);
+  if (gl >= 2) inc += t;
+  const int total = __shfl_sync(0xffffffffu, inc, 3, 4);
+  int k = inc - c;
   uint32_t mm = mk;
   while (mm) {
     const int bit = __ffs(mm) - 1;
     mm &= mm - 1;
-    list[pos++] = (uint8_t)(gl * 32 + bit);
+    list[desc ? total - 1 - k : k] = (uint8_t)(slot_base + gl * 32 + bit);
+    ++k;
   }
   __syncwarp();
   return total;
 }
+
+// Splat indices of a batch (lane c of chunk c), loaded one batch ahead of their copies.
+template <int B>
+__device__ __forceinline__ void load_vals(uint32_t (&kv)[B / 32], const uint32_t* vals, uint32_t b0, int nb) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < B / 32; ++c) {
+    const int i = c * 32 + lane;
+    kv[c] = i < nb ? __ldg(vals + b0 + i) : 0u;
+  }
+}
+
+// Issues the asynchronous copies of a batch's records into buffer `buf` (one commit group).
+// A sun view composites depth alone and needs only the first feature vector.
+template <int B>
+__device__ __forceinline__ void stage_issue(WarpStage<B>& S, int buf, const uint32_t (&kv)[B / 32], int nb,
+                                            const RasterParams& p, int64_t recbase, bool sun) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < B / 32; ++c) {
+    const int i = c * 32 + lane;
+    if (i < nb) {
+      const int64_t rec = recbase + kv[c];
+      const float4* g = p.geom + rec * 3;
+      const float4* f = p.feat + rec * 2;
+      cp_async16(&S.g[buf][i][0], g);
+      cp_async16(&S.g[buf][i][1], g + 1);
+      cp_async16(&S.g[buf][i][2], g + 2);
+      cp_async16(&S.f[buf][i][0], f);
+      if (!sun) cp_async16(&S.f[buf][i][1], f + 1);
+      S.k[buf][i] = kv[c];
+    }
+  }
+  cp_async_commit();
+}
+
+// Sub-block masks of a landed batch: each lane reads the records it copied itself.
+template <int TW, int TH, int B>
+__device__ __forceinline__ void stage_masks(WarpStage<B>& S, int buf, int nb, const LaneGeom& lg,
+                                            const RasterParams& p) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < B / 32; ++c) {
+    const int i = c * 32 + lane;
+    if (i < nb)
+      S.mask[i] = p.subblock_cull ? subblock_mask<TW, TH>(S.g[buf][i][0], S.g[buf][i][1], S.g[buf][i][2], lg.x0,
+                                                          lg.y0, p.cull)
+                                  : 0xffffu;
+  }
+}
+
+// Work item of a warp: one per tile half, or the next item of the persistent queue (claimed one
+// item ahead, so the claim's latency overlaps the current item).
+template <bool PERSIST>
+struct ItemQueue {
+  unsigned int* counter;
+  int item, next;
+  __device__ __forceinline__ void begin(unsigned int* c) {
+    counter = c;
+    if (PERSIST) {
+      int v = 0;
+      if ((threadIdx.x & 31) == 0) v = (int)atomicAdd(counter, 1u);
+      item = __shfl_sync(0xffffffffu, v, 0);
+    } else {
+      item = blockIdx.x;
+    }
+    next = 0;
+  }
+  __device__ __forceinline__ void claim_next() {
+    if (PERSIST && (threadIdx.x & 31) == 0) next = (int)atomicAdd(counter, 1u);
+  }
+  // false when this warp has no item left
+  __device__ __forceinline__ bool advance() {
+    if (!PERSIST) return false;
+    item = __shfl_sync(0xffffffffu, next, 0);
+    return true;
+  }
+};
 
 // ------------------------------------------------------------------------------------------
 // K3 forward
@@ -286,148 +361,175 @@ __device__ __forceinline__ int compact_candidates(uint32_t mk, uint8_t* list) {
 // taken relative to the depth z0 of the pixel's first composited splat (zs = z - z0).  The sum is
 // unchanged by that common shift, and with it the terms are of the size of the depth differences
 // rather than of the depths.  The sum is doubled when it is written.
-template <int TW, int TH, int BATCH, bool PERSIST, bool DIST>
-__global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
-  constexpr int NT = TW * TH / 2;
-  static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are whole 8 x 8 warp blocks");
-  __shared__ float4 sg[BATCH][3];
-  __shared__ float4 sf[BATCH][2];
-  __shared__ uint32_t smask[BATCH];
-  __shared__ uint8_t slist[NT / 8][BATCH + 4];  // candidates of each group (rows padded: the 4 groups of a warp read at one position from different banks)
-  __shared__ int s_item;
-  const int tid = threadIdx.x, lane = tid & 31;
-  int tile;
-  bool first = true;
-  while (true) {
-    if (!PERSIST && !first) break;
-    first = false;
-    if (!next_item<PERSIST>(p, &p.status->work_fwd, tile, s_item)) break;
+
+// Compositing state of one pixel pair of a lane.
+struct FwdPair {
+  float2 T, D, A0, A1, A2, N0, N1, N2, Dst, Dsh, Z0;
+  uint32_t last0, last1;
+  bool done0, done1;
+};
+
+__device__ __forceinline__ void fwd_init(FwdPair& s, uint32_t start, bool out0, bool out1) {
+  s.T = bc2(1.0f);
+  s.D = s.A0 = s.A1 = s.A2 = s.N0 = s.N1 = s.N2 = s.Dst = s.Dsh = s.Z0 = bc2(0.0f);
+  s.last0 = s.last1 = start;
+  s.done0 = out0;
+  s.done1 = out1;
+}
+
+// Composites one splat into a pixel pair (Eq. rasterization, front to back); returns the number
+// of walked pairs (contributing, the stopping one included).  A sun view composites depth alone.
+template <bool SUN, bool DIST>
+__device__ __forceinline__ uint32_t composite(FwdPair& s, const PairEval2& e, bool has, const float4& g2,
+                                              const float4& f0, const float4& f1, uint32_t pos, float t_min) {
+  const bool ck0 = has && !s.done0 && e.contrib0, ck1 = has && !s.done1 && e.contrib1;
+  const float2 Tn = mul2(s.T, add2(bc2(1.0f), neg2(e.alpha)));
+  // a splat that takes T below t_min ends the walk and is not composited
+  const bool stop0 = ck0 && Tn.x < t_min, stop1 = ck1 && Tn.y < t_min;
+  const bool take0 = ck0 && !stop0, take1 = ck1 && !stop1;
+  const float2 aT = mul2(e.alpha, s.T);
+  const float2 w = make_float2(take0 ? aT.x : 0.0f, take1 ? aT.y : 0.0f);
+  const float2 z = fma2(bc2(f0.y), e.v, fma2(bc2(f0.x), e.u, bc2(g2.w)));
+  if (DIST) {
+    // z0: T is exactly 1 until the first splat is composited (alpha >= alpha_min)
+    s.Z0 = make_float2(s.T.x == 1.0f ? z.x : s.Z0.x, s.T.y == 1.0f ? z.y : s.Z0.y);
+    const float2 zs = add2(z, neg2(s.Z0));
+    s.Dst = fma2(w, add2(fma2(neg2(zs), s.T, zs), neg2(s.Dsh)), s.Dst);
+    s.Dsh = fma2(w, zs, s.Dsh);
+  }
+  s.D = fma2(w, z, s.D);
+  if (!SUN) {
+    s.A0 = fma2(w, bc2(f1.y), s.A0);
+    s.A1 = fma2(w, bc2(f1.z), s.A1);
+    s.A2 = fma2(w, bc2(f1.w), s.A2);
+    s.N0 = fma2(w, bc2(f0.z), s.N0);
+    s.N1 = fma2(w, bc2(f0.w), s.N1);
+    s.N2 = fma2(w, bc2(f1.x), s.N2);
+  }
+  s.T = make_float2(take0 ? Tn.x : s.T.x, take1 ? Tn.y : s.T.y);
+  s.last0 = take0 ? pos : s.last0;
+  s.last1 = take1 ? pos : s.last1;
+  s.done0 = s.done0 || stop0;
+  s.done1 = s.done1 || stop1;
+  return (uint32_t)ck0 + (uint32_t)ck1;
+}
+
+// COUNT: the launch also counts the walked pairs (the algorithmic work of the roofline) into the
+// status block; the training step runs without it.
+template <int TW, int TH, int B, bool PERSIST, bool DIST, bool COUNT>
+__global__ void __launch_bounds__(32, 16) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
+  static_assert(TW * TH == kItemsPerTile * kWarpPixels, "two warp items per tile");
+  __shared__ WarpStage<B> S;
+  const int lane = threadIdx.x & 31, grp = lane >> 2;
+  const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  ItemQueue<PERSIST> q;
+  q.begin(&p.status->work_fwd);
+  const int n_items = p.total_tiles * kItemsPerTile;
+  while (q.item < n_items) {
+    q.claim_next();
+    const int tile = q.item / kItemsPerTile, half = q.item % kItemsPerTile;
     const int t = find_target(p.tcams, p.n_targets, tile);
     const TargetCam& cam = p.tcams[t];
-    const LaneGeom lg = lane_geom<TW, TH>(cam, tile);
+    const LaneGeom lg = lane_geom<TW, TH>(cam, tile, half);
     const bool sun = cam.sun != 0;
     const float x = (float)lg.px + 0.5f;
+    const float yb = (float)lg.py0 + 0.5f;
+    const float2 yA = make_float2(yb, yb + 1.0f), yB = make_float2(yb + 2.0f, yb + 3.0f);
     const uint2 range = p.ranges[tile];
     const int64_t recbase = (int64_t)t * p.n_pad;
-
-    // the lane's two pixels (rows py0 and py0 + 2) side by side: .x and .y
-    float2 T = bc2(1.0f), D = bc2(0.0f), A0 = bc2(0.0f), A1 = bc2(0.0f), A2 = bc2(0.0f), N0 = bc2(0.0f),
-           N1 = bc2(0.0f), N2 = bc2(0.0f), Dst = bc2(0.0f), Dsh = bc2(0.0f), Z0f = bc2(0.0f);
-    const float2 y = make_float2((float)lg.py0 + 0.5f, (float)(lg.py0 + 2) + 0.5f);
-    uint32_t last0 = range.x, last1 = range.x;
-    bool done0 = !(lg.px < cam.W && lg.py0 < cam.H), done1 = !(lg.px < cam.W && lg.py0 + 2 < cam.H);
-    uint32_t walked = 0;  // contributing pairs, the stopping one included
-    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += BATCH) {
-      const int nb = min((int)(range.y - b0), BATCH);
-      __syncthreads();
-      for (int i = tid; i < nb; i += NT) {
-        const int64_t rec = recbase + p.vals[b0 + i];
-        const float4* g = p.geom + rec * 3;
-        const float4* f = p.feat + rec * 2;
-        const float4 g0 = g[0], g1 = g[1], g2 = g[2];
-        sg[i][0] = g0;
-        sg[i][1] = g1;
-        sg[i][2] = g2;
-        sf[i][0] = f[0];
-        if (!sun) sf[i][1] = f[1];  // a sun view composites depth alone
-        smask[i] = p.subblock_cull ? subblock_mask<TW, TH>(g0, g1, g2, lg.x0, lg.y0, p.cull) : 0xffffu;
+    const bool inx = lg.px < cam.W;
+    FwdPair sA, sB;
+    fwd_init(sA, range.x, !(inx && lg.py0 < cam.H), !(inx && lg.py0 + 1 < cam.H));
+    fwd_init(sB, range.x, !(inx && lg.py0 + 2 < cam.H), !(inx && lg.py0 + 3 < cam.H));
+    uint32_t walked = 0;
+    // batches of B list entries in list order; batch k is copied into buffer k & 1 while batch
+    // k - 1 is walked
+    const int n = (int)(range.y - range.x), nbat = (n + B - 1) / B;
+    auto nb_of = [&](int k) { return min(n - k * B, B); };
+    uint8_t* list = S.list[grp];
+    uint32_t kv[B / 32];  // splat indices of the next batch to copy
+    if (nbat > 0) {
+      load_vals<B>(kv, p.vals, range.x, nb_of(0));
+      stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
+      if (nbat > 1) load_vals<B>(kv, p.vals, range.x + B, nb_of(1));
+    }
+    for (int bi = 0; bi < nbat; ++bi) {
+      const int buf = bi & 1;
+      const uint32_t b0 = range.x + (uint32_t)(bi * B);
+      const int nb = nb_of(bi);
+      const bool all_done = sA.done0 && sA.done1 && sB.done0 && sB.done1;
+      if (__all_sync(0xffffffffu, all_done)) break;
+      if (bi + 1 < nbat) {
+        // the next batch's copies overlap this batch's walk
+        stage_issue<B>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
+        if (bi + 2 < nbat) load_vals<B>(kv, p.vals, range.x + (uint32_t)((bi + 2) * B), nb_of(bi + 2));
+        cp_async_wait_prev();
+      } else {
+        cp_async_wait_all();
       }
-      const bool all_done = done0 && done1;
-      if (__syncthreads_and(all_done)) break;
-      const uint32_t mk = batch_masks<TW, BATCH>(smask, nb);
+      __syncwarp();  // every lane's copies of this batch are visible to the warp
+      stage_masks<TW, TH, B>(S, buf, nb, lg, p);
+      uint32_t mk = batch_masks<TW, TH, B>(S.mask, nb, half);
       // a group whose 16 pixels have all stopped walks nothing
-      const bool gdone = ((__ballot_sync(0xffffffffu, all_done) >> (lane & 24)) & 0xffu) == 0xffu;
-      const uint8_t* list = slist[tid >> 3];
-      const int total = compact_candidates(gdone ? 0u : mk, slist[tid >> 3]);
+      if (((__ballot_sync(0xffffffffu, all_done) >> (lane & 28)) & 0xfu) == 0xfu) mk = 0u;
+      const int total = compact_candidates(mk, list, buf * B, false);
       const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
-      // two splats per step: their pair evaluations are independent; only the compositing
-      // runs in order (splat a, then splat b) for each pixel.  A sun view (SUN) composites
-      // depth alone: it has no colour or normal output.
       auto walk = [&](auto sun_c) {
         constexpr bool SUN = decltype(sun_c)::value;
-        auto composite = [&](const PairEval2& e, bool ck0, bool ck1, const float4& g2, const float4& f0,
-                             const float4& f1, uint32_t pos) {
-          const float2 Tn = mul2(T, add2(bc2(1.0f), neg2(e.alpha)));
-          // a splat that takes T below t_min ends the walk and is not composited
-          const bool stop0 = ck0 && Tn.x < p.t_min, stop1 = ck1 && Tn.y < p.t_min;
-          const bool take0 = ck0 && !stop0, take1 = ck1 && !stop1;
-          const float2 aT = mul2(e.alpha, T);
-          const float2 w = make_float2(take0 ? aT.x : 0.0f, take1 ? aT.y : 0.0f);
-          const float2 z = fma2(bc2(f0.y), e.v, fma2(bc2(f0.x), e.u, bc2(g2.w)));
-          if (DIST) {
-            // z0: T is exactly 1 until the first splat is composited (alpha >= alpha_min)
-            Z0f = make_float2(T.x == 1.0f ? z.x : Z0f.x, T.y == 1.0f ? z.y : Z0f.y);
-            const float2 zs = add2(z, neg2(Z0f));
-            Dst = fma2(w, add2(fma2(neg2(zs), T, zs), neg2(Dsh)), Dst);
-            Dsh = fma2(w, zs, Dsh);
-          }
-          D = fma2(w, z, D);
-          if (!SUN) {
-            A0 = fma2(w, bc2(f1.y), A0);
-            A1 = fma2(w, bc2(f1.z), A1);
-            A2 = fma2(w, bc2(f1.w), A2);
-            N0 = fma2(w, bc2(f0.z), N0);
-            N1 = fma2(w, bc2(f0.w), N1);
-            N2 = fma2(w, bc2(f1.x), N2);
-          }
-          T = make_float2(take0 ? Tn.x : T.x, take1 ? Tn.y : T.y);
-          last0 = take0 ? pos : last0;
-          last1 = take1 ? pos : last1;
-          done0 = done0 || stop0;
-          done1 = done1 || stop1;
-        };
-        for (int st = 0; st < nsteps; st += 2) {
+        for (int st = 0; st < nsteps; ++st) {
           // lanes whose group has nothing left evaluate a stand-in and composite nothing
-          const bool has_a = st < total, has_b = st + 1 < total;
-          const int ja = has_a ? list[st] : 0;
-          const int jb = has_b ? list[st + 1] : ja;
-          const float4 ga0 = sg[ja][0], ga1 = sg[ja][1], ga2 = sg[ja][2];
-          const float4 gb0 = sg[jb][0], gb1 = sg[jb][1], gb2 = sg[jb][2];
-          const PairEval2 ea = eval_pair2(ga0, ga1, ga2, x, y, p.k);
-          const PairEval2 eb = eval_pair2(gb0, gb1, gb2, x, y, p.k);
-          const float4 fa0 = sf[ja][0], fb0 = sf[jb][0];
-          const float4 fa1 = SUN ? zero4 : sf[ja][1], fb1 = SUN ? zero4 : sf[jb][1];
-          const uint32_t pa = b0 + (uint32_t)ja + 1u, pb = b0 + (uint32_t)jb + 1u;
-          const bool ca0 = has_a && !done0 && ea.contrib0, ca1 = has_a && !done1 && ea.contrib1;
-          walked += (uint32_t)ca0 + (uint32_t)ca1;
-          composite(ea, ca0, ca1, ga2, fa0, fa1, pa);
-          const bool cb0 = has_b && !done0 && eb.contrib0, cb1 = has_b && !done1 && eb.contrib1;
-          walked += (uint32_t)cb0 + (uint32_t)cb1;
-          composite(eb, cb0, cb1, gb2, fb0, fb1, pb);
+          const bool has = st < total;
+          const int slot = has ? (int)list[st] : buf * B;
+          const float4* gs = &S.g[0][0][0] + slot * 3;
+          const float4* fs = &S.f[0][0][0] + slot * 2;
+          const float4 g0 = gs[0], g1 = gs[1], g2 = gs[2];
+          const float4 f0 = fs[0];
+          const float4 f1 = SUN ? zero4 : fs[1];
+          const PairEval2 eA = eval_pair2(g0, g1, g2, x, yA, p.k);
+          const PairEval2 eB = eval_pair2(g0, g1, g2, x, yB, p.k);
+          const uint32_t pos = b0 + (uint32_t)(slot & (B - 1)) + 1u;
+          const uint32_t wa = composite<SUN, DIST>(sA, eA, has, g2, f0, f1, pos, p.t_min);
+          const uint32_t wb = composite<SUN, DIST>(sB, eB, has, g2, f0, f1, pos, p.t_min);
+          if (COUNT) walked += wa + wb;
         }
       };
       if (sun) walk(std::true_type{}); else walk(std::false_type{});
+      __syncwarp();  // the buffer and the lists are refilled next
     }
-    const TargetIO io = p.io[t];
+    cp_async_wait_all();  // no copy is left in flight when the walk ends early
+    const TargetIO& io = p.io[t];
     const int64_t hw = (int64_t)cam.W * cam.H;
-    auto pick = [](float2 v, int k) { return k == 0 ? v.x : v.y; };
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int py = lg.py0 + 2 * k;
-      if (!(lg.px < cam.W && py < cam.H)) continue;
+    for (int k = 0; k < 4; ++k) {
+      const FwdPair& s = k < 2 ? sA : sB;
+      const bool hi = k & 1;
+      const int py = lg.py0 + k;
+      if (!(inx && py < cam.H)) continue;
       const int64_t pix = (int64_t)py * cam.W + lg.px;
+      auto pick = [hi](float2 v) { return hi ? v.y : v.x; };
       if (io.rgb) {
         // the splats carry C rgb; the offset c completes C A + c (Sec. 3.1 Eq. image_formation)
-        io.rgb[pix] = pick(A0, k) + cam.C[3];
-        io.rgb[hw + pix] = pick(A1, k) + cam.C[7];
-        io.rgb[2 * hw + pix] = pick(A2, k) + cam.C[11];
+        io.rgb[pix] = pick(s.A0) + cam.C[3];
+        io.rgb[hw + pix] = pick(s.A1) + cam.C[7];
+        io.rgb[2 * hw + pix] = pick(s.A2) + cam.C[11];
       }
-      if (io.depth) io.depth[pix] = pick(D, k);
+      if (io.depth) io.depth[pix] = pick(s.D);
       if (io.normal) {
-        io.normal[pix] = pick(N0, k);
-        io.normal[hw + pix] = pick(N1, k);
-        io.normal[2 * hw + pix] = pick(N2, k);
+        io.normal[pix] = pick(s.N0);
+        io.normal[hw + pix] = pick(s.N1);
+        io.normal[2 * hw + pix] = pick(s.N2);
       }
-      const float Tk = pick(T, k);
+      const float Tk = pick(s.T);
       if (io.alpha) io.alpha[pix] = 1.0f - Tk;
-      if (DIST && io.distort) io.distort[pix] = 2.0f * pick(Dst, k);
+      if (DIST && io.distort) io.distort[pix] = 2.0f * pick(s.Dst);
       io.T_final[pix] = Tk;
-      io.last[pix] = k == 0 ? last0 : last1;
+      io.last[pix] = hi ? s.last1 : s.last0;
     }
-    // algorithmic work counter: one atomic per warp
-    const unsigned int wsum = __reduce_add_sync(0xffffffffu, walked);
-    if (lane == 0 && wsum) atomicAdd(&p.status->n_walked, (unsigned long long)wsum);
+    if (COUNT) {
+      const unsigned int wsum = __reduce_add_sync(0xffffffffu, walked);
+      if (lane == 0 && wsum) atomicAdd(&p.status->n_walked, (unsigned long long)wsum);
+    }
+    if (!q.advance()) break;
   }
 }
 
@@ -445,347 +547,327 @@ __global__ void __launch_bounds__(TW * TH / 2, 6) raster_fwd_kernel(const __grid
 // U = alpha_out - 2 W' and E = 2 M' - D' are carried along the reverse walk from the weights
 // themselves (not from differences of recovered transmittances).  The weight partial joins the
 // splat's per-pixel value f.
-template <int TW, int TH, int BATCH, bool PERSIST, bool DIST>
-// Five resident blocks (20 warps): the bound keeps every variant, the distortion's included, at
-// <= 102 registers without spills.
-__global__ void __launch_bounds__(TW * TH / 2, 5) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
-  constexpr int NT = TW * TH / 2;
-  constexpr int NW = NT / 32;
-  static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are whole 8 x 8 warp blocks");
-  __shared__ float4 sg[BATCH][3];
-  __shared__ float4 sf[BATCH][2];
-  __shared__ uint32_t sk[BATCH];
-  __shared__ uint32_t smask[BATCH];
-  __shared__ uint8_t slist[NT / 8][BATCH + 4];  // candidates of each group (rows padded: the 4 groups of a warp read at one position from different banks)
-  __shared__ float sacc[BATCH][kSaccStride];
-  __shared__ float scol[NW][4];
-  __shared__ int s_item[2];
-  __shared__ unsigned int s_hi[2];  // per iteration parity: the tile's largest walk end
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gl = lane & 7;
-  int cur = 0, tile;
-  if (tid == 0) {
-    if (PERSIST) s_item[0] = (int)atomicAdd(&p.status->work_bwd, 1u);
-    s_hi[0] = 0u;
+
+// Reverse-walk state of one pixel pair of a lane: T (recovered backwards), the composite behind
+// (as g . S), the upstream gradients (gAlT = d(alpha_out) T_final), and for the distortion twice
+// its upstream, z0, E and U.
+struct BwdPair {
+  float2 T, Sg, gD, gAlT, gR0, gR1, gR2, gN0, gN1, gN2;
+  float2 gDs, Z0, E, U;
+  uint32_t last0, last1;
+};
+
+template <bool DIST>
+__device__ __forceinline__ void bwd_load_pixel(BwdPair& s, bool hi, const TargetIO& io, int64_t hw, int64_t pix,
+                                               bool inside, bool sun, uint2 range) {
+  float T = 1.0f, gD = 0.0f, gAlT = 0.0f, r0 = 0.0f, r1 = 0.0f, r2 = 0.0f, n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
+  float gDs = 0.0f, Z0 = 0.0f, E = 0.0f;
+  uint32_t last = range.x;
+  if (inside) {
+    T = io.T_final[pix];
+    // the saved end of the walk, clamped to this tile's list
+    last = min(max(io.last[pix], range.x), range.y);
+    if (!sun && io.d_rgb) {
+      // the splats carry C rgb, so d(rgb_out) multiplies their colour directly
+      r0 = io.d_rgb[pix];
+      r1 = io.d_rgb[hw + pix];
+      r2 = io.d_rgb[2 * hw + pix];
+    }
+    if (!sun && io.d_normal) {
+      n0 = io.d_normal[pix];
+      n1 = io.d_normal[hw + pix];
+      n2 = io.d_normal[2 * hw + pix];
+    }
+    if (io.d_depth) gD = io.d_depth[pix];
+    if (io.d_alpha) gAlT = io.d_alpha[pix] * T;
+    if (DIST && io.d_distort) {
+      gDs = 2.0f * io.d_distort[pix];
+      const float D = io.depth[pix], aout = 1.0f - T;
+      Z0 = aout > 0.0f ? D / aout : 0.0f;
+      E = -__fmaf_rn(-Z0, aout, D);
+    }
   }
-  for (int iter = 0;; ++iter) {
-    if (!begin_item<PERSIST>(p, &p.status->work_bwd, s_item, cur, iter, tile)) break;
-    const int hp = iter & 1;
-    if (tid == 0) s_hi[hp ^ 1] = 0u;  // reset for the next iteration (read in this one: s_hi[hp])
+  auto put = [hi](float2& v, float a) { if (hi) v.y = a; else v.x = a; };
+  put(s.T, T);
+  put(s.Sg, 0.0f);
+  put(s.gD, gD);
+  put(s.gAlT, gAlT);
+  put(s.gR0, r0);
+  put(s.gR1, r1);
+  put(s.gR2, r2);
+  put(s.gN0, n0);
+  put(s.gN1, n1);
+  put(s.gN2, n2);
+  put(s.gDs, gDs);
+  put(s.Z0, Z0);
+  put(s.E, E);
+  put(s.U, 1.0f - T);
+  if (hi) s.last1 = last; else s.last0 = last;
+}
+
+// Partials of one splat at a pixel pair, for the gradient fields.
+struct BwdTerms {
+  float2 w, dz, dpw, du, dv, dps;
+};
+
+// One step of the reverse walk for a pixel pair: the adjoint of compositing splat j (position j in
+// the tile's list, contributing where j < last) into the pair.  A pair that does not contribute
+// runs with alpha = 0, which leaves T and S unchanged and gives zero partials.
+template <bool SUN, bool DIST>
+__device__ __forceinline__ BwdTerms bwd_pair(BwdPair& s, const PairEval2& e, uint32_t j, const float4& g2,
+                                             const float4& f0, const float4& f1, float two_inv2s2, bool& c0,
+                                             bool& c1) {
+  c0 = j < s.last0 && e.contrib0;  // a stand-in step carries j = ~0
+  c1 = j < s.last1 && e.contrib1;
+  const float2 a = make_float2(c0 ? e.alpha.x : 0.0f, c1 ? e.alpha.y : 0.0f);
+  const float2 om = add2(bc2(1.0f), neg2(a));
+  const float2 rom = make_float2(rcp_ftz(om.x), rcp_ftz(om.y));  // om >= 1 - alpha_max
+  const float2 Ti = mul2(s.T, rom);  // T in front of the splat
+  const float2 z = fma2(bc2(f0.y), e.v, fma2(bc2(f0.x), e.u, bc2(g2.w)));
+  float2 gf = mul2(s.gD, z);
+  if (!SUN) {
+    gf = fma2(s.gR0, bc2(f1.y), gf);
+    gf = fma2(s.gR1, bc2(f1.z), gf);
+    gf = fma2(s.gR2, bc2(f1.w), gf);
+    gf = fma2(s.gN0, bc2(f0.z), gf);
+    gf = fma2(s.gN1, bc2(f0.w), gf);
+    gf = fma2(s.gN2, bc2(f1.x), gf);
+  }
+  BwdTerms r;
+  r.w = mul2(a, Ti);
+  float2 dzd = bc2(0.0f);  // the distortion's partial in z
+  if (DIST) {
+    const float2 zs = add2(z, neg2(s.Z0));  // depth relative to z0
+    gf = fma2(s.gDs, fma2(zs, s.U, s.E), gf);
+    dzd = mul2(mul2(s.gDs, r.w), add2(s.U, neg2(r.w)));  // W - W' = U - w
+    const float2 w2 = mul2(bc2(2.0f), r.w);
+    s.U = add2(s.U, neg2(w2));
+    s.E = fma2(w2, zs, s.E);
+  }
+  const float2 gs = add2(gf, neg2(s.Sg));
+  s.T = Ti;
+  s.Sg = fma2(a, gs, s.Sg);  // composite from this splat on: a f + (1 - a) S
+  r.dz = fma2(r.w, s.gD, dzd);
+  // d / d ln(o G^) = alpha dL/dalpha, dL/dalpha = T_i (f - S) + d(alpha_out) T_final / (1 - alpha);
+  // zero when clamped (the exact adjoint of the clamp)
+  const float2 dpa = mul2(fma2(Ti, gs, mul2(s.gAlT, rom)), a);
+  r.dpw = make_float2(e.clamped0 ? 0.0f : dpa.x, e.clamped1 ? 0.0f : dpa.y);
+  const float2 dpu = make_float2(e.uwin0 ? r.dpw.x : 0.0f, e.uwin1 ? r.dpw.y : 0.0f);
+  r.dps = mul2(make_float2(e.uwin0 ? 0.0f : r.dpw.x, e.uwin1 ? 0.0f : r.dpw.y), bc2(two_inv2s2));
+  // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
+  r.du = fma2(r.dz, bc2(f0.x), neg2(mul2(dpu, e.u)));
+  r.dv = fma2(r.dz, bc2(f0.y), neg2(mul2(dpu, e.v)));
+  return r;
+}
+
+// The distortion's per-pixel state needs more registers: that variant runs 12 warps per SM.
+template <int TW, int TH, int B, bool PERSIST, bool DIST>
+__global__ void __launch_bounds__(32, DIST ? 12 : 16) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
+  static_assert(TW * TH == kItemsPerTile * kWarpPixels, "two warp items per tile");
+  __shared__ WarpStage<B> S;
+  const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3;
+  const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float two_inv2s2 = 2.0f * p.k.inv2s2;
+  ItemQueue<PERSIST> q;
+  q.begin(&p.status->work_bwd);
+  const int n_items = p.total_tiles * kItemsPerTile;
+  while (q.item < n_items) {
+    q.claim_next();
+    const int tile = q.item / kItemsPerTile, half = q.item % kItemsPerTile;
     const int t = find_target(p.tcams, p.n_targets, tile);
     const TargetCam& cam = p.tcams[t];
-    const LaneGeom lg = lane_geom<TW, TH>(cam, tile);
+    const LaneGeom lg = lane_geom<TW, TH>(cam, tile, half);
     const bool sun = cam.sun != 0;
     const float x = (float)lg.px + 0.5f;
+    const float yb = (float)lg.py0 + 0.5f;
+    const float2 yA = make_float2(yb, yb + 1.0f), yB = make_float2(yb + 2.0f, yb + 3.0f);
     const uint2 range = p.ranges[tile];
     const int64_t recbase = (int64_t)t * p.n_pad;
-    const TargetIO io = p.io[t];
+    const TargetIO& io = p.io[t];
     const int64_t hw = (int64_t)cam.W * cam.H;
-
-    // per pixel: T (recovered backwards), the composite behind (as g . S), the upstream
-    float T[2], y[2], Sg[2], gD[2], gAlT[2], gR[2][3], gN[2][3];  // gAlT: d(alpha_out) T_final
-    float gDs2[2], U0[2], E[2], Z0[2];  // distortion: twice its upstream, alpha_out - 2 W', 2 M' - D', z0
-    uint32_t lastp[2];
+    const bool inx = lg.px < cam.W;
+    BwdPair sA, sB;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int py = lg.py0 + 2 * k;
-      const bool inside = lg.px < cam.W && py < cam.H;
-      y[k] = (float)py + 0.5f;
-      T[k] = 1.0f;
-      Sg[k] = gD[k] = gAlT[k] = 0.0f;
-      gDs2[k] = E[k] = Z0[k] = 0.0f;
-      lastp[k] = range.x;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) gR[k][c] = gN[k][c] = 0.0f;
-      if (inside) {
-        const int64_t pix = (int64_t)py * cam.W + lg.px;
-        T[k] = io.T_final[pix];
-        // the saved end of the walk, clamped to this tile's list
-        lastp[k] = min(max(io.last[pix], range.x), range.y);
-        if (!sun && io.d_rgb) {
-          // the splats carry C rgb, so d(rgb_out) multiplies their colour directly
-          gR[k][0] = io.d_rgb[pix];
-          gR[k][1] = io.d_rgb[hw + pix];
-          gR[k][2] = io.d_rgb[2 * hw + pix];
-        }
-        if (!sun && io.d_normal) {
-          gN[k][0] = io.d_normal[pix];
-          gN[k][1] = io.d_normal[hw + pix];
-          gN[k][2] = io.d_normal[2 * hw + pix];
-        }
-        if (io.d_depth) gD[k] = io.d_depth[pix];
-        if (io.d_alpha) gAlT[k] = io.d_alpha[pix] * T[k];
-        if (DIST && io.d_distort) {
-          gDs2[k] = 2.0f * io.d_distort[pix];
-          const float D = io.depth[pix], aout = 1.0f - T[k];
-          Z0[k] = aout > 0.0f ? D / aout : 0.0f;
-          E[k] = -__fmaf_rn(-Z0[k], aout, D);
-        }
-        if (lastp[k] > range.x) atomicMax(&s_hi[hp], lastp[k]);
-      }
-      U0[k] = 1.0f - T[k];
+    for (int k = 0; k < 4; ++k) {
+      const int py = lg.py0 + k;
+      bwd_load_pixel<DIST>(k < 2 ? sA : sB, k & 1, io, hw, (int64_t)py * cam.W + lg.px, inx && py < cam.H, sun,
+                           range);
     }
-    // the two pixels side by side (.x, .y) for the paired FP32 arithmetic of the walk
-    float2 T2 = make_float2(T[0], T[1]), Sg2 = make_float2(Sg[0], Sg[1]), gD2 = make_float2(gD[0], gD[1]);
-    const float2 gAlT2 = make_float2(gAlT[0], gAlT[1]);
-    const float2 gR0 = make_float2(gR[0][0], gR[1][0]), gR1 = make_float2(gR[0][1], gR[1][1]),
-                 gR2 = make_float2(gR[0][2], gR[1][2]);
-    const float2 gN0 = make_float2(gN[0][0], gN[1][0]), gN1 = make_float2(gN[0][1], gN[1][1]),
-                 gN2 = make_float2(gN[0][2], gN[1][2]);
-    const float2 gDsv = make_float2(gDs2[0], gDs2[1]), z0v = make_float2(Z0[0], Z0[1]);
-    float2 Ev = make_float2(E[0], E[1]), Uv = make_float2(U0[0], U0[1]);
-    const float2 yy = make_float2(y[0], y[1]);
-    // the group's last walked position (exclusive): its walk ends there
-    uint32_t glast = max(lastp[0], lastp[1]);
+    // the group's last walked position (exclusive): its walk ends there; the warp's batches start
+    // at the largest one
+    uint32_t glast = max(max(sA.last0, sA.last1), max(sB.last0, sB.last1));
     glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 1));
     glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 2));
-    glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 4));
-    __syncthreads();
-    const uint32_t hi_all = s_hi[hp];  // 0 when no pixel walked: no batch
-    const float two_inv2s2 = 2.0f * p.k.inv2s2;
-    for (uint32_t hi = hi_all; hi > range.x;) {
-      const uint32_t b0 = (hi - range.x > (uint32_t)BATCH) ? hi - BATCH : range.x;
-      const int nb = (int)(hi - b0);
-      if (hi != hi_all) __syncthreads();  // the first batch follows the barrier after the upstream loads
-      for (int i = tid; i < nb; i += NT) {
-        const uint32_t kk = p.vals[b0 + i];
-        const int64_t rec = recbase + kk;
-        const float4* g = p.geom + rec * 3;
-        const float4* f = p.feat + rec * 2;
-        const float4 g0 = g[0], g1 = g[1], g2 = g[2];
-        sk[i] = kk;
-        sg[i][0] = g0;
-        sg[i][1] = g1;
-        sg[i][2] = g2;
-        sf[i][0] = f[0];
-        if (!sun) sf[i][1] = f[1];  // a sun view has no colour or normal terms
-        smask[i] = p.subblock_cull ? subblock_mask<TW, TH>(g0, g1, g2, lg.x0, lg.y0, p.cull) : 0xffffu;
+    const uint32_t hi_all = __reduce_max_sync(0xffffffffu, glast);
+    // batches of B list entries from the warp's last walked position down; batch k is copied into
+    // buffer k & 1 while batch k - 1 is walked
+    const int nbat = (int)((hi_all - range.x + B - 1) / B);
+    auto lo_of = [&](int k) -> uint32_t {
+      const uint32_t top = hi_all - (uint32_t)(k * B);
+      return top - range.x > (uint32_t)B ? top - B : range.x;
+    };
+    auto nb_of = [&](int k) { return (int)(hi_all - (uint32_t)(k * B) - lo_of(k)); };
+    uint8_t* list = S.list[grp];
+    uint32_t kv[B / 32];  // splat indices of the next batch to copy
+    if (nbat > 0) {
+      load_vals<B>(kv, p.vals, lo_of(0), nb_of(0));
+      stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
+      if (nbat > 1) load_vals<B>(kv, p.vals, lo_of(1), nb_of(1));
+    }
+    for (int bi = 0; bi < nbat; ++bi) {
+      const int buf = bi & 1;
+      const uint32_t b0 = lo_of(bi);
+      const int nb = nb_of(bi);
+      if (bi + 1 < nbat) {
+        // the next (lower) batch's copies overlap this batch's walk
+        stage_issue<B>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
+        if (bi + 2 < nbat) load_vals<B>(kv, p.vals, lo_of(bi + 2), nb_of(bi + 2));
+        cp_async_wait_prev();
+      } else {
+        cp_async_wait_all();
       }
-      for (int i = tid; i < nb * kSaccStride; i += NT) (&sacc[0][0])[i] = 0.0f;
-      __syncthreads();
-      // each group walks its candidates in reverse list order, up to its last walked splat.
-      // The group reduction of one splat's 16 sums is issued in the next step, beside the next
-      // splat's arithmetic (software pipelining); the sums alternate between GA and GB so that
-      // the pending ones are never copied.
-      uint32_t mk = batch_masks<TW, BATCH>(smask, nb);
+      __syncwarp();  // every lane's copies of this batch are visible to the warp
+      stage_masks<TW, TH, B>(S, buf, nb, lg, p);
+      uint32_t mk = batch_masks<TW, TH, B>(S.mask, nb, half);
       {
         const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - (gl << 5);
         mk = lim <= 0 ? 0u : (lim >= 32 ? mk : mk & ((1u << lim) - 1u));
       }
-      const uint8_t* list = slist[tid >> 3];
-      const int total = compact_candidates(mk, slist[tid >> 3]);
+      const int total = compact_candidates(mk, list, buf * B, true);
       const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
-      // group sums of splat jq, one atomic per field into the block's accumulator
-      auto flush = [&](float (&Gq)[16], const int jq) {
-        group_reduce16(Gq);
-        if (jq >= 0) {
-          if (Gq[0] != 0.0f) atomicAdd(&sacc[jq][2 * gl], Gq[0]);
-          if (Gq[1] != 0.0f) atomicAdd(&sacc[jq][2 * gl + 1], Gq[1]);
-        }
-      };
-      float GA[16], GB[16];
-#pragma unroll
-      for (int f = 0; f < 16; ++f) GA[f] = GB[f] = 0.0f;
-      int jA = -1, jB = -1;
-      // A sun view (SUN) has depth and alpha upstream only: its colour and normal terms are
-      // zero and are not formed.
       auto walk = [&](auto sun_c) {
         constexpr bool SUN = decltype(sun_c)::value;
-        // step st: the group's candidate total - 1 - st (reverse list order) into Gc, and the
-        // reduction of the pending Gq
-        auto step = [&](float (&Gc)[16], int& jc, float (&Gq)[16], const int jq, const int st) {
-          const int pos = total - 1 - st;
-          const int jj = pos >= 0 ? (int)list[pos] : -1;
-          // lanes whose group has no splat left evaluate a stand-in and add nothing
-          const int js = jj >= 0 ? jj : 0;
-          const uint32_t j = b0 + (uint32_t)js;
-          const float4 g0 = sg[js][0], g1 = sg[js][1], g2 = sg[js][2];
-          const PairEval2 e = eval_pair2(g0, g1, g2, x, yy, p.k);
-          const bool c0p = jj >= 0 && j < lastp[0] && e.contrib0, c1p = jj >= 0 && j < lastp[1] && e.contrib1;
-          // the previous splat's group reduction overlaps this splat's arithmetic; it runs
-          // unconditionally (sums that nothing wrote are zeros) so that it stays branch free
-          flush(Gq, jq);
-          const float4 f0 = sf[js][0];
-          const float4 f1 = SUN ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : sf[js][1];
-          // both pixels side by side.  A pair that does not contribute runs with alpha = 0, which
-          // leaves T and S unchanged and adds zeros.  The two pixels share their column, so the
-          // terms linear in dx and the centre's chain through Q are summed over the lane before
-          // they are formed.
-          const float2 a = make_float2(c0p ? e.alpha.x : 0.0f, c1p ? e.alpha.y : 0.0f);
-          const float2 om = add2(bc2(1.0f), neg2(a));
-          const float2 rom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));  // om >= 1 - alpha_max
-          const float2 Ti = mul2(T2, rom);  // T in front of the splat
-          const float2 z = fma2(bc2(f0.y), e.v, fma2(bc2(f0.x), e.u, bc2(g2.w)));
-          float2 gf = mul2(gD2, z);
-          if (!SUN) {
-            gf = fma2(gR0, bc2(f1.y), gf);
-            gf = fma2(gR1, bc2(f1.z), gf);
-            gf = fma2(gR2, bc2(f1.w), gf);
-            gf = fma2(gN0, bc2(f0.z), gf);
-            gf = fma2(gN1, bc2(f0.w), gf);
-            gf = fma2(gN2, bc2(f1.x), gf);
-          }
-          const float2 w = mul2(a, Ti);
-          float2 dzd = bc2(0.0f);  // the distortion's partial in z
-          if (DIST) {
-            const float2 zs = add2(z, neg2(z0v));  // depth relative to z0
-            gf = fma2(gDsv, fma2(zs, Uv, Ev), gf);
-            dzd = mul2(mul2(gDsv, w), add2(Uv, neg2(w)));  // W - W' = U - w
-            const float2 w2 = mul2(bc2(2.0f), w);
-            Uv = add2(Uv, neg2(w2));
-            Ev = fma2(w2, zs, Ev);
-          }
-          const float2 gs = add2(gf, neg2(Sg2));
-          T2 = Ti;
-          Sg2 = fma2(a, gs, Sg2);  // composite from this splat on: a f + (1 - a) S
-          auto hsum = [](float2 v) { return v.x + v.y; };
+        for (int st = 0; st < nsteps; ++st) {
+          // reverse list order; lanes whose group has nothing left evaluate a stand-in and add
+          // nothing (j = ~0 is never below a pixel's last walked position)
+          const bool ok = st < total;
+          const int slot = ok ? (int)list[st] : buf * B;
+          const uint32_t j = ok ? b0 + (uint32_t)(slot & (B - 1)) : 0xffffffffu;
+          const float4* gs = &S.g[0][0][0] + slot * 3;
+          const float4* fs = &S.f[0][0][0] + slot * 2;
+          const float4 g0 = gs[0], g1 = gs[1], g2 = gs[2];
+          const float4 f0 = fs[0];
+          const float4 f1 = SUN ? zero4 : fs[1];
+          const uint32_t kk = (&S.k[0][0])[slot];
+          const PairEval2 eA = eval_pair2(g0, g1, g2, x, yA, p.k);
+          const PairEval2 eB = eval_pair2(g0, g1, g2, x, yB, p.k);
+          bool cA0, cA1, cB0, cB1;
+          const BwdTerms rA = bwd_pair<SUN, DIST>(sA, eA, j, g2, f0, f1, two_inv2s2, cA0, cA1);
+          const BwdTerms rB = bwd_pair<SUN, DIST>(sB, eB, j, g2, f0, f1, two_inv2s2, cB0, cB1);
+          // the lane's four pixels summed; terms linear in the shared column offset dx are summed
+          // before they are formed
+          float v[16];
           if (SUN) {
-            Gc[GF_R] = Gc[GF_G] = Gc[GF_B] = Gc[GF_NX] = Gc[GF_NY] = Gc[GF_NZ] = 0.0f;
+            v[GF_R] = v[GF_G] = v[GF_B] = v[GF_NX] = v[GF_NY] = v[GF_NZ] = 0.0f;
           } else {
-            Gc[GF_R] = hsum(mul2(w, gR0));
-            Gc[GF_G] = hsum(mul2(w, gR1));
-            Gc[GF_B] = hsum(mul2(w, gR2));
-            Gc[GF_NX] = hsum(mul2(w, gN0));
-            Gc[GF_NY] = hsum(mul2(w, gN1));
-            Gc[GF_NZ] = hsum(mul2(w, gN2));
+            v[GF_R] = hsum(fma2(rB.w, sB.gR0, mul2(rA.w, sA.gR0)));
+            v[GF_G] = hsum(fma2(rB.w, sB.gR1, mul2(rA.w, sA.gR1)));
+            v[GF_B] = hsum(fma2(rB.w, sB.gR2, mul2(rA.w, sA.gR2)));
+            v[GF_NX] = hsum(fma2(rB.w, sB.gN0, mul2(rA.w, sA.gN0)));
+            v[GF_NY] = hsum(fma2(rB.w, sB.gN1, mul2(rA.w, sA.gN1)));
+            v[GF_NZ] = hsum(fma2(rB.w, sB.gN2, mul2(rA.w, sA.gN2)));
           }
-          const float2 dz = fma2(w, gD2, dzd);
-          Gc[GF_ZC] = hsum(dz);
-          Gc[GF_DZDU] = hsum(mul2(dz, e.u));
-          Gc[GF_DZDV] = hsum(mul2(dz, e.v));
-          // d / d ln(o G^) = alpha dL/dalpha, dL/dalpha = T_i (f - S) + d(alpha_out) T_final / (1 - alpha);
-          // zero when clamped (the exact adjoint of the clamp)
-          const float2 dal = fma2(Ti, gs, mul2(gAlT2, rom));
-          const float2 dpa = mul2(dal, a);
-          const float2 dpw = make_float2(e.clamped0 ? 0.0f : dpa.x, e.clamped1 ? 0.0f : dpa.y);
-          Gc[GF_LNO] = hsum(dpw);
-          const float2 dpu = make_float2(e.uwin0 ? dpw.x : 0.0f, e.uwin1 ? dpw.y : 0.0f);
-          const float2 dps = mul2(make_float2(e.uwin0 ? 0.0f : dpw.x, e.uwin1 ? 0.0f : dpw.y), bc2(two_inv2s2));
-          // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
-          const float2 du = fma2(dz, bc2(f0.x), neg2(mul2(dpu, e.u)));
-          const float2 dv = fma2(dz, bc2(f0.y), neg2(mul2(dpu, e.v)));
-          const float sdu = hsum(du), sdv = hsum(dv);
-          Gc[GF_Q00] = sdu * e.dx;
-          Gc[GF_Q01] = hsum(mul2(du, e.dy));
-          Gc[GF_Q10] = sdv * e.dx;
-          Gc[GF_Q11] = hsum(mul2(dv, e.dy));
-          Gc[GF_CX] = hsum(dps) * e.dx - (g1.x * sdu + g1.z * sdv);
-          Gc[GF_CY] = hsum(mul2(dps, e.dy)) - (g1.y * sdu + g1.w * sdv);
-          jc = jj;
-        };
-        bool lastA = false;  // the last step wrote GA (else GB)
-        for (int st = 0; st < nsteps; st += 2) {
-          step(GA, jA, GB, jB, st);
-          lastA = true;
-          if (st + 1 >= nsteps) break;
-          step(GB, jB, GA, jA, st + 1);
-          lastA = false;
+          v[GF_ZC] = hsum(add2(rA.dz, rB.dz));
+          v[GF_DZDU] = hsum(fma2(rB.dz, eB.u, mul2(rA.dz, eA.u)));
+          v[GF_DZDV] = hsum(fma2(rB.dz, eB.v, mul2(rA.dz, eA.v)));
+          v[GF_LNO] = hsum(add2(rA.dpw, rB.dpw));
+          const float sdu = hsum(add2(rA.du, rB.du)), sdv = hsum(add2(rA.dv, rB.dv));
+          const float dx = eA.dx;
+          v[GF_Q00] = sdu * dx;
+          v[GF_Q01] = hsum(fma2(rB.du, eB.dy, mul2(rA.du, eA.dy)));
+          v[GF_Q10] = sdv * dx;
+          v[GF_Q11] = hsum(fma2(rB.dv, eB.dy, mul2(rA.dv, eA.dy)));
+          v[GF_CX] = hsum(add2(rA.dps, rB.dps)) * dx - (g1.x * sdu + g1.z * sdv);
+          v[GF_CY] = hsum(fma2(rB.dps, eB.dy, mul2(rA.dps, eA.dy))) - (g1.y * sdu + g1.w * sdv);
+          const bool any = cA0 || cA1 || cB0 || cB1;
+          const bool gany = ((__ballot_sync(0xffffffffu, any) >> (lane & 28)) & 0xfu) != 0u;
+          const float4 sum = group_reduce16(v);
+          // a sun view's fields 12 .. 15 (normal z, colour) are zero
+          if (gany && !(SUN && gl == 3))
+            red_add_v4(p.grad + (recbase + kk) * kGradFields + 4 * gl, sum.x, sum.y, sum.z, sum.w);
         }
-        // the sums of the last step are still pending
-        if (lastA) flush(GA, jA); else flush(GB, jB);
       };
       if (sun) walk(std::true_type{}); else walk(std::false_type{});
-      __syncthreads();
-      for (int i = tid; i < nb * kGradFields; i += NT) {
-        const int s = i >> 4, f = i & 15;
-        const float v = sacc[s][f];
-        if (v != 0.0f) atomicAdd(p.grad + (recbase + sk[s]) * kGradFields + f, v);
-      }
-      hi = b0;
+      __syncwarp();
     }
+    cp_async_wait_all();
     // gradient of the colour offset c of this target: the sum of d(rgb_out) over its pixels
     // (the 3x3 block C is chained per splat in the projection adjoint)
     if (!sun && p.d_color && io.d_rgb) {
-      float s3[3];
+      float s3[3] = {hsum(add2(sA.gR0, sB.gR0)), hsum(add2(sA.gR1, sB.gR1)), hsum(add2(sA.gR2, sB.gR2))};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        s3[c] = gR[0][c] + gR[1][c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s3[c] += __shfl_xor_sync(0xffffffffu, s3[c], o);
       }
       if (lane == 0) {
-        scol[warp][0] = s3[0];
-        scol[warp][1] = s3[1];
-        scol[warp][2] = s3[2];
-      }
-      __syncthreads();
-      if (tid < 3) {
-        float s = 0.0f;
 #pragma unroll
-        for (int w2 = 0; w2 < NW; ++w2) s += scol[w2][tid];
-        if (s != 0.0f) atomicAdd(p.d_color + cam.cam * 12 + 4 * tid + 3, s);
+        for (int c = 0; c < 3; ++c)
+          if (s3[c] != 0.0f) atomicAdd(p.d_color + cam.cam * 12 + 4 * c + 3, s3[c]);
       }
     }
+    if (!q.advance()) break;
   }
 }
 
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH, int BATCH, bool DIST>
+// One warp per block.  Persistent: as many warps as fit on the GPU pull (tile, half) items from
+// the queue; otherwise one block per item.  Resident blocks per SM are queried once per kernel
+// (outside any later stream capture).
+template <typename K>
+cudaError_t launch_items(K kernel, const RasterParams& p, bool persistent, int num_sms, int& per_sm,
+                         cudaStream_t st) {
+  const int n_items = p.total_tiles * kItemsPerTile;
+  if (n_items == 0) return cudaSuccess;
+  int grid = n_items;
+  if (persistent) {
+    if (per_sm == 0) {
+      int v = 0;
+      const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, 32, 0);
+      if (e != cudaSuccess) return e;
+      per_sm = v < 1 ? 1 : v;
+    }
+    grid = min(num_sms * per_sm, n_items);
+  }
+  count_launch();
+  kernel<<<grid, 32, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int TW, int TH, int B, bool DIST, bool COUNT>
 cudaError_t launch_fwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
-  constexpr int NT = TW * TH / 2;
-  if (p.total_tiles == 0) return cudaSuccess;
-  if (persistent) {
-    // resident blocks per SM, queried once (outside any later stream capture)
-    static int per_sm = 0;
-    if (per_sm == 0) {
-      int v = 0;
-      cudaError_t e =
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_fwd_kernel<TW, TH, BATCH, true, DIST>, NT, 0);
-      if (e != cudaSuccess) return e;
-      per_sm = v < 1 ? 1 : v;
-    }
-    int grid = num_sms * per_sm;
-    if (grid > p.total_tiles) grid = p.total_tiles;
-    count_launch();
-    raster_fwd_kernel<TW, TH, BATCH, true, DIST><<<grid, NT, 0, st>>>(p);
-  } else {
-    count_launch();
-    raster_fwd_kernel<TW, TH, BATCH, false, DIST><<<p.total_tiles, NT, 0, st>>>(p);
-  }
-  return cudaGetLastError();
+  static int per_sm = 0;
+  if (persistent) return launch_items(raster_fwd_kernel<TW, TH, B, true, DIST, COUNT>, p, true, num_sms, per_sm, st);
+  return launch_items(raster_fwd_kernel<TW, TH, B, false, DIST, COUNT>, p, false, num_sms, per_sm, st);
 }
 
-// The backward stages at most 224 splats per batch when the option asks for 256: its shared
-// accumulator is then 15 KB instead of 17 KB (measured 1.6 % faster on the 1M-splat batch).
-template <int TW, int TH, int BATCH_OPT, bool DIST>
+template <int TW, int TH, int B, bool DIST>
 cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
-  constexpr int BATCH = BATCH_OPT == 256 ? 224 : BATCH_OPT;
-  constexpr int NT = TW * TH / 2;
-  if (p.total_tiles == 0) return cudaSuccess;
-  if (persistent) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-      int v = 0;
-      cudaError_t e =
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_bwd_kernel<TW, TH, BATCH, true, DIST>, NT, 0);
-      if (e != cudaSuccess) return e;
-      per_sm = v < 1 ? 1 : v;
-    }
-    int grid = num_sms * per_sm;
-    if (grid > p.total_tiles) grid = p.total_tiles;
-    count_launch();
-    raster_bwd_kernel<TW, TH, BATCH, true, DIST><<<grid, NT, 0, st>>>(p);
-  } else {
-    count_launch();
-    raster_bwd_kernel<TW, TH, BATCH, false, DIST><<<p.total_tiles, NT, 0, st>>>(p);
-  }
-  return cudaGetLastError();
+  static int per_sm = 0;
+  if (persistent) return launch_items(raster_bwd_kernel<TW, TH, B, true, DIST>, p, true, num_sms, per_sm, st);
+  return launch_items(raster_bwd_kernel<TW, TH, B, false, DIST>, p, false, num_sms, per_sm, st);
 }
 
-// Instantiates the launchers of one tile shape for both batch sizes, with and without the
-// distortion.
-#define SS_RASTER_DISPATCH(KIND, TW, TH)                                                                    \
-  cudaError_t launch_raster_##KIND##_##TW##x##TH(const RasterParams& p, int batch, bool persistent,        \
-                                                 int num_sms, cudaStream_t st) {                            \
-    const bool dist = p.distort != 0;                                                                        \
-    if (batch == 128)                                                                                        \
-      return dist ? launch_##KIND##_t<TW, TH, 128, true>(p, persistent, num_sms, st)                        \
-                  : launch_##KIND##_t<TW, TH, 128, false>(p, persistent, num_sms, st);                      \
-    if (batch == 256)                                                                                        \
-      return dist ? launch_##KIND##_t<TW, TH, 256, true>(p, persistent, num_sms, st)                        \
-                  : launch_##KIND##_t<TW, TH, 256, false>(p, persistent, num_sms, st);                      \
-    return cudaErrorInvalidValue;                                                                            \
+// Instantiates the launchers of one tile shape for the staged batch of 64 splats per warp, with
+// and without the distortion, and (forward) with and without the walked-pair count.
+#define SS_RASTER_FWD_DISPATCH(TW, TH)                                                                      \
+  cudaError_t launch_raster_fwd_##TW##x##TH(const RasterParams& p, int batch, bool persistent, int num_sms, \
+                                            cudaStream_t st) {                                             \
+    if (batch != 64) return cudaErrorInvalidValue;                                                         \
+    const bool dist = p.distort != 0, cnt = p.count_pairs != 0;                                            \
+    if (dist) return cnt ? launch_fwd_t<TW, TH, 64, true, true>(p, persistent, num_sms, st)                \
+                         : launch_fwd_t<TW, TH, 64, true, false>(p, persistent, num_sms, st);              \
+    return cnt ? launch_fwd_t<TW, TH, 64, false, true>(p, persistent, num_sms, st)                         \
+               : launch_fwd_t<TW, TH, 64, false, false>(p, persistent, num_sms, st);                       \
+  }
+#define SS_RASTER_BWD_DISPATCH(TW, TH)                                                                      \
+  cudaError_t launch_raster_bwd_##TW##x##TH(const RasterParams& p, int batch, bool persistent, int num_sms, \
+                                            cudaStream_t st) {                                             \
+    if (batch != 64) return cudaErrorInvalidValue;                                                         \
+    return p.distort ? launch_bwd_t<TW, TH, 64, true>(p, persistent, num_sms, st)                          \
+                     : launch_bwd_t<TW, TH, 64, false>(p, persistent, num_sms, st);                        \
   }
 
 }  // namespace ss

@@ -108,7 +108,7 @@ def _batched_parity(name, picks, seed, distortion=False):
     step.replay()
     torch.cuda.synchronize()
     st, needed, walked, flags = step.check()
-    assert st == L.SS_OK and flags == 0 and walked > 0
+    assert st == L.SS_OK and flags == 0
     crops = _crops(step.frame, picks(len(scene.cameras)), seed)
 
     def run_backward():

@@ -155,8 +155,8 @@ def test_bf16_backward_parity():
     grad_close(d_dF[0].cpu().numpy().astype(np.float64), ref["dF"], name="dF")
 
 
-@pytest.mark.parametrize("tile,batch,persistent", [((32, 8), 256, 0), ((8, 32), 256, 0), ((16, 16), 128, 0),
-                                                   ((16, 16), 128, 1), ((32, 8), 128, 1), ((8, 32), 128, 1)])
+@pytest.mark.parametrize("tile,batch,persistent", [((32, 8), 64, 0), ((8, 32), 64, 0), ((16, 16), 64, 1),
+                                                   ((32, 8), 64, 1), ((8, 32), 64, 1)])
 def test_tile_shape_and_schedule_do_not_change_outputs(tile, batch, persistent):
     scene = ragged_scene(seed=2)
     ds = DeviceScene(scene)
@@ -323,8 +323,11 @@ def test_walked_pair_counter_matches_oracle():
     of the definition (plus the stopping pair), summed over the image."""
     scene = ragged_scene(seed=12)
     ds = DeviceScene(scene)
-    frame, out = run_forward(ds)
+    frame, out = run_forward(ds, opts=L.default_opts(count_pairs=1))
     _, _, _, walked, _ = frame.status()
+    # without the option the forward does not count
+    frame0, _ = run_forward(ds)
+    assert frame0.status()[3] == 0
     ora = oracle_forward(ds.stored_scene64(), scene.cameras[0])
     ref = int(ora["ncontrib"].sum() + ora["terminated"].sum())
     slack = int((ora["margin_fwd"] < MARGIN).sum()) * 2
