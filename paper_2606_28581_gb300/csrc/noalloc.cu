@@ -1,13 +1,14 @@
 // Forward render of one view without any device allocation.
 //
-// For callers that cannot call cudaMalloc: code running inside a CUDA stream capture (where a
-// device allocation would invalidate the capture), host applications whose device memory is
-// reserved once at start-up (a real-time viewer, an inference service under a fixed memory
-// budget), or plug-ins that are handed a stream but no allocator.  The frame's workspace is a
+// For callers that cannot call cudaMalloc: host applications whose device memory is reserved once
+// at start-up (a real-time viewer, an inference service under a fixed memory budget), or plug-ins
+// that are handed a stream but no allocator.  The call synchronises its stream once, to read the
+// view's intersection count.  The frame's workspace is a
 // file-scope static device array of kNoAllocScratchBytes; every GPU that loads this library holds
 // that much memory until the process exits.  Every call shares the array and leaves its contents
 // behind; the calls below clear what has to start at zero (the status block and the per-tile
 // ranges), and calls that overlap on the GPU (two streams, or two threads) race on the array.
+#include <atomic>
 #include <cmath>
 
 #include "kernels.cuh"
@@ -23,17 +24,20 @@ namespace {
 constexpr int kMaxDevices = 64;
 
 // Device address of the scratch array, looked up once per device (with that device current).
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+// Atomic, so that host threads making their first calls at once do not race on the cache (they
+// look up the same address).  The cached address belongs to the device's context of the time:
+// after a cudaDeviceReset the process must not call this entry point again on that device.
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
 
 ss_status scratch_for_current_device(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SS_ERR_CUDA;
-  if (g_scratch_ptr[dev] == nullptr) {
-    void* p = nullptr;
+  void* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (p == nullptr) {
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return SS_ERR_CUDA;
-    g_scratch_ptr[dev] = p;
+    g_scratch_ptr[dev].store(p, std::memory_order_release);
   }
-  *out = g_scratch_ptr[dev];
+  *out = p;
   return SS_OK;
 }
 

@@ -1,6 +1,7 @@
-"""The allocation-free entry point (for callers that cannot call cudaMalloc, e.g. inside a
-stream capture or under a fixed device-memory budget): its forward render must equal the
-workspace path's, call after call, although every call reuses the library's static scratch.
+"""The allocation-free entry point (for callers that cannot call cudaMalloc, e.g. under a device
+memory budget fixed at start-up, or plug-ins given a stream but no allocator): its forward render
+must equal the workspace path's, call after call, although every call reuses the library's
+static scratch.
 Collected last on purpose."""
 import ctypes
 
