@@ -46,7 +46,7 @@ struct Layout {
   TargetStatic tg[kMaxTargets];
 };
 
-int radix_passes(int lo, int hi) { return (hi - lo + 7) / 8; }
+constexpr int kTileDigitBits = 9;  // the tile sort's digit width (the height sort takes 8)
 
 bool finite(float x) { return std::isfinite(x); }
 
@@ -147,10 +147,10 @@ ss_status make_layout(const ss_splats* s, const ss_camera* cams, int32_t n_cams,
   L->key_bits = kb;
   L->hbit_lo = (s->dtype == SS_BF16) ? 16 : 0;
   L->count_scan = plan_scan(L->T * L->n);
-  L->rp_tiles = plan_radix(capacity);
+  L->rp_tiles = plan_radix(capacity, kTileDigitBits);
   L->rp_height = plan_radix(s->n);
-  L->tiles_in_b = radix_passes(0, kb) % 2 == 1;
-  L->height_in_b = radix_passes(L->hbit_lo, 32) % 2 == 1;
+  L->tiles_in_b = radix_pass_count(0, kb, kTileDigitBits) % 2 == 1;
+  L->height_in_b = radix_pass_count(L->hbit_lo, 32, 8) % 2 == 1;
 
   const size_t TN = (size_t)L->T * (size_t)L->n_pad;
   size_t off = 0;
@@ -183,9 +183,10 @@ ss_status make_layout(const ss_splats* s, const ss_camera* cams, int32_t n_cams,
   L->vals_a = take(cap4);
   L->keys_b = take(cap4);
   L->vals_b = take(cap4);
-  int64_t hb = L->rp_tiles.nblocks > L->rp_height.nblocks ? L->rp_tiles.nblocks : L->rp_height.nblocks;
-  L->hist = take((size_t)hb * 256 * 4);
-  L->hist_off = take((size_t)hb * 256 * 4);
+  const int64_t hb_t = L->rp_tiles.nblocks << kTileDigitBits, hb_h = L->rp_height.nblocks << 8;
+  const int64_t hb = hb_t > hb_h ? hb_t : hb_h;  // histogram entries of the larger sort
+  L->hist = take((size_t)hb * 4);
+  L->hist_off = take((size_t)hb * 4);
   L->ranges = take((size_t)tiles * 8);
   L->total = off;
   return SS_OK;

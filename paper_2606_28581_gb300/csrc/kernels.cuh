@@ -115,13 +115,16 @@ cudaError_t exclusive_scan_u32_u64(const uint32_t* in, unsigned long long* out, 
 
 struct RadixPlan {
   int64_t capacity;     // max elements
-  int64_t nblocks;      // tiles of kRadixTile
-  ScanPlan hist_scan;   // over 256 * nblocks histogram entries
+  int digit_bits;       // 8 or 9
+  int64_t nblocks;      // blocks of radix_tile(digit_bits) elements
+  ScanPlan hist_scan;   // over 2^digit_bits * nblocks histogram entries
 };
 constexpr int kRadixThreads = 256;
 constexpr int kRadixItems = 16;
 constexpr int kRadixTile = kRadixThreads * kRadixItems;
-RadixPlan plan_radix(int64_t capacity);
+int radix_tile(int digit_bits);
+int radix_pass_count(int bit_lo, int bit_hi, int digit_bits);
+RadixPlan plan_radix(int64_t capacity, int digit_bits = 8);
 // Stable LSD radix sort of (key, value) pairs on key bits [bit_lo, bit_hi).  The element
 // count is n_host, or *n_dev when n_dev is not null (device-resident count).  Returns in
 // *in_b whether the sorted result ended in the b buffers.

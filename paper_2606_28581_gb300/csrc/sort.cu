@@ -4,9 +4,10 @@
 // which is the same for every view, so one stable sort of the splats by height (descending,
 // ties by index) serves all targets.  Every (target, splat, tile) overlap is then emitted in
 // that order and stably sorted by the global tile id: within a tile the list stays front to
-// back.  Both sorts are a hand-written stable LSD radix sort (8-bit digits, per-block digit
-// histograms, a device-wide exclusive scan, and a stable scatter that ranks equal digits with
-// warp match masks in element order).
+// back.  Both sorts are a hand-written stable LSD radix sort (per-block digit histograms, a
+// device-wide exclusive scan, and a stable scatter that ranks equal digits with warp match masks
+// in element order); the height sort takes 8-bit digits, the tile sort 9-bit digits, so that
+// the tile ids of up to 2^18 tiles take two passes.
 #include "kernels.cuh"
 
 namespace ss {
@@ -163,56 +164,62 @@ __device__ __forceinline__ int64_t radix_count(int64_t n_host, const uint32_t* n
   return n_dev ? (int64_t)(*n_dev) : n_host;
 }
 
+// Digit histograms of one block's tile, RB-bit digits.
+template <int RB, int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(const uint32_t* keys, int64_t n_host,
                                                                        const uint32_t* n_dev, int shift,
                                                                        uint32_t mask, uint32_t* hist,
                                                                        int64_t nblocks) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
+  constexpr int NB = 1 << RB, TILE = kRadixThreads * ITEMS;
+  __shared__ uint32_t h[NB];
+  for (int d = threadIdx.x; d < NB; d += kRadixThreads) h[d] = 0;
   __syncthreads();
   const int64_t n = radix_count(n_host, n_dev);
-  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  const int64_t base = (int64_t)blockIdx.x * TILE;
   if (base < n) {
 #pragma unroll 4
-    for (int i = 0; i < kRadixItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
       const int64_t idx = base + (int64_t)i * kRadixThreads + threadIdx.x;
       if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & mask], 1u);
     }
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+  for (int d = threadIdx.x; d < NB; d += kRadixThreads) hist[(int64_t)d * nblocks + blockIdx.x] = h[d];
 }
 
 // Stable scatter of one block's tile: ranks within the block (warps own consecutive
 // sub-chunks, equal digits ranked in element order with warp match masks), the tile reordered
 // by digit in shared memory, then written out in runs that are contiguous in the output.
+template <int RB, int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n_host, const uint32_t* n_dev, int shift, uint32_t mask,
     const uint32_t* hist_off, int64_t nblocks) {
   constexpr int kWarps = kRadixThreads / 32;
-  __shared__ uint32_t whist[kWarps][256];
-  __shared__ uint32_t dbase[256];   // output position of the block's first element of each digit
-  __shared__ uint32_t dstart[256];  // block-local position of the first element of each digit
-  __shared__ uint32_t sk[kRadixTile], sv[kRadixTile];
+  constexpr int NB = 1 << RB, TILE = kRadixThreads * ITEMS, DPT = NB / kRadixThreads;  // digits per thread
+  static_assert(NB % kRadixThreads == 0, "whole digits per thread");
+  __shared__ uint32_t whist[kWarps][NB];
+  __shared__ uint32_t dbase[NB];   // output position of the block's first element of each digit
+  __shared__ uint32_t dstart[NB];  // block-local position of the first element of each digit
+  __shared__ uint32_t sk[TILE], sv[TILE];
   const int64_t n = radix_count(n_host, n_dev);
-  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  const int64_t base = (int64_t)blockIdx.x * TILE;
   if (base >= n) return;
-  const int count = (int)min((int64_t)kRadixTile, n - base);
+  const int count = (int)min((int64_t)TILE, n - base);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kWarps * 256; i += kRadixThreads) (&whist[0][0])[i] = 0;
-  dbase[threadIdx.x] = hist_off[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  for (int i = threadIdx.x; i < kWarps * NB; i += kRadixThreads) (&whist[0][0])[i] = 0;
+  for (int d = threadIdx.x; d < NB; d += kRadixThreads) dbase[d] = hist_off[(int64_t)d * nblocks + blockIdx.x];
   __syncthreads();
   const uint32_t lt = (1u << lane) - 1u;
-  const int wbase = warp * (kRadixItems * 32);
-  uint32_t k[kRadixItems], v[kRadixItems], rk[kRadixItems];
+  const int wbase = warp * (ITEMS * 32);
+  uint32_t k[ITEMS], v[ITEMS], rk[ITEMS];
 #pragma unroll
-  for (int i = 0; i < kRadixItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int idx = wbase + i * 32 + lane;
     const bool valid = idx < count;
     k[i] = valid ? keys_in[base + idx] : 0u;
     v[i] = valid ? vals_in[base + idx] : 0u;
-    const uint32_t d = valid ? ((k[i] >> shift) & mask) : 256u;
+    const uint32_t d = valid ? ((k[i] >> shift) & mask) : (uint32_t)NB;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
     if (valid) before = whist[warp][d];
@@ -223,20 +230,33 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
   }
   __syncthreads();
   {
-    // per digit: exclusive scan of the warps' counts, then over the digits
-    uint32_t run = 0;
+    // per digit: exclusive scan of the warps' counts; then over the digits (each thread owns
+    // DPT consecutive digits)
+    uint32_t tsum = 0, dsum[DPT];
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const uint32_t c = whist[w][threadIdx.x];
-      whist[w][threadIdx.x] = run;
-      run += c;
+    for (int q = 0; q < DPT; ++q) {
+      const int d = threadIdx.x * DPT + q;
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = whist[w][d];
+        whist[w][d] = run;
+        run += c;
+      }
+      dsum[q] = run;
+      tsum += run;
     }
     unsigned long long tot;
-    dstart[threadIdx.x] = (uint32_t)block_exclusive_scan((unsigned long long)run, &tot);
+    uint32_t pre = (uint32_t)block_exclusive_scan((unsigned long long)tsum, &tot);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      dstart[threadIdx.x * DPT + q] = pre;
+      pre += dsum[q];
+    }
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < kRadixItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int idx = wbase + i * 32 + lane;
     if (idx < count) {
       const uint32_t d = (k[i] >> shift) & mask;
@@ -255,37 +275,61 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
   }
 }
 
-RadixPlan plan_radix(int64_t capacity) {
+// Elements per block for a digit width: 8-bit digits take 16 per thread, 9-bit digits 12 (their
+// 512-bucket rank tables leave less shared memory for the tile).
+int radix_tile(int digit_bits) { return kRadixThreads * (digit_bits == 9 ? 12 : kRadixItems); }
+
+int radix_pass_count(int bit_lo, int bit_hi, int digit_bits) {
+  return (bit_hi - bit_lo + digit_bits - 1) / digit_bits;
+}
+
+RadixPlan plan_radix(int64_t capacity, int digit_bits) {
   RadixPlan p{};
   p.capacity = capacity;
-  p.nblocks = (capacity + kRadixTile - 1) / kRadixTile;
+  p.digit_bits = digit_bits;
+  p.nblocks = (capacity + radix_tile(digit_bits) - 1) / radix_tile(digit_bits);
   if (p.nblocks < 1) p.nblocks = 1;
-  p.hist_scan = plan_scan(256 * p.nblocks);
+  p.hist_scan = plan_scan((int64_t)(1 << digit_bits) * p.nblocks);
   return p;
 }
+
+namespace {
+template <int RB, int ITEMS>
+cudaError_t radix_pass(const uint32_t* ki, const uint32_t* vi, uint32_t* ko, uint32_t* vo, int64_t n_host,
+                       const uint32_t* n_dev, int shift, uint32_t mask, uint32_t* hist, uint32_t* hist_off,
+                       unsigned long long* scan_scratch, const ScanPlan& hs, int64_t nblocks, cudaStream_t st) {
+  count_launch();
+  radix_upsweep_kernel<RB, ITEMS><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, n_host, n_dev, shift, mask,
+                                                                               hist, nblocks);
+  cudaError_t e = exclusive_scan_u32(hist, hist_off, (int64_t)(1 << RB) * nblocks, scan_scratch, hs,
+                                     scan_scratch + hs.scratch_elems - 1, st);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  radix_downsweep_kernel<RB, ITEMS><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n_host, n_dev,
+                                                                                 shift, mask, hist_off, nblocks);
+  return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
                              int64_t n_host, const uint32_t* n_dev, int bit_lo, int bit_hi,
                              uint32_t* hist, uint32_t* hist_off, unsigned long long* scan_scratch,
                              const RadixPlan& plan, bool* in_b, cudaStream_t st) {
   *in_b = false;
-  const int64_t nblocks = n_dev ? plan.nblocks : (n_host + kRadixTile - 1) / kRadixTile;
+  const int db = plan.digit_bits;
+  const int64_t tile = radix_tile(db);
+  const int64_t nblocks = n_dev ? plan.nblocks : (n_host + tile - 1) / tile;
   if (nblocks == 0) return cudaSuccess;
-  const ScanPlan hs = n_dev ? plan.hist_scan : plan_scan(256 * nblocks);
+  const ScanPlan hs = n_dev ? plan.hist_scan : plan_scan((int64_t)(1 << db) * nblocks);
   uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
-  for (int shift = bit_lo; shift < bit_hi; shift += 8) {
-    const int bits = (bit_hi - shift) < 8 ? (bit_hi - shift) : 8;
+  for (int shift = bit_lo; shift < bit_hi; shift += db) {
+    const int bits = (bit_hi - shift) < db ? (bit_hi - shift) : db;
     const uint32_t mask = (1u << bits) - 1u;
-    count_launch();
-    radix_upsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, n_host, n_dev, shift, mask, hist,
-                                                                       nblocks);
-    cudaError_t e = exclusive_scan_u32(hist, hist_off, 256 * nblocks, scan_scratch, hs,
-                                       scan_scratch + hs.scratch_elems - 1, st);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    radix_downsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n_host, n_dev, shift,
-                                                                         mask, hist_off, nblocks);
-    e = cudaGetLastError();
+    const cudaError_t e =
+        db == 9 ? radix_pass<9, 12>(ki, vi, ko, vo, n_host, n_dev, shift, mask, hist, hist_off, scan_scratch, hs,
+                                    nblocks, st)
+                : radix_pass<8, kRadixItems>(ki, vi, ko, vo, n_host, n_dev, shift, mask, hist, hist_off,
+                                             scan_scratch, hs, nblocks, st);
     if (e != cudaSuccess) return e;
     uint32_t* t;
     t = ki; ki = ko; ko = t;
