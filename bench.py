@@ -476,6 +476,38 @@ def measure_depth_normal(torch, step, reps: int):
             "bwd_frac": bb / (bms * 1e-3) / 1e9 / peak}
 
 
+def measure_config(torch, name: str, storage_dtype, steps: int, warmup: int = 3):
+    """Another configuration of the same path, timed alone: the workload's main views and sun
+    views as one BatchedStep (two CUDA graphs, persistent launches, 16 x 16 tiles), forward and
+    backward, with CUDA events.  Mpix/s counts main-view pixels per forward+backward step."""
+    import scenegen
+    from paper_2606_28581_gb300 import _lib as L
+    from paper_2606_28581_gb300.batched import BatchedStep
+    from paper_2606_28581_gb300.frame import Frame
+    scene = scenegen.workload(name, seed=0)
+    cams = scene.cameras
+    passes = L.SS_PASS_MAIN | L.SS_PASS_SUN
+    splats = upload_splats(torch, scene, storage_dtype)
+    dF = torch.from_numpy(np.stack([c.dF_xy for c in cams]).astype(np.float32)).cuda()
+    color = torch.from_numpy(np.stack([c.color for c in cams]).astype(np.float32)).cuda()
+    ups = make_upstream(torch, Frame(cams, passes).targets, 4321)
+    step = BatchedStep(cams, splats, scene.n, dF, color, ups, passes=passes, opts=L.default_opts(persistent=1))
+    step.capture()
+    for _ in range(warmup):
+        step.replay()
+    ms = time_loop(torch, step.replay, steps)
+    st = step.check()[0]
+    if st != L.SS_OK:
+        raise RuntimeError(f"{name} step status {L.status_string(st)}")
+    main_px, sun_px = step.main_pixels, step.sun_pixels
+    out = {"workload": WORKLOAD_TEXT[name], "n_splats": scene.n,
+           "storage": "bf16" if storage_dtype == torch.bfloat16 else "fp32", "value": main_px / (ms * 1e-3) / 1e6,
+           "unit": UNIT, "ms_per_step": ms, "steps": steps, "main_pixels": main_px, "sun_pixels": sun_px}
+    del step
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------------------ oracle arm
 def oracle_sample(scene, seconds_target: float, seed: int = 0, parts: bool = False):
     """Time the FP64 oracle (forward + backward) on crops of view 0, growing the crop until
@@ -653,6 +685,15 @@ def run_ours(args, dist):
     dnormal = measure_depth_normal(torch, step, k_steps)
     optimizer = measure_optimizer(torch, scene.n, step.grads, storage, k_steps)
     init = measure_init(torch, 3)
+    # the other configurations of the path: the single 2048^2 view with its shadow pass in FP32
+    # and in BF16 storage, and the small 128^2 view (parity of each against the oracle is checked
+    # by the test suite, not here)
+    single = small = None
+    if args.workload == "batched" and not args.profile:
+        s32 = measure_config(torch, "single", torch.float32, 20)
+        s16 = measure_config(torch, "single", torch.bfloat16, 20)
+        single = {"fp32": s32, "bf16": s16, "bf16_over_fp32": s16["value"] / s32["value"]}
+        small = measure_config(torch, "small", torch.float32, 50)
     distortion = None
     if not args.no_distortion:
         mk_d = lambda u: BatchedStep(cams, splats, scene.n, dF, color, u, passes=passes, opts=opts,
@@ -702,7 +743,7 @@ def run_ours(args, dist):
                 raise RuntimeError(f"plain frame status {L.status_string(stf)}")
         plain = {"value": main_px / (pms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": pms, "steps": p_steps,
                  "storage": "fp32", "launch": f"{len(frames)} sequential single-view call sequences (eager, one "
-                                               "block per tile, 16x16 tiles)"}
+                                               "warp per half tile, 16x16 tiles)"}
         del frames, outs, ios, splats32
         torch.cuda.empty_cache()
 
@@ -773,7 +814,7 @@ def run_ours(args, dist):
                 "batched_over_plain": (value / dist.world) / plain["value"] if plain else None,
                 "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
                 "shade": shade, "depth_normal": dnormal, "distortion": distortion, "optimizer": optimizer,
-                "init": init,
+                "init": init, "single": single, "small": small,
                 "steps_per_s": 1e3 / ms_max, "peak_hbm_gb": peak_hbm_gb,
                 "device": {"sms": sms, "arch": arch, "name": torch.cuda.get_device_name()}}
         print(json.dumps(line), flush=True)
