@@ -12,6 +12,7 @@ from oracle import normals as NO
 from paper_2606_28581_gb300 import _lib as L
 from paper_2606_28581_gb300.frame import Frame
 from tests.gpu_util import MARGIN, grad_close, to_np
+from tests.tolerances import CHAIN_GRAD_FLOOR, NORMAL_FWD_TOL, NORMAL_GRAD_FLOOR
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +61,7 @@ def test_depth_normal_matches_oracle_forward_and_backward():
         keep = _alpha_margin(a)
         keeps.append(keep)
         assert ok.mean() > 0.5
-        assert np.abs(to_np(views[c]["normal"]) - N)[:, keep].max() <= 1e-4
+        assert np.abs(to_np(views[c]["normal"]) - N)[:, keep].max() <= NORMAL_FWD_TOL
         dNs.append(rng.normal(size=(3, cam.height, cam.width)) * keep)
         views[c].update(d_normal=torch.from_numpy(dNs[c].astype(np.float32)).cuda(),
                         d_depth=torch.zeros_like(views[c]["depth"]), d_alpha=torch.zeros_like(views[c]["alpha"]))
@@ -72,7 +73,7 @@ def test_depth_normal_matches_oracle_forward_and_backward():
         g = NO.depth_normal_backward(dNs[c], d, a, scene.cameras[c], EPS, dF=to_np(dF[c]))
         grad_close(to_np(views[c]["d_depth"]), g["depth"], name=f"view {c} d_depth")
         grad_close(to_np(views[c]["d_alpha"]), g["alpha"], name=f"view {c} d_alpha")
-        grad_close(to_np(d_dF[c]), g["dF"], name=f"view {c} d_dF", floor=1e-2)
+        grad_close(to_np(d_dF[c]), g["dF"], name=f"view {c} d_dF")
 
 
 def test_normal_consistency_chain_matches_oracle_chain():
@@ -111,9 +112,11 @@ def test_normal_consistency_chain_matches_oracle_chain():
     W_ = torch.from_numpy(w.astype(np.float32)).cuda()
     loss = (W_ * (outs[0]["alpha"] - (outs[0]["normal"] * Ng[0]).sum(0))).sum()
     loss.backward()
+    # the GPU chain works on FP32 rasterized planes; the FP32-sized plane errors alone move the FP64
+    # chain's gradients beyond the default per-element floor (tests/test_fp32_bounds.py)
     for k in ("means", "scales", "quats", "opacity", "rgb"):
-        grad_close(to_np(P[k].grad).reshape(-1), ref[k].reshape(-1), name=k, floor=2e-2)
-    grad_close(to_np(P["dF"].grad[0]), ref["dF"] + gN["dF"], name="dF", floor=2e-2)
+        grad_close(to_np(P[k].grad).reshape(-1), ref[k].reshape(-1), name=k, floor=CHAIN_GRAD_FLOOR)
+    grad_close(to_np(P["dF"].grad[0]), ref["dF"] + gN["dF"], name="dF", floor=CHAIN_GRAD_FLOOR)
 
 
 def test_depth_normal_full_size_views():
@@ -146,7 +149,7 @@ def test_depth_normal_full_size_views():
         d, a = planes[c]
         N, ok = NO.depth_normal(d, a, cam, EPS, dF=to_np(dF[c]))
         assert ok.mean() > 0.8
-        assert np.abs(to_np(views[c]["normal"]) - N).max() <= 1e-4
+        assert np.abs(to_np(views[c]["normal"]) - N).max() <= NORMAL_FWD_TOL
         dN = rng.normal(size=(3, cam.height, cam.width))
         dNs.append(dN.astype(np.float32).astype(np.float64))
         views[c].update(d_normal=f(dNs[c]), d_depth=torch.zeros_like(views[c]["depth"]),
@@ -158,8 +161,8 @@ def test_depth_normal_full_size_views():
         d, a = planes[c]
         g = NO.depth_normal_backward(dNs[c], d, a, cam, EPS, dF=to_np(dF[c]))
         # a pixel's depth gradient sums its four neighbours' contributions, which reach ~2e4 here
-        # and can cancel to ~1: FP32 leaves such a pixel within ~1e-5 of the largest contribution,
-        # so the per-element floor is 1e-2 of the largest value (the global bound stays 1e-3)
-        grad_close(to_np(views[c]["d_depth"]), g["depth"], name=f"view {c} d_depth", floor=1e-2)
-        grad_close(to_np(views[c]["d_alpha"]), g["alpha"], name=f"view {c} d_alpha", floor=1e-2)
-        grad_close(to_np(d_dF[c]), g["dF"], name=f"view {c} d_dF", floor=1e-2)
+        # and can cancel to ~1; one FP32 rounding of z = D / alpha already moves such pixels beyond
+        # the default per-element floor (tests/test_fp32_bounds.py); the global bound stays 1e-3
+        grad_close(to_np(views[c]["d_depth"]), g["depth"], name=f"view {c} d_depth", floor=NORMAL_GRAD_FLOOR)
+        grad_close(to_np(views[c]["d_alpha"]), g["alpha"], name=f"view {c} d_alpha", floor=NORMAL_GRAD_FLOOR)
+        grad_close(to_np(d_dF[c]), g["dF"], name=f"view {c} d_dF")

@@ -13,6 +13,7 @@ from oracle import shade as S
 from paper_2606_28581_gb300 import _lib as L
 from paper_2606_28581_gb300.frame import Frame
 from tests.gpu_util import grad_close, to_np
+from tests.tolerances import CHAIN_GRAD_FLOOR
 
 pytestmark = pytest.mark.gpu
 
@@ -167,11 +168,11 @@ def test_render_and_shade_chain_matches_oracle_chain():
     img = shade(frame, outs, La, P["dF"], opts)
     loss = (img[0]["image"] * torch.from_numpy(wI.astype(np.float32)).cuda()).sum()
     loss.backward()
-    # the GPU chain shades the FP32 rasterizer outputs; through the bilinear occluder sample the
-    # shading's derivative is large at sun-depth discontinuities, so per element the bound's floor
-    # is 2 % of the largest gradient (the per-tensor bound stays 1e-3)
+    # the GPU chain shades the FP32 rasterizer outputs, and the sun-visibility test amplifies their
+    # errors: FP32-sized plane errors alone move the FP64 chain's gradients beyond the default
+    # per-element floor (tests/test_fp32_bounds.py); the per-tensor bound stays 1e-3
     for k in ("means", "scales", "quats", "opacity", "rgb"):
-        grad_close(to_np(P[k].grad).reshape(-1), (gm[k] + gsun[k]).reshape(-1), name=k, floor=2e-2)
-    grad_close(to_np(P["dF"].grad[0]), gm["dF"] + gsun["dF"] + gs["dF"], name="dF", floor=2e-2)
-    grad_close(to_np(P["color"].grad[0]), gm["color"], name="color", floor=2e-2)
-    grad_close(to_np(La.grad[0]), gs["La"], name="La", floor=2e-2)
+        grad_close(to_np(P[k].grad).reshape(-1), (gm[k] + gsun[k]).reshape(-1), name=k, floor=CHAIN_GRAD_FLOOR)
+    grad_close(to_np(P["dF"].grad[0]), gm["dF"] + gsun["dF"] + gs["dF"], name="dF", floor=CHAIN_GRAD_FLOOR)
+    grad_close(to_np(P["color"].grad[0]), gm["color"], name="color", floor=CHAIN_GRAD_FLOOR)
+    grad_close(to_np(La.grad[0]), gs["La"], name="La", floor=CHAIN_GRAD_FLOOR)
