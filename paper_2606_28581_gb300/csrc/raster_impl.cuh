@@ -30,8 +30,9 @@
 
 namespace ss {
 
-constexpr int kWarpPixels = 128;  // pixels of one warp work item
-constexpr int kItemsPerTile = 2;  // every tile shape holds 256 pixels
+constexpr int kWarpPixels = 128;  // pixels of one warp
+constexpr int kTileWarps = 2;     // every tile shape holds 256 pixels: two warps per tile block
+constexpr int kTileThreads = 32 * kTileWarps;
 
 __device__ __forceinline__ int find_target(const TargetCam* tc, int n_targets, int tile) {
   int lo = 0, hi = n_targets - 1;
@@ -122,16 +123,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Shared memory of one warp: two buffers of B staged records (geometry 48 B, features 32 B, the
-// splat index), the sub-block masks of the current batch and each group's candidate list.
+// Shared memory of one tile block: two buffers of B staged records (geometry 48 B, features 32 B,
+// the splat index), the sub-block masks of the current batch and each group's candidate list.
 template <int B>
-struct WarpStage {
+struct TileStage {
   float4 g[2][B][3];
   float4 f[2][B][2];
   uint32_t k[2][B];
   uint32_t mask[B];
-  uint8_t list[8][B + 4];  // per group its candidates' slots (buffer * B + index); rows padded so that
-                           // the groups read at one position from different banks
+  uint8_t list[8 * kTileWarps][B + 4];  // per group its candidates' slots (buffer * B + index); rows
+                                        // padded so that the groups read at one position from
+                                        // different banks
 };
 
 // Pixels of this lane and the tile's origin.  The warp's half of the tile is 16 x 8 (8 x 16 for
@@ -274,13 +276,14 @@ __device__ __forceinline__ int compact_candidates(uint32_t mk, uint8_t* list, in
   return total;
 }
 
-// Splat indices of a batch (lane c of chunk c), loaded one batch ahead of their copies.
+// Splat indices of a batch (thread t holds entries t, t + kTileThreads, ...), loaded one batch
+// ahead of their copies.
 template <int B>
-__device__ __forceinline__ void load_vals(uint32_t (&kv)[B / 32], const uint32_t* vals, uint32_t b0, int nb) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void load_vals(uint32_t (&kv)[B / kTileThreads], const uint32_t* vals, uint32_t b0,
+                                          int nb) {
 #pragma unroll
-  for (int c = 0; c < B / 32; ++c) {
-    const int i = c * 32 + lane;
+  for (int c = 0; c < B / kTileThreads; ++c) {
+    const int i = c * kTileThreads + threadIdx.x;
     kv[c] = i < nb ? __ldg(vals + b0 + i) : 0u;
   }
 }
@@ -288,12 +291,11 @@ __device__ __forceinline__ void load_vals(uint32_t (&kv)[B / 32], const uint32_t
 // Issues the asynchronous copies of a batch's records into buffer `buf` (one commit group).
 // A sun view composites depth alone and needs only the first feature vector.
 template <int B>
-__device__ __forceinline__ void stage_issue(WarpStage<B>& S, int buf, const uint32_t (&kv)[B / 32], int nb,
-                                            const RasterParams& p, int64_t recbase, bool sun) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void stage_issue(TileStage<B>& S, int buf, const uint32_t (&kv)[B / kTileThreads],
+                                            int nb, const RasterParams& p, int64_t recbase, bool sun) {
 #pragma unroll
-  for (int c = 0; c < B / 32; ++c) {
-    const int i = c * 32 + lane;
+  for (int c = 0; c < B / kTileThreads; ++c) {
+    const int i = c * kTileThreads + threadIdx.x;
     if (i < nb) {
       const int64_t rec = recbase + kv[c];
       const float4* g = p.geom + rec * 3;
@@ -309,14 +311,14 @@ __device__ __forceinline__ void stage_issue(WarpStage<B>& S, int buf, const uint
   cp_async_commit();
 }
 
-// Sub-block masks of a landed batch: each lane reads the records it copied itself.
+// Sub-block masks of a landed batch: each thread reads the records it copied itself (before the
+// barrier that publishes copies and masks to the block).
 template <int TW, int TH, int B>
-__device__ __forceinline__ void stage_masks(WarpStage<B>& S, int buf, int nb, const LaneGeom& lg,
+__device__ __forceinline__ void stage_masks(TileStage<B>& S, int buf, int nb, const LaneGeom& lg,
                                             const RasterParams& p) {
-  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int c = 0; c < B / 32; ++c) {
-    const int i = c * 32 + lane;
+  for (int c = 0; c < B / kTileThreads; ++c) {
+    const int i = c * kTileThreads + threadIdx.x;
     if (i < nb)
       S.mask[i] = p.subblock_cull ? subblock_mask<TW, TH>(S.g[buf][i][0], S.g[buf][i][1], S.g[buf][i][2], lg.x0,
                                                           lg.y0, p.cull)
@@ -324,30 +326,36 @@ __device__ __forceinline__ void stage_masks(WarpStage<B>& S, int buf, int nb, co
   }
 }
 
-// Work item of a warp: one per tile half, or the next item of the persistent queue (claimed one
-// item ahead, so the claim's latency overlaps the current item).
+// Work item of a block: one tile per block, or the next tile of the persistent queue, claimed one
+// item ahead by thread 0 so that the claim's latency overlaps the current item.  The barriers
+// around each read of the shared slot order it against thread 0's next claim, and the one that
+// ends an item also frees the staging buffers for the next.
 template <bool PERSIST>
 struct ItemQueue {
   unsigned int* counter;
-  int item, next;
-  __device__ __forceinline__ void begin(unsigned int* c) {
+  int* slot;  // shared
+  int item;
+  __device__ __forceinline__ void begin(unsigned int* c, int* s) {
     counter = c;
+    slot = s;
     if (PERSIST) {
-      int v = 0;
-      if ((threadIdx.x & 31) == 0) v = (int)atomicAdd(counter, 1u);
-      item = __shfl_sync(0xffffffffu, v, 0);
+      if (threadIdx.x == 0) *slot = (int)atomicAdd(counter, 1u);
+      __syncthreads();
+      item = *slot;
+      __syncthreads();
     } else {
       item = blockIdx.x;
     }
-    next = 0;
   }
   __device__ __forceinline__ void claim_next() {
-    if (PERSIST && (threadIdx.x & 31) == 0) next = (int)atomicAdd(counter, 1u);
+    if (PERSIST && threadIdx.x == 0) *slot = (int)atomicAdd(counter, 1u);
   }
-  // false when this warp has no item left
+  // false when this block has no item left
   __device__ __forceinline__ bool advance() {
     if (!PERSIST) return false;
-    item = __shfl_sync(0xffffffffu, next, 0);
+    __syncthreads();
+    item = *slot;
+    __syncthreads();
     return true;
   }
 };
@@ -417,17 +425,17 @@ __device__ __forceinline__ uint32_t composite(FwdPair& s, const PairEval2& e, bo
 // COUNT: the launch also counts the walked pairs (the algorithmic work of the roofline) into the
 // status block; the training step runs without it.
 template <int TW, int TH, int B, bool PERSIST, bool DIST, bool COUNT>
-__global__ void __launch_bounds__(32, 16) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
-  static_assert(TW * TH == kItemsPerTile * kWarpPixels, "two warp items per tile");
-  __shared__ WarpStage<B> S;
-  const int lane = threadIdx.x & 31, grp = lane >> 2;
+__global__ void __launch_bounds__(kTileThreads, 8) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
+  static_assert(TW * TH == kTileWarps * kWarpPixels, "two warps per tile");
+  __shared__ TileStage<B> S;
+  __shared__ int s_item;
+  const int lane = threadIdx.x & 31, grp = lane >> 2, half = threadIdx.x >> 5;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   ItemQueue<PERSIST> q;
-  q.begin(&p.status->work_fwd);
-  const int n_items = p.total_tiles * kItemsPerTile;
-  while (q.item < n_items) {
+  q.begin(&p.status->work_fwd, &s_item);
+  while (q.item < p.total_tiles) {
     q.claim_next();
-    const int tile = q.item / kItemsPerTile, half = q.item % kItemsPerTile;
+    const int tile = q.item;
     const int t = find_target(p.tcams, p.n_targets, tile);
     const TargetCam& cam = p.tcams[t];
     const LaneGeom lg = lane_geom<TW, TH>(cam, tile, half);
@@ -446,8 +454,8 @@ __global__ void __launch_bounds__(32, 16) raster_fwd_kernel(const __grid_constan
     // k - 1 is walked
     const int n = (int)(range.y - range.x), nbat = (n + B - 1) / B;
     auto nb_of = [&](int k) { return min(n - k * B, B); };
-    uint8_t* list = S.list[grp];
-    uint32_t kv[B / 32];  // splat indices of the next batch to copy
+    uint8_t* list = S.list[half * 8 + grp];
+    uint32_t kv[B / kTileThreads];  // splat indices of the next batch to copy
     if (nbat > 0) {
       load_vals<B>(kv, p.vals, range.x, nb_of(0));
       stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
@@ -458,7 +466,8 @@ __global__ void __launch_bounds__(32, 16) raster_fwd_kernel(const __grid_constan
       const uint32_t b0 = range.x + (uint32_t)(bi * B);
       const int nb = nb_of(bi);
       const bool all_done = sA.done0 && sA.done1 && sB.done0 && sB.done1;
-      if (__all_sync(0xffffffffu, all_done)) break;
+      // both warps are done with the previous batch's buffer (refilled next), or with the tile
+      if (__syncthreads_and(all_done)) break;
       if (bi + 1 < nbat) {
         // the next batch's copies overlap this batch's walk
         stage_issue<B>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
@@ -467,8 +476,8 @@ __global__ void __launch_bounds__(32, 16) raster_fwd_kernel(const __grid_constan
       } else {
         cp_async_wait_all();
       }
-      __syncwarp();  // every lane's copies of this batch are visible to the warp
       stage_masks<TW, TH, B>(S, buf, nb, lg, p);
+      __syncthreads();  // every thread's copies and masks of this batch are visible to the block
       uint32_t mk = batch_masks<TW, TH, B>(S.mask, nb, half);
       // a group whose 16 pixels have all stopped walks nothing
       if (((__ballot_sync(0xffffffffu, all_done) >> (lane & 28)) & 0xfu) == 0xfu) mk = 0u;
@@ -494,7 +503,6 @@ __global__ void __launch_bounds__(32, 16) raster_fwd_kernel(const __grid_constan
         }
       };
       if (sun) walk(std::true_type{}); else walk(std::false_type{});
-      __syncwarp();  // the buffer and the lists are refilled next
     }
     cp_async_wait_all();  // no copy is left in flight when the walk ends early
     const TargetIO& io = p.io[t];
@@ -662,18 +670,19 @@ __device__ __forceinline__ BwdTerms bwd_pair(BwdPair& s, const PairEval2& e, uin
 
 // The distortion's per-pixel state needs more registers: that variant runs 12 warps per SM.
 template <int TW, int TH, int B, bool PERSIST, bool DIST>
-__global__ void __launch_bounds__(32, DIST ? 12 : 16) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
-  static_assert(TW * TH == kItemsPerTile * kWarpPixels, "two warp items per tile");
-  __shared__ WarpStage<B> S;
-  const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3;
+__global__ void __launch_bounds__(kTileThreads, DIST ? 6 : 8) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
+  static_assert(TW * TH == kTileWarps * kWarpPixels, "two warps per tile");
+  __shared__ TileStage<B> S;
+  __shared__ int s_item;
+  __shared__ uint32_t s_hi[kTileWarps];
+  const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3, half = threadIdx.x >> 5;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const float two_inv2s2 = 2.0f * p.k.inv2s2;
   ItemQueue<PERSIST> q;
-  q.begin(&p.status->work_bwd);
-  const int n_items = p.total_tiles * kItemsPerTile;
-  while (q.item < n_items) {
+  q.begin(&p.status->work_bwd, &s_item);
+  while (q.item < p.total_tiles) {
     q.claim_next();
-    const int tile = q.item / kItemsPerTile, half = q.item % kItemsPerTile;
+    const int tile = q.item;
     const int t = find_target(p.tcams, p.n_targets, tile);
     const TargetCam& cam = p.tcams[t];
     const LaneGeom lg = lane_geom<TW, TH>(cam, tile, half);
@@ -698,7 +707,13 @@ __global__ void __launch_bounds__(32, DIST ? 12 : 16) raster_bwd_kernel(const __
     uint32_t glast = max(max(sA.last0, sA.last1), max(sB.last0, sB.last1));
     glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 1));
     glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 2));
-    const uint32_t hi_all = __reduce_max_sync(0xffffffffu, glast);
+    // the tile's largest last walked position: the block's batches start there
+    const uint32_t whi = __reduce_max_sync(0xffffffffu, glast);
+    if (lane == 0) s_hi[half] = whi;
+    __syncthreads();
+    uint32_t hi_all = s_hi[0];
+#pragma unroll
+    for (int w = 1; w < kTileWarps; ++w) hi_all = max(hi_all, s_hi[w]);
     // batches of B list entries from the warp's last walked position down; batch k is copied into
     // buffer k & 1 while batch k - 1 is walked
     const int nbat = (int)((hi_all - range.x + B - 1) / B);
@@ -707,8 +722,8 @@ __global__ void __launch_bounds__(32, DIST ? 12 : 16) raster_bwd_kernel(const __
       return top - range.x > (uint32_t)B ? top - B : range.x;
     };
     auto nb_of = [&](int k) { return (int)(hi_all - (uint32_t)(k * B) - lo_of(k)); };
-    uint8_t* list = S.list[grp];
-    uint32_t kv[B / 32];  // splat indices of the next batch to copy
+    uint8_t* list = S.list[half * 8 + grp];
+    uint32_t kv[B / kTileThreads];  // splat indices of the next batch to copy
     if (nbat > 0) {
       load_vals<B>(kv, p.vals, lo_of(0), nb_of(0));
       stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
@@ -718,6 +733,7 @@ __global__ void __launch_bounds__(32, DIST ? 12 : 16) raster_bwd_kernel(const __
       const int buf = bi & 1;
       const uint32_t b0 = lo_of(bi);
       const int nb = nb_of(bi);
+      if (bi > 0) __syncthreads();  // both warps are done with the buffer refilled next
       if (bi + 1 < nbat) {
         // the next (lower) batch's copies overlap this batch's walk
         stage_issue<B>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
@@ -726,8 +742,8 @@ __global__ void __launch_bounds__(32, DIST ? 12 : 16) raster_bwd_kernel(const __
       } else {
         cp_async_wait_all();
       }
-      __syncwarp();  // every lane's copies of this batch are visible to the warp
       stage_masks<TW, TH, B>(S, buf, nb, lg, p);
+      __syncthreads();  // every thread's copies and masks of this batch are visible to the block
       uint32_t mk = batch_masks<TW, TH, B>(S.mask, nb, half);
       {
         const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - (gl << 5);
@@ -788,7 +804,6 @@ __global__ void __launch_bounds__(32, DIST ? 12 : 16) raster_bwd_kernel(const __
         }
       };
       if (sun) walk(std::true_type{}); else walk(std::false_type{});
-      __syncwarp();
     }
     cp_async_wait_all();
     // gradient of the colour offset c of this target: the sum of d(rgb_out) over its pixels
@@ -813,26 +828,26 @@ __global__ void __launch_bounds__(32, DIST ? 12 : 16) raster_bwd_kernel(const __
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-// One warp per block.  Persistent: as many warps as fit on the GPU pull (tile, half) items from
-// the queue; otherwise one block per item.  Resident blocks per SM are queried once per kernel
+// One two-warp block per tile.  Persistent: as many blocks as fit on the GPU pull tiles from the
+// queue; otherwise one block per tile.  Resident blocks per SM are queried once per kernel
 // (outside any later stream capture).
 template <typename K>
 cudaError_t launch_items(K kernel, const RasterParams& p, bool persistent, int num_sms, int& per_sm,
                          cudaStream_t st) {
-  const int n_items = p.total_tiles * kItemsPerTile;
+  const int n_items = p.total_tiles;
   if (n_items == 0) return cudaSuccess;
   int grid = n_items;
   if (persistent) {
     if (per_sm == 0) {
       int v = 0;
-      const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, 32, 0);
+      const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kTileThreads, 0);
       if (e != cudaSuccess) return e;
       per_sm = v < 1 ? 1 : v;
     }
     grid = min(num_sms * per_sm, n_items);
   }
   count_launch();
-  kernel<<<grid, 32, 0, st>>>(p);
+  kernel<<<grid, kTileThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -850,24 +865,24 @@ cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cu
   return launch_items(raster_bwd_kernel<TW, TH, B, false, DIST>, p, false, num_sms, per_sm, st);
 }
 
-// Instantiates the launchers of one tile shape for the staged batch of 64 splats per warp, with
+// Instantiates the launchers of one tile shape for the staged batch of 128 splats per block, with
 // and without the distortion, and (forward) with and without the walked-pair count.
 #define SS_RASTER_FWD_DISPATCH(TW, TH)                                                                      \
   cudaError_t launch_raster_fwd_##TW##x##TH(const RasterParams& p, int batch, bool persistent, int num_sms, \
                                             cudaStream_t st) {                                             \
-    if (batch != 64) return cudaErrorInvalidValue;                                                         \
+    if (batch != 128) return cudaErrorInvalidValue;                                                         \
     const bool dist = p.distort != 0, cnt = p.count_pairs != 0;                                            \
-    if (dist) return cnt ? launch_fwd_t<TW, TH, 64, true, true>(p, persistent, num_sms, st)                \
-                         : launch_fwd_t<TW, TH, 64, true, false>(p, persistent, num_sms, st);              \
-    return cnt ? launch_fwd_t<TW, TH, 64, false, true>(p, persistent, num_sms, st)                         \
-               : launch_fwd_t<TW, TH, 64, false, false>(p, persistent, num_sms, st);                       \
+    if (dist) return cnt ? launch_fwd_t<TW, TH, 128, true, true>(p, persistent, num_sms, st)                \
+                         : launch_fwd_t<TW, TH, 128, true, false>(p, persistent, num_sms, st);              \
+    return cnt ? launch_fwd_t<TW, TH, 128, false, true>(p, persistent, num_sms, st)                         \
+               : launch_fwd_t<TW, TH, 128, false, false>(p, persistent, num_sms, st);                       \
   }
 #define SS_RASTER_BWD_DISPATCH(TW, TH)                                                                      \
   cudaError_t launch_raster_bwd_##TW##x##TH(const RasterParams& p, int batch, bool persistent, int num_sms, \
                                             cudaStream_t st) {                                             \
-    if (batch != 64) return cudaErrorInvalidValue;                                                         \
-    return p.distort ? launch_bwd_t<TW, TH, 64, true>(p, persistent, num_sms, st)                          \
-                     : launch_bwd_t<TW, TH, 64, false>(p, persistent, num_sms, st);                        \
+    if (batch != 128) return cudaErrorInvalidValue;                                                         \
+    return p.distort ? launch_bwd_t<TW, TH, 128, true>(p, persistent, num_sms, st)                          \
+                     : launch_bwd_t<TW, TH, 128, false>(p, persistent, num_sms, st);                        \
   }
 
 }  // namespace ss
