@@ -55,7 +55,7 @@ ss_status check_opts(const ss_raster_opts* o) {
   const bool shape = (o->tile_w == 16 && o->tile_h == 16) || (o->tile_w == 32 && o->tile_h == 8) ||
                      (o->tile_w == 8 && o->tile_h == 32);
   if (!shape) return SS_ERR_INVALID_ARG;
-  if (o->batch != 128) return SS_ERR_INVALID_ARG;
+  if (o->batch != 256) return SS_ERR_INVALID_ARG;
   if (o->pixels_per_thread != 4) return SS_ERR_INVALID_ARG;
   if (o->count_pairs != 0 && o->count_pairs != 1) return SS_ERR_INVALID_ARG;
   if (o->persistent != 0 && o->persistent != 1) return SS_ERR_INVALID_ARG;
@@ -304,7 +304,7 @@ void ss_default_opts(ss_raster_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->tile_w = 16;
   o->tile_h = 16;
-  o->batch = 128;
+  o->batch = 256;
   o->persistent = 0;
   o->sigma_px = 0.70710678f;
   o->det_eps = 1e-6f;

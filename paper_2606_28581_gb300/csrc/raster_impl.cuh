@@ -1,12 +1,14 @@
 // Forward (K3) and backward (K4) rasterization, Sec. 3.2 Eq. rasterization.
 //
 // Work decomposition.  A screen tile (16 x 16, 32 x 8 or 8 x 32 px) is split into 4 x 4 pixel
-// sub-blocks.  One warp renders 128 pixels of a tile (a 16 x 8 half, or an 8 x 16 half of an
-// 8 x 32 tile): eight sub-blocks, one per group of four lanes.  Lane l of a group owns column l of
-// its sub-block, four pixels, kept as two pairs (rows 0-1 and 2-3) so that the paired FP32
-// instructions of sm_100-family GPUs compute two pixels in one issue.  A warp is a work item of
-// its own: it stages the tile's sorted splat list in its own shared memory, batch by batch, with
-// cp.async copies double-buffered against the walk, and needs no block-wide barrier.
+// sub-blocks.  A block of two warps renders one tile; each warp renders 128 pixels (a 16 x 8
+// half, or an 8 x 16 half of an 8 x 32 tile): eight sub-blocks, one per group of four lanes.
+// Lane l of a group owns column l of its sub-block, four pixels, kept as two pairs (rows 0-1 and
+// 2-3) so that the paired FP32 instructions of sm_100-family GPUs compute two pixels in one issue.
+// The block stages the tile's sorted splat list in shared memory in batches of 256 records copied
+// with cp.async (the next batch's splat indices are loaded while a batch is walked); large
+// batches keep the eight groups of a warp, which walk their own candidate lists in lockstep,
+// evenly loaded.
 //
 // The thread that stages a splat forms the set of the tile's 16 sub-blocks its support can reach
 // (`subblock_mask`); each group walks only the staged splats that reach its sub-block, in list
@@ -123,13 +125,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Shared memory of one tile block: two buffers of B staged records (geometry 48 B, features 32 B,
-// the splat index), the sub-block masks of the current batch and each group's candidate list.
+// Shared memory of one tile block: one or two buffers of B staged records (geometry 48 B, features
+// 32 B, the splat index), the sub-block masks of the current batch and each group's candidates.
+// Batches of up to 128 records are double-buffered (the next batch copied while one is walked);
+// larger ones fit shared memory once.
+template <int B>
+__host__ __device__ constexpr int stage_bufs() { return B > 128 ? 1 : 2; }
+template <int B>
+__host__ __device__ constexpr int mask_chunks() { return (B + 127) / 128; }  // 32-entry chunks held per lane of a group
+
 template <int B>
 struct TileStage {
-  float4 g[2][B][3];
-  float4 f[2][B][2];
-  uint32_t k[2][B];
+  float4 g[stage_bufs<B>()][B][3];
+  float4 f[stage_bufs<B>()][B][2];
+  uint32_t k[stage_bufs<B>()][B];
   uint32_t mask[B];
   uint8_t list[8 * kTileWarps][B + 4];  // per group its candidates' slots (buffer * B + index); rows
                                         // padded so that the groups read at one position from
@@ -228,49 +237,59 @@ __device__ __forceinline__ uint32_t subblock_mask(const float4 g0, const float4 
   return mask;
 }
 
-// Candidate masks of a staged batch: lane gl of a group ends with the group's mask of chunk gl
-// (staged splats [32 gl, 32 gl + 32)).  Holding every chunk at once lets a group walk its
+// Candidate masks of a staged batch: lane gl of a group ends with the group's masks of chunks gl
+// and gl + 4 (staged splats [32 c, 32 c + 32)).  Holding every chunk at once lets a group walk its
 // candidates across chunk boundaries.
 template <int TW, int TH, int B>
-__device__ __forceinline__ uint32_t batch_masks(const uint32_t* smask, int nb, int half) {
-  static_assert(B % 32 == 0 && B / 32 <= 4, "one chunk per lane of a group");
+__device__ __forceinline__ void batch_masks(const uint32_t* smask, int nb, int half, uint32_t (&mk)[mask_chunks<B>()]) {
+  static_assert(B % 32 == 0 && B / 32 <= 4 * mask_chunks<B>(), "chunks per lane of a group");
   const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3;
-  uint32_t mk = 0;
+#pragma unroll
+  for (int q = 0; q < mask_chunks<B>(); ++q) mk[q] = 0u;
 #pragma unroll
   for (int c = 0; c < B / 32; ++c) {
-    if (c * 32 >= nb) break;  // warp-uniform
+    if (c * 32 >= nb) break;  // block-uniform
     const int i = c * 32 + lane;
     const uint32_t v = i < nb ? smask[i] : 0u;
 #pragma unroll
     for (int gg = 0; gg < 8; ++gg) {
       const uint32_t m = __ballot_sync(0xffffffffu, (v >> group_sub<TW, TH>(half, gg)) & 1u);
-      mk = (grp == gg && gl == c) ? m : mk;
+      if (grp == gg && gl == (c & 3)) mk[c >> 2] = m;
     }
   }
-  return mk;
 }
 
-// Writes a group's candidates of a staged batch (the set bits of its chunk masks, lane gl holding
-// chunk gl) to the group's list as shared-memory slots (slot_base + index), in list order or, with
-// `desc`, in reverse list order, and returns their number.  The walk then reads its next splat
-// from the list at a position that depends on the step count alone, so no step waits on the
-// previous one to find its splat.  Every lane of the warp takes part.
-__device__ __forceinline__ int compact_candidates(uint32_t mk, uint8_t* list, int slot_base, bool desc) {
+// Writes a group's candidates of a staged batch (the set bits of its chunk masks) to the group's
+// list as shared-memory slots (slot_base + index), in list order or, with `desc`, in reverse list
+// order, and returns their number.  The walk then reads its next splat from the list at a
+// position that depends on the step count alone, so no step waits on the previous one to find
+// its splat.  Every lane of the warp takes part.
+template <int CH>
+__device__ __forceinline__ int compact_candidates(const uint32_t (&mk)[CH], uint8_t* list, int slot_base,
+                                                  bool desc) {
   const int gl = threadIdx.x & 3;
-  const int c = __popc(mk);
-  int inc = c;
-  int t = __shfl_up_sync(0xffffffffu, inc, 1, 4);
-  if (gl >= 1) inc += t;
-  t = __shfl_up_sync(0xffffffffu, inc, 2, 4);
-  if (gl >= 2) inc += t;
-  const int total = __shfl_sync(0xffffffffu, inc, 3, 4);
-  int k = inc - c;
-  uint32_t mm = mk;
-  while (mm) {
-    const int bit = __ffs(mm) - 1;
-    mm &= mm - 1;
-    list[desc ? total - 1 - k : k] = (uint8_t)(slot_base + gl * 32 + bit);
-    ++k;
+  int before[CH], total = 0;
+#pragma unroll
+  for (int q = 0; q < CH; ++q) {
+    const int c = __popc(mk[q]);
+    int inc = c;
+    int t = __shfl_up_sync(0xffffffffu, inc, 1, 4);
+    if (gl >= 1) inc += t;
+    t = __shfl_up_sync(0xffffffffu, inc, 2, 4);
+    if (gl >= 2) inc += t;
+    before[q] = total + inc - c;
+    total += __shfl_sync(0xffffffffu, inc, 3, 4);
+  }
+#pragma unroll
+  for (int q = 0; q < CH; ++q) {
+    int k = before[q];
+    uint32_t mm = mk[q];
+    while (mm) {
+      const int bit = __ffs(mm) - 1;
+      mm &= mm - 1;
+      list[desc ? total - 1 - k : k] = (uint8_t)(slot_base + (q * 4 + gl) * 32 + bit);
+      ++k;
+    }
   }
   __syncwarp();
   return total;
@@ -427,6 +446,7 @@ __device__ __forceinline__ uint32_t composite(FwdPair& s, const PairEval2& e, bo
 template <int TW, int TH, int B, bool PERSIST, bool DIST, bool COUNT>
 __global__ void __launch_bounds__(kTileThreads, 8) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
   static_assert(TW * TH == kTileWarps * kWarpPixels, "two warps per tile");
+  constexpr int kBufs = stage_bufs<B>();
   __shared__ TileStage<B> S;
   __shared__ int s_item;
   const int lane = threadIdx.x & 31, grp = lane >> 2, half = threadIdx.x >> 5;
@@ -458,17 +478,24 @@ __global__ void __launch_bounds__(kTileThreads, 8) raster_fwd_kernel(const __gri
     uint32_t kv[B / kTileThreads];  // splat indices of the next batch to copy
     if (nbat > 0) {
       load_vals<B>(kv, p.vals, range.x, nb_of(0));
-      stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
-      if (nbat > 1) load_vals<B>(kv, p.vals, range.x + B, nb_of(1));
+      if (kBufs == 2) {
+        stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
+        if (nbat > 1) load_vals<B>(kv, p.vals, range.x + B, nb_of(1));
+      }
     }
     for (int bi = 0; bi < nbat; ++bi) {
-      const int buf = bi & 1;
+      const int buf = kBufs == 2 ? (bi & 1) : 0;
       const uint32_t b0 = range.x + (uint32_t)(bi * B);
       const int nb = nb_of(bi);
       const bool all_done = sA.done0 && sA.done1 && sB.done0 && sB.done1;
       // both warps are done with the previous batch's buffer (refilled next), or with the tile
       if (__syncthreads_and(all_done)) break;
-      if (bi + 1 < nbat) {
+      if (kBufs == 1) {
+        // one buffer: this batch's copies, the next batch's indices loaded meanwhile
+        stage_issue<B>(S, 0, kv, nb, p, recbase, sun);
+        if (bi + 1 < nbat) load_vals<B>(kv, p.vals, range.x + (uint32_t)((bi + 1) * B), nb_of(bi + 1));
+        cp_async_wait_all();
+      } else if (bi + 1 < nbat) {
         // the next batch's copies overlap this batch's walk
         stage_issue<B>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
         if (bi + 2 < nbat) load_vals<B>(kv, p.vals, range.x + (uint32_t)((bi + 2) * B), nb_of(bi + 2));
@@ -478,9 +505,13 @@ __global__ void __launch_bounds__(kTileThreads, 8) raster_fwd_kernel(const __gri
       }
       stage_masks<TW, TH, B>(S, buf, nb, lg, p);
       __syncthreads();  // every thread's copies and masks of this batch are visible to the block
-      uint32_t mk = batch_masks<TW, TH, B>(S.mask, nb, half);
+      uint32_t mk[mask_chunks<B>()];
+      batch_masks<TW, TH, B>(S.mask, nb, half, mk);
       // a group whose 16 pixels have all stopped walks nothing
-      if (((__ballot_sync(0xffffffffu, all_done) >> (lane & 28)) & 0xfu) == 0xfu) mk = 0u;
+      if (((__ballot_sync(0xffffffffu, all_done) >> (lane & 28)) & 0xfu) == 0xfu) {
+#pragma unroll
+        for (int q = 0; q < mask_chunks<B>(); ++q) mk[q] = 0u;
+      }
       const int total = compact_candidates(mk, list, buf * B, false);
       const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
       auto walk = [&](auto sun_c) {
@@ -672,6 +703,7 @@ __device__ __forceinline__ BwdTerms bwd_pair(BwdPair& s, const PairEval2& e, uin
 template <int TW, int TH, int B, bool PERSIST, bool DIST>
 __global__ void __launch_bounds__(kTileThreads, DIST ? 6 : 8) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
   static_assert(TW * TH == kTileWarps * kWarpPixels, "two warps per tile");
+  constexpr int kBufs = stage_bufs<B>();
   __shared__ TileStage<B> S;
   __shared__ int s_item;
   __shared__ uint32_t s_hi[kTileWarps];
@@ -726,15 +758,21 @@ __global__ void __launch_bounds__(kTileThreads, DIST ? 6 : 8) raster_bwd_kernel(
     uint32_t kv[B / kTileThreads];  // splat indices of the next batch to copy
     if (nbat > 0) {
       load_vals<B>(kv, p.vals, lo_of(0), nb_of(0));
-      stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
-      if (nbat > 1) load_vals<B>(kv, p.vals, lo_of(1), nb_of(1));
+      if (kBufs == 2) {
+        stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
+        if (nbat > 1) load_vals<B>(kv, p.vals, lo_of(1), nb_of(1));
+      }
     }
     for (int bi = 0; bi < nbat; ++bi) {
-      const int buf = bi & 1;
+      const int buf = kBufs == 2 ? (bi & 1) : 0;
       const uint32_t b0 = lo_of(bi);
       const int nb = nb_of(bi);
       if (bi > 0) __syncthreads();  // both warps are done with the buffer refilled next
-      if (bi + 1 < nbat) {
+      if (kBufs == 1) {
+        stage_issue<B>(S, 0, kv, nb, p, recbase, sun);
+        if (bi + 1 < nbat) load_vals<B>(kv, p.vals, lo_of(bi + 1), nb_of(bi + 1));
+        cp_async_wait_all();
+      } else if (bi + 1 < nbat) {
         // the next (lower) batch's copies overlap this batch's walk
         stage_issue<B>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
         if (bi + 2 < nbat) load_vals<B>(kv, p.vals, lo_of(bi + 2), nb_of(bi + 2));
@@ -744,10 +782,13 @@ __global__ void __launch_bounds__(kTileThreads, DIST ? 6 : 8) raster_bwd_kernel(
       }
       stage_masks<TW, TH, B>(S, buf, nb, lg, p);
       __syncthreads();  // every thread's copies and masks of this batch are visible to the block
-      uint32_t mk = batch_masks<TW, TH, B>(S.mask, nb, half);
-      {
-        const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - (gl << 5);
-        mk = lim <= 0 ? 0u : (lim >= 32 ? mk : mk & ((1u << lim) - 1u));
+      uint32_t mk[mask_chunks<B>()];
+      batch_masks<TW, TH, B>(S.mask, nb, half, mk);
+#pragma unroll
+      for (int q = 0; q < mask_chunks<B>(); ++q) {
+        // candidates at or after the group's last walked position are not walked
+        const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - ((q * 4 + gl) << 5);
+        mk[q] = lim <= 0 ? 0u : (lim >= 32 ? mk[q] : mk[q] & ((1u << lim) - 1u));
       }
       const int total = compact_candidates(mk, list, buf * B, true);
       const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
@@ -865,24 +906,24 @@ cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cu
   return launch_items(raster_bwd_kernel<TW, TH, B, false, DIST>, p, false, num_sms, per_sm, st);
 }
 
-// Instantiates the launchers of one tile shape for the staged batch of 128 splats per block, with
+// Instantiates the launchers of one tile shape for the staged batch of 256 splats per block, with
 // and without the distortion, and (forward) with and without the walked-pair count.
 #define SS_RASTER_FWD_DISPATCH(TW, TH)                                                                      \
   cudaError_t launch_raster_fwd_##TW##x##TH(const RasterParams& p, int batch, bool persistent, int num_sms, \
                                             cudaStream_t st) {                                             \
-    if (batch != 128) return cudaErrorInvalidValue;                                                         \
+    if (batch != 256) return cudaErrorInvalidValue;                                                         \
     const bool dist = p.distort != 0, cnt = p.count_pairs != 0;                                            \
-    if (dist) return cnt ? launch_fwd_t<TW, TH, 128, true, true>(p, persistent, num_sms, st)                \
-                         : launch_fwd_t<TW, TH, 128, true, false>(p, persistent, num_sms, st);              \
-    return cnt ? launch_fwd_t<TW, TH, 128, false, true>(p, persistent, num_sms, st)                         \
-               : launch_fwd_t<TW, TH, 128, false, false>(p, persistent, num_sms, st);                       \
+    if (dist) return cnt ? launch_fwd_t<TW, TH, 256, true, true>(p, persistent, num_sms, st)                \
+                         : launch_fwd_t<TW, TH, 256, true, false>(p, persistent, num_sms, st);              \
+    return cnt ? launch_fwd_t<TW, TH, 256, false, true>(p, persistent, num_sms, st)                         \
+               : launch_fwd_t<TW, TH, 256, false, false>(p, persistent, num_sms, st);                       \
   }
 #define SS_RASTER_BWD_DISPATCH(TW, TH)                                                                      \
   cudaError_t launch_raster_bwd_##TW##x##TH(const RasterParams& p, int batch, bool persistent, int num_sms, \
                                             cudaStream_t st) {                                             \
-    if (batch != 128) return cudaErrorInvalidValue;                                                         \
-    return p.distort ? launch_bwd_t<TW, TH, 128, true>(p, persistent, num_sms, st)                          \
-                     : launch_bwd_t<TW, TH, 128, false>(p, persistent, num_sms, st);                        \
+    if (batch != 256) return cudaErrorInvalidValue;                                                         \
+    return p.distort ? launch_bwd_t<TW, TH, 256, true>(p, persistent, num_sms, st)                          \
+                     : launch_bwd_t<TW, TH, 256, false>(p, persistent, num_sms, st);                        \
   }
 
 }  // namespace ss

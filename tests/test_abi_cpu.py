@@ -42,7 +42,7 @@ def test_binding_covers_every_declared_symbol():
 def test_default_opts_and_status_strings(lib):
     from paper_2606_28581_gb300 import _lib as L
     o = L.default_opts()
-    assert (o.tile_w, o.tile_h, o.batch, o.persistent, o.pixels_per_thread, o.count_pairs) == (16, 16, 128, 0, 4, 0)
+    assert (o.tile_w, o.tile_h, o.batch, o.persistent, o.pixels_per_thread, o.count_pairs) == (16, 16, 256, 0, 4, 0)
     assert abs(o.alpha_min - 1 / 255) < 1e-9 and abs(o.alpha_max - 0.99) < 1e-7 and abs(o.t_min - 1e-4) < 1e-9
     assert L.status_string(L.SS_ERR_CAPACITY) == "intersection capacity exceeded"
 
@@ -59,7 +59,7 @@ def test_workspace_size_validates_on_the_host(lib):
     size = L.workspace_size(s, cams, 1, L.SS_PASS_MAIN | L.SS_PASS_SUN, o, 1 << 20)
     assert size > 2 * sc.n * (48 + 32 + 8 + 64)
     out = ctypes.c_size_t(0)
-    for bad in (L.default_opts(batch=100), L.default_opts(batch=64), L.default_opts(pixels_per_thread=2),
+    for bad in (L.default_opts(batch=100), L.default_opts(batch=128), L.default_opts(pixels_per_thread=2),
                 L.default_opts(tile_w=32, tile_h=16), L.default_opts(subblock_cull=2),
                 L.default_opts(count_pairs=2)):
         assert lib.ss_workspace_size(ctypes.byref(s), cams, 1, 1, ctypes.byref(bad), 1 << 20,

@@ -39,8 +39,8 @@ def test_distortion_forward_parity(name):
     check_forward(gpu_planes(out, 0), ora, sun=False, tol=FWD_TOL)
 
 
-@pytest.mark.parametrize("tile,batch,persistent", [((16, 16), 128, 1), ((32, 8), 128, 0), ((8, 32), 128, 1),
-                                                   ((16, 16), 128, 0)])
+@pytest.mark.parametrize("tile,batch,persistent", [((16, 16), 256, 1), ((32, 8), 256, 0), ((8, 32), 256, 1),
+                                                   ((16, 16), 256, 0)])
 def test_distortion_tile_shapes_agree(tile, batch, persistent):
     scene = ragged_scene(seed=4)
     ds = DeviceScene(scene)

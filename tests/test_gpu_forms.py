@@ -224,7 +224,7 @@ def test_autotuner_picks_and_caches(tmp_path):
         ups = [dict(depth=torch.ones(t.height, t.width, device="cuda")) for t in frame0.targets]
         splats = dict(means=ds.means, scales=ds.scales, quats=ds.quats, opacity=ds.opacity, rgb=ds.rgb)
         mk = lambda o: BatchedStep(scene.cameras, splats, ds.n, ds.dF, ds.color, ups, opts=o)
-        cands = [(16, 16, 128, 4), (8, 32, 128, 4)]
+        cands = [(16, 16, 256, 4), (8, 32, 256, 4)]
         opts, entry = autotune(mk, "test-key", candidates=cands)
         assert (opts.tile_w, opts.tile_h, opts.batch, opts.pixels_per_thread) in cands and opts.persistent == 1
         assert len(entry["ms"]) == 2

@@ -155,8 +155,8 @@ def test_bf16_backward_parity():
     grad_close(d_dF[0].cpu().numpy().astype(np.float64), ref["dF"], name="dF")
 
 
-@pytest.mark.parametrize("tile,batch,persistent", [((32, 8), 128, 0), ((8, 32), 128, 0), ((16, 16), 128, 1),
-                                                   ((32, 8), 128, 1), ((8, 32), 128, 1)])
+@pytest.mark.parametrize("tile,batch,persistent", [((32, 8), 256, 0), ((8, 32), 256, 0), ((16, 16), 256, 1),
+                                                   ((32, 8), 256, 1), ((8, 32), 256, 1)])
 def test_tile_shape_and_schedule_do_not_change_outputs(tile, batch, persistent):
     scene = ragged_scene(seed=2)
     ds = DeviceScene(scene)
