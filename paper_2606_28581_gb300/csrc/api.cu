@@ -46,7 +46,10 @@ struct Layout {
   TargetStatic tg[kMaxTargets];
 };
 
-constexpr int kTileDigitBits = 9;  // the tile sort's digit width (the height sort takes 8)
+// The tile sort's digit width: 9-bit digits where they save a pass over 8-bit ones (keys of 9 or
+// 17-18 bits), else 8-bit ones, whose passes are cheaper (smaller histograms, larger blocks).
+// The height sort takes 8-bit digits.
+int tile_digit_bits(int key_bits) { return (key_bits + 8) / 9 < (key_bits + 7) / 8 ? 9 : 8; }
 
 bool finite(float x) { return std::isfinite(x); }
 
@@ -147,9 +150,9 @@ ss_status make_layout(const ss_splats* s, const ss_camera* cams, int32_t n_cams,
   L->key_bits = kb;
   L->hbit_lo = (s->dtype == SS_BF16) ? 16 : 0;
   L->count_scan = plan_scan(L->T * L->n);
-  L->rp_tiles = plan_radix(capacity, kTileDigitBits);
+  L->rp_tiles = plan_radix(capacity, tile_digit_bits(kb));
   L->rp_height = plan_radix(s->n);
-  L->tiles_in_b = radix_pass_count(0, kb, kTileDigitBits) % 2 == 1;
+  L->tiles_in_b = radix_pass_count(0, kb, tile_digit_bits(kb)) % 2 == 1;
   L->height_in_b = radix_pass_count(L->hbit_lo, 32, 8) % 2 == 1;
 
   const size_t TN = (size_t)L->T * (size_t)L->n_pad;
@@ -183,7 +186,7 @@ ss_status make_layout(const ss_splats* s, const ss_camera* cams, int32_t n_cams,
   L->vals_a = take(cap4);
   L->keys_b = take(cap4);
   L->vals_b = take(cap4);
-  const int64_t hb_t = L->rp_tiles.nblocks << kTileDigitBits, hb_h = L->rp_height.nblocks << 8;
+  const int64_t hb_t = L->rp_tiles.nblocks << L->rp_tiles.digit_bits, hb_h = L->rp_height.nblocks << 8;
   const int64_t hb = hb_t > hb_h ? hb_t : hb_h;  // histogram entries of the larger sort
   L->hist = take((size_t)hb * 4);
   L->hist_off = take((size_t)hb * 4);

@@ -6,8 +6,8 @@
 // that order and stably sorted by the global tile id: within a tile the list stays front to
 // back.  Both sorts are a hand-written stable LSD radix sort (per-block digit histograms, a
 // device-wide exclusive scan, and a stable scatter that ranks equal digits with warp match masks
-// in element order); the height sort takes 8-bit digits, the tile sort 9-bit digits, so that
-// the tile ids of up to 2^18 tiles take two passes.
+// in element order); the height sort takes 8-bit digits, the tile sort 9-bit digits where they
+// save a pass (tile ids of 17-18 bits take two 9-bit passes instead of three 8-bit ones).
 #include "kernels.cuh"
 
 namespace ss {
