@@ -109,11 +109,12 @@ typedef struct {
 
 /* Rasterizer options.  ss_default_opts() fills the defaults in brackets. */
 typedef struct {
-  int32_t tile_w, tile_h; /* screen tile [16 x 16]; also 32 x 8 and 8 x 32 */
+  int32_t tile_w, tile_h; /* screen tile [16 x 16]; also 32 x 8, 8 x 32 (two warps per tile) and
+                             32 x 16, 16 x 32 (four warps per tile) */
   int32_t batch;          /* splats a tile block stages in shared memory per batch [256], the
                              only value; the block copies each batch with cp.async */
-  int32_t persistent;     /* [0] one block (two warps) per tile; 1: one persistent launch whose
-                             blocks pull tiles from a queue */
+  int32_t persistent;     /* [0] one block (one warp per 128 pixels) per tile; 1: one persistent
+                             launch whose blocks pull tiles from a queue */
   float sigma_px;         /* screen-space low-pass sigma, pixels [1/sqrt(2)] */
   float det_eps;          /* |det M| threshold, px^2 [1e-6] */
   float alpha_min;        /* a splat contributes iff alpha >= alpha_min [1/255] */

@@ -26,7 +26,7 @@ from . import _lib as L
 from .frame import Frame, Outputs, grads_struct
 
 # (tile_w, tile_h, batch, pixels per thread)
-TILE_CANDIDATES = [(16, 16, 256, 4), (32, 8, 256, 4), (8, 32, 256, 4)]
+TILE_CANDIDATES = [(16, 16, 256, 4), (32, 8, 256, 4), (8, 32, 256, 4), (32, 16, 256, 4), (16, 32, 256, 4)]
 
 
 def _opts(c):

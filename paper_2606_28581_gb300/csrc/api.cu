@@ -56,7 +56,8 @@ bool finite(float x) { return std::isfinite(x); }
 ss_status check_opts(const ss_raster_opts* o) {
   if (!o) return SS_ERR_INVALID_ARG;
   const bool shape = (o->tile_w == 16 && o->tile_h == 16) || (o->tile_w == 32 && o->tile_h == 8) ||
-                     (o->tile_w == 8 && o->tile_h == 32);
+                     (o->tile_w == 8 && o->tile_h == 32) || (o->tile_w == 32 && o->tile_h == 16) ||
+                     (o->tile_w == 16 && o->tile_h == 32);
   if (!shape) return SS_ERR_INVALID_ARG;
   if (o->batch != 256) return SS_ERR_INVALID_ARG;
   if (o->pixels_per_thread != 4) return SS_ERR_INVALID_ARG;

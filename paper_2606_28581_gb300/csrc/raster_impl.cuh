@@ -33,8 +33,9 @@
 namespace ss {
 
 constexpr int kWarpPixels = 128;  // pixels of one warp
-constexpr int kTileWarps = 2;     // every tile shape holds 256 pixels: two warps per tile block
-constexpr int kTileThreads = 32 * kTileWarps;
+// warps of a tile block: one per 128 pixels of the tile
+template <int TW, int TH>
+__host__ __device__ constexpr int tile_warps() { return TW * TH / kWarpPixels; }
 
 __device__ __forceinline__ int find_target(const TargetCam* tc, int n_targets, int tile) {
   int lo = 0, hi = n_targets - 1;
@@ -134,13 +135,13 @@ __host__ __device__ constexpr int stage_bufs() { return B > 128 ? 1 : 2; }
 template <int B>
 __host__ __device__ constexpr int mask_chunks() { return (B + 127) / 128; }  // 32-entry chunks held per lane of a group
 
-template <int B>
+template <int B, int NW>
 struct TileStage {
   float4 g[stage_bufs<B>()][B][3];
   float4 f[stage_bufs<B>()][B][2];
   uint32_t k[stage_bufs<B>()][B];
   uint32_t mask[B];
-  uint8_t list[8 * kTileWarps][B + 4];  // per group its candidates' slots (buffer * B + index); rows
+  uint8_t list[8 * NW][B + 4];  // per group its candidates' slots (buffer * B + index); rows
                                         // padded so that the groups read at one position from
                                         // different banks
 };
@@ -297,24 +298,23 @@ __device__ __forceinline__ int compact_candidates(const uint32_t (&mk)[CH], uint
 
 // Splat indices of a batch (thread t holds entries t, t + kTileThreads, ...), loaded one batch
 // ahead of their copies.
-template <int B>
-__device__ __forceinline__ void load_vals(uint32_t (&kv)[B / kTileThreads], const uint32_t* vals, uint32_t b0,
-                                          int nb) {
+template <int B, int NT>
+__device__ __forceinline__ void load_vals(uint32_t (&kv)[B / NT], const uint32_t* vals, uint32_t b0, int nb) {
 #pragma unroll
-  for (int c = 0; c < B / kTileThreads; ++c) {
-    const int i = c * kTileThreads + threadIdx.x;
+  for (int c = 0; c < B / NT; ++c) {
+    const int i = c * NT + threadIdx.x;
     kv[c] = i < nb ? __ldg(vals + b0 + i) : 0u;
   }
 }
 
 // Issues the asynchronous copies of a batch's records into buffer `buf` (one commit group).
 // A sun view composites depth alone and needs only the first feature vector.
-template <int B>
-__device__ __forceinline__ void stage_issue(TileStage<B>& S, int buf, const uint32_t (&kv)[B / kTileThreads],
+template <int B, int NW>
+__device__ __forceinline__ void stage_issue(TileStage<B, NW>& S, int buf, const uint32_t (&kv)[B / (32 * NW)],
                                             int nb, const RasterParams& p, int64_t recbase, bool sun) {
 #pragma unroll
-  for (int c = 0; c < B / kTileThreads; ++c) {
-    const int i = c * kTileThreads + threadIdx.x;
+  for (int c = 0; c < B / (32 * NW); ++c) {
+    const int i = c * (32 * NW) + threadIdx.x;
     if (i < nb) {
       const int64_t rec = recbase + kv[c];
       const float4* g = p.geom + rec * 3;
@@ -332,12 +332,12 @@ __device__ __forceinline__ void stage_issue(TileStage<B>& S, int buf, const uint
 
 // Sub-block masks of a landed batch: each thread reads the records it copied itself (before the
 // barrier that publishes copies and masks to the block).
-template <int TW, int TH, int B>
-__device__ __forceinline__ void stage_masks(TileStage<B>& S, int buf, int nb, const LaneGeom& lg,
+template <int TW, int TH, int B, int NW>
+__device__ __forceinline__ void stage_masks(TileStage<B, NW>& S, int buf, int nb, const LaneGeom& lg,
                                             const RasterParams& p) {
 #pragma unroll
-  for (int c = 0; c < B / kTileThreads; ++c) {
-    const int i = c * kTileThreads + threadIdx.x;
+  for (int c = 0; c < B / (32 * NW); ++c) {
+    const int i = c * (32 * NW) + threadIdx.x;
     if (i < nb)
       S.mask[i] = p.subblock_cull ? subblock_mask<TW, TH>(S.g[buf][i][0], S.g[buf][i][1], S.g[buf][i][2], lg.x0,
                                                           lg.y0, p.cull)
@@ -444,10 +444,12 @@ __device__ __forceinline__ uint32_t composite(FwdPair& s, const PairEval2& e, bo
 // COUNT: the launch also counts the walked pairs (the algorithmic work of the roofline) into the
 // status block; the training step runs without it.
 template <int TW, int TH, int B, bool PERSIST, bool DIST, bool COUNT>
-__global__ void __launch_bounds__(kTileThreads, 8) raster_fwd_kernel(const __grid_constant__ RasterParams p) {
-  static_assert(TW * TH == kTileWarps * kWarpPixels, "two warps per tile");
+__global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), 16 / tile_warps<TW, TH>())
+    raster_fwd_kernel(const __grid_constant__ RasterParams p) {
+  constexpr int NW = tile_warps<TW, TH>(), NT = 32 * NW;
+  static_assert(TW * TH == NW * kWarpPixels, "whole warps per tile");
   constexpr int kBufs = stage_bufs<B>();
-  __shared__ TileStage<B> S;
+  __shared__ TileStage<B, NW> S;
   __shared__ int s_item;
   const int lane = threadIdx.x & 31, grp = lane >> 2, half = threadIdx.x >> 5;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -475,12 +477,12 @@ __global__ void __launch_bounds__(kTileThreads, 8) raster_fwd_kernel(const __gri
     const int n = (int)(range.y - range.x), nbat = (n + B - 1) / B;
     auto nb_of = [&](int k) { return min(n - k * B, B); };
     uint8_t* list = S.list[half * 8 + grp];
-    uint32_t kv[B / kTileThreads];  // splat indices of the next batch to copy
+    uint32_t kv[B / NT];  // splat indices of the next batch to copy
     if (nbat > 0) {
-      load_vals<B>(kv, p.vals, range.x, nb_of(0));
+      load_vals<B, NT>(kv, p.vals, range.x, nb_of(0));
       if (kBufs == 2) {
-        stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
-        if (nbat > 1) load_vals<B>(kv, p.vals, range.x + B, nb_of(1));
+        stage_issue<B, NW>(S, 0, kv, nb_of(0), p, recbase, sun);
+        if (nbat > 1) load_vals<B, NT>(kv, p.vals, range.x + B, nb_of(1));
       }
     }
     for (int bi = 0; bi < nbat; ++bi) {
@@ -492,18 +494,18 @@ __global__ void __launch_bounds__(kTileThreads, 8) raster_fwd_kernel(const __gri
       if (__syncthreads_and(all_done)) break;
       if (kBufs == 1) {
         // one buffer: this batch's copies, the next batch's indices loaded meanwhile
-        stage_issue<B>(S, 0, kv, nb, p, recbase, sun);
-        if (bi + 1 < nbat) load_vals<B>(kv, p.vals, range.x + (uint32_t)((bi + 1) * B), nb_of(bi + 1));
+        stage_issue<B, NW>(S, 0, kv, nb, p, recbase, sun);
+        if (bi + 1 < nbat) load_vals<B, NT>(kv, p.vals, range.x + (uint32_t)((bi + 1) * B), nb_of(bi + 1));
         cp_async_wait_all();
       } else if (bi + 1 < nbat) {
         // the next batch's copies overlap this batch's walk
-        stage_issue<B>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
-        if (bi + 2 < nbat) load_vals<B>(kv, p.vals, range.x + (uint32_t)((bi + 2) * B), nb_of(bi + 2));
+        stage_issue<B, NW>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
+        if (bi + 2 < nbat) load_vals<B, NT>(kv, p.vals, range.x + (uint32_t)((bi + 2) * B), nb_of(bi + 2));
         cp_async_wait_prev();
       } else {
         cp_async_wait_all();
       }
-      stage_masks<TW, TH, B>(S, buf, nb, lg, p);
+      stage_masks<TW, TH, B, NW>(S, buf, nb, lg, p);
       __syncthreads();  // every thread's copies and masks of this batch are visible to the block
       uint32_t mk[mask_chunks<B>()];
       batch_masks<TW, TH, B>(S.mask, nb, half, mk);
@@ -701,12 +703,14 @@ __device__ __forceinline__ BwdTerms bwd_pair(BwdPair& s, const PairEval2& e, uin
 
 // The distortion's per-pixel state needs more registers: that variant runs 12 warps per SM.
 template <int TW, int TH, int B, bool PERSIST, bool DIST>
-__global__ void __launch_bounds__(kTileThreads, DIST ? 6 : 8) raster_bwd_kernel(const __grid_constant__ RasterParams p) {
-  static_assert(TW * TH == kTileWarps * kWarpPixels, "two warps per tile");
+__global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / tile_warps<TW, TH>())
+    raster_bwd_kernel(const __grid_constant__ RasterParams p) {
+  constexpr int NW = tile_warps<TW, TH>(), NT = 32 * NW;
+  static_assert(TW * TH == NW * kWarpPixels, "whole warps per tile");
   constexpr int kBufs = stage_bufs<B>();
-  __shared__ TileStage<B> S;
+  __shared__ TileStage<B, NW> S;
   __shared__ int s_item;
-  __shared__ uint32_t s_hi[kTileWarps];
+  __shared__ uint32_t s_hi[NW];
   const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3, half = threadIdx.x >> 5;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const float two_inv2s2 = 2.0f * p.k.inv2s2;
@@ -745,7 +749,7 @@ __global__ void __launch_bounds__(kTileThreads, DIST ? 6 : 8) raster_bwd_kernel(
     __syncthreads();
     uint32_t hi_all = s_hi[0];
 #pragma unroll
-    for (int w = 1; w < kTileWarps; ++w) hi_all = max(hi_all, s_hi[w]);
+    for (int w = 1; w < NW; ++w) hi_all = max(hi_all, s_hi[w]);
     // batches of B list entries from the warp's last walked position down; batch k is copied into
     // buffer k & 1 while batch k - 1 is walked
     const int nbat = (int)((hi_all - range.x + B - 1) / B);
@@ -755,12 +759,12 @@ __global__ void __launch_bounds__(kTileThreads, DIST ? 6 : 8) raster_bwd_kernel(
     };
     auto nb_of = [&](int k) { return (int)(hi_all - (uint32_t)(k * B) - lo_of(k)); };
     uint8_t* list = S.list[half * 8 + grp];
-    uint32_t kv[B / kTileThreads];  // splat indices of the next batch to copy
+    uint32_t kv[B / NT];  // splat indices of the next batch to copy
     if (nbat > 0) {
-      load_vals<B>(kv, p.vals, lo_of(0), nb_of(0));
+      load_vals<B, NT>(kv, p.vals, lo_of(0), nb_of(0));
       if (kBufs == 2) {
-        stage_issue<B>(S, 0, kv, nb_of(0), p, recbase, sun);
-        if (nbat > 1) load_vals<B>(kv, p.vals, lo_of(1), nb_of(1));
+        stage_issue<B, NW>(S, 0, kv, nb_of(0), p, recbase, sun);
+        if (nbat > 1) load_vals<B, NT>(kv, p.vals, lo_of(1), nb_of(1));
       }
     }
     for (int bi = 0; bi < nbat; ++bi) {
@@ -769,18 +773,18 @@ __global__ void __launch_bounds__(kTileThreads, DIST ? 6 : 8) raster_bwd_kernel(
       const int nb = nb_of(bi);
       if (bi > 0) __syncthreads();  // both warps are done with the buffer refilled next
       if (kBufs == 1) {
-        stage_issue<B>(S, 0, kv, nb, p, recbase, sun);
-        if (bi + 1 < nbat) load_vals<B>(kv, p.vals, lo_of(bi + 1), nb_of(bi + 1));
+        stage_issue<B, NW>(S, 0, kv, nb, p, recbase, sun);
+        if (bi + 1 < nbat) load_vals<B, NT>(kv, p.vals, lo_of(bi + 1), nb_of(bi + 1));
         cp_async_wait_all();
       } else if (bi + 1 < nbat) {
         // the next (lower) batch's copies overlap this batch's walk
-        stage_issue<B>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
-        if (bi + 2 < nbat) load_vals<B>(kv, p.vals, lo_of(bi + 2), nb_of(bi + 2));
+        stage_issue<B, NW>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
+        if (bi + 2 < nbat) load_vals<B, NT>(kv, p.vals, lo_of(bi + 2), nb_of(bi + 2));
         cp_async_wait_prev();
       } else {
         cp_async_wait_all();
       }
-      stage_masks<TW, TH, B>(S, buf, nb, lg, p);
+      stage_masks<TW, TH, B, NW>(S, buf, nb, lg, p);
       __syncthreads();  // every thread's copies and masks of this batch are visible to the block
       uint32_t mk[mask_chunks<B>()];
       batch_masks<TW, TH, B>(S.mask, nb, half, mk);
@@ -873,7 +877,7 @@ __global__ void __launch_bounds__(kTileThreads, DIST ? 6 : 8) raster_bwd_kernel(
 // queue; otherwise one block per tile.  Resident blocks per SM are queried once per kernel
 // (outside any later stream capture).
 template <typename K>
-cudaError_t launch_items(K kernel, const RasterParams& p, bool persistent, int num_sms, int& per_sm,
+cudaError_t launch_items(K kernel, int threads, const RasterParams& p, bool persistent, int num_sms, int& per_sm,
                          cudaStream_t st) {
   const int n_items = p.total_tiles;
   if (n_items == 0) return cudaSuccess;
@@ -881,29 +885,29 @@ cudaError_t launch_items(K kernel, const RasterParams& p, bool persistent, int n
   if (persistent) {
     if (per_sm == 0) {
       int v = 0;
-      const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kTileThreads, 0);
+      const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, 0);
       if (e != cudaSuccess) return e;
       per_sm = v < 1 ? 1 : v;
     }
     grid = min(num_sms * per_sm, n_items);
   }
   count_launch();
-  kernel<<<grid, kTileThreads, 0, st>>>(p);
+  kernel<<<grid, threads, 0, st>>>(p);
   return cudaGetLastError();
 }
 
 template <int TW, int TH, int B, bool DIST, bool COUNT>
 cudaError_t launch_fwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
   static int per_sm = 0;
-  if (persistent) return launch_items(raster_fwd_kernel<TW, TH, B, true, DIST, COUNT>, p, true, num_sms, per_sm, st);
-  return launch_items(raster_fwd_kernel<TW, TH, B, false, DIST, COUNT>, p, false, num_sms, per_sm, st);
+  if (persistent) return launch_items(raster_fwd_kernel<TW, TH, B, true, DIST, COUNT>, 32 * tile_warps<TW, TH>(), p, true, num_sms, per_sm, st);
+  return launch_items(raster_fwd_kernel<TW, TH, B, false, DIST, COUNT>, 32 * tile_warps<TW, TH>(), p, false, num_sms, per_sm, st);
 }
 
 template <int TW, int TH, int B, bool DIST>
 cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
   static int per_sm = 0;
-  if (persistent) return launch_items(raster_bwd_kernel<TW, TH, B, true, DIST>, p, true, num_sms, per_sm, st);
-  return launch_items(raster_bwd_kernel<TW, TH, B, false, DIST>, p, false, num_sms, per_sm, st);
+  if (persistent) return launch_items(raster_bwd_kernel<TW, TH, B, true, DIST>, 32 * tile_warps<TW, TH>(), p, true, num_sms, per_sm, st);
+  return launch_items(raster_bwd_kernel<TW, TH, B, false, DIST>, 32 * tile_warps<TW, TH>(), p, false, num_sms, per_sm, st);
 }
 
 // Instantiates the launchers of one tile shape for the staged batch of 256 splats per block, with

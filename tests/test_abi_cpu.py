@@ -60,7 +60,7 @@ def test_workspace_size_validates_on_the_host(lib):
     assert size > 2 * sc.n * (48 + 32 + 8 + 64)
     out = ctypes.c_size_t(0)
     for bad in (L.default_opts(batch=100), L.default_opts(batch=128), L.default_opts(pixels_per_thread=2),
-                L.default_opts(tile_w=32, tile_h=16), L.default_opts(subblock_cull=2),
+                L.default_opts(tile_w=32, tile_h=32), L.default_opts(subblock_cull=2),
                 L.default_opts(count_pairs=2)):
         assert lib.ss_workspace_size(ctypes.byref(s), cams, 1, 1, ctypes.byref(bad), 1 << 20,
                                      ctypes.byref(out)) == L.SS_ERR_INVALID_ARG

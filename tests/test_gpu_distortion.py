@@ -40,7 +40,7 @@ def test_distortion_forward_parity(name):
 
 
 @pytest.mark.parametrize("tile,batch,persistent", [((16, 16), 256, 1), ((32, 8), 256, 0), ((8, 32), 256, 1),
-                                                   ((16, 16), 256, 0)])
+                                                   ((16, 16), 256, 0), ((32, 16), 256, 1)])
 def test_distortion_tile_shapes_agree(tile, batch, persistent):
     scene = ragged_scene(seed=4)
     ds = DeviceScene(scene)

@@ -156,7 +156,8 @@ def test_bf16_backward_parity():
 
 
 @pytest.mark.parametrize("tile,batch,persistent", [((32, 8), 256, 0), ((8, 32), 256, 0), ((16, 16), 256, 1),
-                                                   ((32, 8), 256, 1), ((8, 32), 256, 1)])
+                                                   ((32, 8), 256, 1), ((8, 32), 256, 1), ((32, 16), 256, 0),
+                                                   ((16, 32), 256, 1)])
 def test_tile_shape_and_schedule_do_not_change_outputs(tile, batch, persistent):
     scene = ragged_scene(seed=2)
     ds = DeviceScene(scene)
