@@ -121,10 +121,10 @@ typedef struct {
   float alpha_max;        /* alpha = min(alpha_max, o G^) [0.99] */
   float t_min;            /* stop before the splat that takes T below t_min [1e-4] */
   int32_t pixels_per_thread; /* [4], the only value: each lane owns one column of four pixels
-                                of a 4 x 4 sub-block.  Tile shape, batch and persistence never
-                                change an output. */
+                                of a sub-block (4 x 4 in the forward, 2 x 4 in the backward).
+                                Tile shape, batch and persistence never change an output. */
   int32_t subblock_cull;  /* [1] each group of lanes walks only the staged splats whose support
-                             can reach its 4 x 4 sub-block; 0 walks every staged splat in every
+                             can reach its sub-block; 0 walks every staged splat in every
                              sub-block.  The outputs are identical (the test is conservative);
                              0 is slower and serves to check that. */
   int32_t count_pairs;    /* [0] 1: ss_rasterize_fwd also counts the walked (pixel, splat) pairs
@@ -246,7 +246,7 @@ ss_status ss_rasterize_fwd(const ss_splats* splats, const ss_camera* cams, int32
  * and ss_project_splats for the same frame.  Per pixel the walk runs in reverse
  * from `last`, recovering the transmittance from T_final (Sec. 3.2
  * Eq. rasterization, differentiated); per-splat partials are summed over each
- * lane's four pixels and reduced across the four lanes of a 4 x 4 sub-block,
+ * lane's four pixels and reduced across the two lanes of a 2 x 4 sub-block,
  * then added into per-(target, splat) records in the workspace with vector
  * reductions in L2; K5 (ss_project_bwd) chains them through the projection.
  * Call it once per ss_project_splats: the records start from zero there.

@@ -1,29 +1,31 @@
 // Forward (K3) and backward (K4) rasterization, Sec. 3.2 Eq. rasterization.
 //
-// Work decomposition.  A screen tile (16 x 16, 32 x 8 or 8 x 32 px) is split into 4 x 4 pixel
-// sub-blocks.  A block of two warps renders one tile; each warp renders 128 pixels (a 16 x 8
-// half, or an 8 x 16 half of an 8 x 32 tile): eight sub-blocks, one per group of four lanes.
-// Lane l of a group owns column l of its sub-block, four pixels, kept as two pairs (rows 0-1 and
-// 2-3) so that the paired FP32 instructions of sm_100-family GPUs compute two pixels in one issue.
-// The block stages the tile's sorted splat list in shared memory in batches of 256 records copied
+// Work decomposition.  A screen tile (16 x 16, 32 x 8, 8 x 32, 32 x 16 or 16 x 32 px) is rendered
+// by one block of one warp per 128 pixels (a 16 x 8 part, or 8 x 16 in 8-wide tiles).  A warp's
+// pixels are split into sub-blocks of GL columns by 4 rows, one per group of GL lanes: 4 x 4 in the
+// forward (eight groups of four lanes), 2 x 4 in the backward (sixteen groups of two).  Lane l of
+// a group owns column l of its sub-block, four pixels, kept as two pairs (rows 0-1 and 2-3) so
+// that the paired FP32 instructions of sm_100-family GPUs compute two pixels in one issue.  The
+// block stages the tile's sorted splat list in shared memory in batches of 256 records copied
 // with cp.async (the next batch's splat indices are loaded while a batch is walked); large
-// batches keep the eight groups of a warp, which walk their own candidate lists in lockstep,
-// evenly loaded.
+// batches keep the groups of a warp, which walk their own candidate lists in lockstep, evenly
+// loaded.
 //
-// The thread that stages a splat forms the set of the tile's 16 sub-blocks its support can reach
+// The thread that stages a splat forms the set of the tile's sub-blocks its support can reach
 // (`subblock_mask`); each group walks only the staged splats that reach its sub-block, in list
 // order (forward) or reverse list order (backward).  A pixel's walk is therefore exactly the
-// per-pixel definition, whatever the tile shape or schedule, and every pixel runs the same FP32
-// operations in both kernels, so the backward retraces the forward's alpha decisions bit for bit.
+// per-pixel definition, whatever the tile shape, grouping or schedule, and every pixel runs the
+// same FP32 operations in both kernels, so the backward retraces the forward's alpha decisions
+// bit for bit.
 //
 // Backward: with T_i the transmittance in front of splat i and S_i the composite behind it
 // (normalised to T_{i+1}), d f / d alpha_i = T_i (f_i - S_i); the alpha output adds
 // T_final / (1 - alpha_i).  T_i is recovered as T_{i+1} / (1 - alpha_i) from the saved T_final
 // (alpha <= alpha_max < 1 keeps the division safe); only T_final and the end of the walk are
 // stored per pixel.  A lane sums its four pixels' contributions to the 16 gradient fields of the
-// splat, the four lanes of the group reduce them with a transposed butterfly (each lane ends with
-// four fields), and each lane adds its four fields to the (target, splat) gradient record with one
-// vector reduction in L2 (red.global.add.v4.f32).
+// splat, the lanes of the group reduce them with a transposed butterfly (each of the two lanes
+// ends with eight fields), and each lane adds its fields to the (target, splat) gradient record
+// with vector reductions in L2 (red.global.add.v4.f32).
 #pragma once
 
 #include <type_traits>
@@ -36,6 +38,20 @@ constexpr int kWarpPixels = 128;  // pixels of one warp
 // warps of a tile block: one per 128 pixels of the tile
 template <int TW, int TH>
 __host__ __device__ constexpr int tile_warps() { return TW * TH / kWarpPixels; }
+// Lanes of a group (GL, two or four): a group owns a sub-block of GL pixel columns by 4 rows, one
+// column per lane; a warp holds 32 / GL groups.
+template <int TW, int TH, int GL>
+__host__ __device__ constexpr int tile_subblocks() { return TW * TH / (4 * GL); }
+// A tile's sub-block mask: one bit per sub-block.
+template <int TW, int TH, int GL>
+using SubMask = std::conditional_t<(tile_subblocks<TW, TH, GL>() > 32), unsigned long long, uint32_t>;
+// Staging and grouping of each direction.  Both stage batches of 256 records.  The forward walks
+// 4 x 4 sub-blocks (groups of four lanes).  The backward walks 2 x 4 sub-blocks (groups of two
+// lanes): on the 16-view workload they evaluate 1.41 pairs per walked pair against 1.66, at the
+// price of two L2 vector reductions per lane and step instead of one.  The forward, whose step has
+// no reduction, measured no faster with the finer grain.
+constexpr int kFwdBatch = 256, kFwdGroupLanes = 4;
+constexpr int kBwdBatch = 256, kBwdGroupLanes = 2;
 
 __device__ __forceinline__ int find_target(const TargetCam* tc, int n_targets, int tile) {
   int lo = 0, hi = n_targets - 1;
@@ -90,25 +106,23 @@ __device__ __forceinline__ PairEval2 eval_pair2(const float4 g0, const float4 g1
   return e;
 }
 
-// Transposed reduction of 16 values over the 4 lanes of a group: lane gl of the group ends with
-// the group sums of fields 4 gl .. 4 gl + 3 (12 shuffles; each exchange sends the half of the
-// values that the partner keeps).
-__device__ __forceinline__ float4 group_reduce16(float v[16]) {
+// Transposed reduction of 16 values over the lanes of a group: lane gl of the group ends with the
+// group sums of fields F gl .. F gl + F - 1 (F = 16 / GL) in v[0 .. F - 1].  Each exchange
+// sends the half of the values that the partner keeps (8 shuffles for two lanes, 12 for four).
+template <int GL>
+__device__ __forceinline__ void group_reduce16(float v[16]) {
+  static_assert(GL == 2 || GL == 4, "groups of two or four lanes");
   const int lane = threadIdx.x & 31;
-  const bool up2 = lane & 2, up1 = lane & 1;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float send = up2 ? v[i] : v[i + 8];
-    const float keep = up2 ? v[i + 8] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
+  for (int s = GL / 2, n = 16; s >= 1; s >>= 1, n >>= 1) {
+    const bool up = lane & s;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float send = up1 ? v[i] : v[i + 4];
-    const float keep = up1 ? v[i + 4] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+    for (int i = 0; i < n / 2; ++i) {
+      const float send = up ? v[i] : v[i + n / 2];
+      const float keep = up ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
   }
-  return make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // One vector reduction of four floats into global memory (16-byte aligned), performed in L2.
@@ -132,55 +146,59 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // larger ones fit shared memory once.
 template <int B>
 __host__ __device__ constexpr int stage_bufs() { return B > 128 ? 1 : 2; }
-template <int B>
-__host__ __device__ constexpr int mask_chunks() { return (B + 127) / 128; }  // 32-entry chunks held per lane of a group
+// 32-entry chunks of a batch held per lane of a group
+template <int B, int GL>
+__host__ __device__ constexpr int mask_chunks() { return (B + 32 * GL - 1) / (32 * GL); }
+// entries of a batch that each thread of a block of NT threads copies
+template <int B, int NT>
+__host__ __device__ constexpr int per_thread() { return (B + NT - 1) / NT; }
 
-template <int B, int NW>
+template <int B, int NW, typename M, int GL>
 struct TileStage {
   float4 g[stage_bufs<B>()][B][3];
   float4 f[stage_bufs<B>()][B][2];
   uint32_t k[stage_bufs<B>()][B];
-  uint32_t mask[B];
-  uint8_t list[8 * NW][B + 4];  // per group its candidates' slots (buffer * B + index); rows
+  M mask[B];
+  uint8_t list[32 / GL * NW][B + 4];  // per group its candidates' slots (buffer * B + index); rows
                                         // padded so that the groups read at one position from
                                         // different banks
 };
 
-// Pixels of this lane and the tile's origin.  The warp's half of the tile is 16 x 8 (8 x 16 for
-// 8-wide tiles); its eight 4 x 4 sub-blocks go to the eight groups in row-major order.
+// Pixels of this lane and the tile's origin.  A warp's 128 pixels are 16 x 8 (8 x 16 for 8-wide
+// tiles); its sub-blocks go to its groups in row-major order.
 struct LaneGeom {
   int px;        // pixel column
   int py0;       // first of the lane's four pixel rows
-  int sub;       // bit of the lane's sub-block in the tile's 16-bit sub-block mask
+  int sub;       // bit of the lane's sub-block in the tile's sub-block mask
   float x0, y0;  // the tile's first pixel column and row
 };
 
-template <int TW, int TH>
+template <int TW, int TH, int GL>
 __device__ __forceinline__ int group_sub(int half, int grp) {
   constexpr int WW = TW >= 16 ? 16 : 8, WH = kWarpPixels / WW;
-  constexpr int WX = TW / WW, GX = WW / 4, SBX = TW / 4;
+  constexpr int WX = TW / WW, GX = WW / GL, SBX = TW / GL;
   const int wx = half % WX, wy = half / WX;
   const int sbx = wx * GX + grp % GX, sby = wy * (WH / 4) + grp / GX;
   return sby * SBX + sbx;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int GL>
 __device__ __forceinline__ LaneGeom lane_geom(const TargetCam& cam, int tile, int half) {
-  constexpr int SBX = TW / 4;
-  const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3;
+  constexpr int SBX = TW / GL;
+  const int lane = threadIdx.x & 31, grp = lane / GL, gl = lane % GL;
   const int local = tile - cam.tile_base;
   const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
   LaneGeom g;
-  g.sub = group_sub<TW, TH>(half, grp);
+  g.sub = group_sub<TW, TH, GL>(half, grp);
   const int sby = g.sub / SBX, sbx = g.sub - sby * SBX;
-  g.px = tx * TW + sbx * 4 + gl;
+  g.px = tx * TW + sbx * GL + gl;
   g.py0 = ty * TH + sby * 4;
   g.x0 = (float)(tx * TW);
   g.y0 = (float)(ty * TH);
   return g;
 }
 
-// The 4 x 4 sub-blocks of a tile that a splat can reach: bit (row * TW / 4 + col) is set when the
+// The GL x 4 sub-blocks of a tile that a splat can reach: bit (row * TW / GL + col) is set when the
 // support {alpha >= alpha_min} can contain a pixel centre of sub-block (col, row).  The support is
 // the ellipse |Q d|^2 <= r2 united with the disc |d|^2 <= sigma^2 r2 (d = x - c,
 // r2 = 2 (ln o - ln alpha_min)).  A convex set meets a rectangle exactly when its slice through
@@ -191,10 +209,12 @@ __device__ __forceinline__ LaneGeom lane_geom(const TargetCam& cam, int tile, in
 // Conservative: r2 is inflated by 0.2 % (far above the FP32 error of the slice formulas and of
 // eval_pair) and the rectangles are padded by 2e-3 px (the centre's low part is ignored).
 // Degenerate splats (record ex < 0) have the disc only.
-template <int TW, int TH>
-__device__ __forceinline__ uint32_t subblock_mask(const float4 g0, const float4 g1, const float4 g2, float x0,
-                                                  float y0, const CullConsts& cc) {
-  constexpr int SBX = TW / 4, SBY = TH / 4;
+template <int TW, int TH, int GL>
+__device__ __forceinline__ SubMask<TW, TH, GL> subblock_mask(const float4 g0, const float4 g1, const float4 g2,
+                                                            float x0, float y0, const CullConsts& cc) {
+  using M = SubMask<TW, TH, GL>;
+  constexpr int SW = GL, SBX = TW / SW, SBY = TH / 4;
+  constexpr float kInvSW = 1.0f / SW;
   constexpr float kPad = 2e-3f;
   const float r2 = fmaxf(2.0f * (g2.x - cc.ln_amin), 0.0f) * 1.002f + 1e-4f;
   const float rd2 = r2 * cc.sigma2;
@@ -210,7 +230,7 @@ __device__ __forceinline__ uint32_t subblock_mask(const float4 g0, const float4 
   const float iA00 = 1.0f / A00;
   // tile-relative offsets: pixel centre (x0 + i + 0.5) - cx
   const float ox = x0 + 0.5f - g0.x, oy = y0 + 0.5f - g0.y;
-  uint32_t mask = 0;
+  M mask = 0;
 #pragma unroll
   for (int b = 0; b < SBY; ++b) {
     const float yl = oy + (float)(4 * b) - kPad, yh = oy + (float)(4 * b + 3) + kPad;
@@ -227,35 +247,36 @@ __device__ __forceinline__ uint32_t subblock_mask(const float4 g0, const float4 
       lo = fminf(lo, -hw);
       hi = fmaxf(hi, hw);
     }
-    // columns c with [ox + 4c, ox + 4c + 3] (padded) meeting [lo, hi]
-    const float cl = fmaxf(ceilf((lo - ox - 3.0f - kPad) * 0.25f), 0.0f);
-    const float ch = fminf(floorf((hi - ox + kPad) * 0.25f), (float)(SBX - 1));
+    // columns c with [ox + SW c, ox + SW c + SW - 1] (padded) meeting [lo, hi]
+    const float cl = fmaxf(ceilf((lo - ox - (float)(SW - 1) - kPad) * kInvSW), 0.0f);
+    const float ch = fminf(floorf((hi - ox + kPad) * kInvSW), (float)(SBX - 1));
     if (cl <= ch) {
       const int a = (int)cl, z = (int)ch;
-      mask |= ((2u << z) - (1u << a)) << (b * SBX);
+      mask |= ((M(2) << z) - (M(1) << a)) << (b * SBX);
     }
   }
   return mask;
 }
 
-// Candidate masks of a staged batch: lane gl of a group ends with the group's masks of chunks gl
-// and gl + 4 (staged splats [32 c, 32 c + 32)).  Holding every chunk at once lets a group walk its
-// candidates across chunk boundaries.
-template <int TW, int TH, int B>
-__device__ __forceinline__ void batch_masks(const uint32_t* smask, int nb, int half, uint32_t (&mk)[mask_chunks<B>()]) {
-  static_assert(B % 32 == 0 && B / 32 <= 4 * mask_chunks<B>(), "chunks per lane of a group");
-  const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3;
+// Candidate masks of a staged batch: lane gl of a group ends with the group's masks of chunks
+// gl, gl + GL, ... (staged splats [32 c, 32 c + 32)).  Holding every chunk at once lets a
+// group walk its candidates across chunk boundaries.
+template <int TW, int TH, int B, int GL>
+__device__ __forceinline__ void batch_masks(const SubMask<TW, TH, GL>* smask, int nb, int half,
+                                            uint32_t (&mk)[mask_chunks<B, GL>()]) {
+  static_assert(B % 32 == 0 && B / 32 <= GL * mask_chunks<B, GL>(), "chunks per lane of a group");
+  const int lane = threadIdx.x & 31, grp = lane / GL, gl = lane % GL;
 #pragma unroll
-  for (int q = 0; q < mask_chunks<B>(); ++q) mk[q] = 0u;
+  for (int q = 0; q < mask_chunks<B, GL>(); ++q) mk[q] = 0u;
 #pragma unroll
   for (int c = 0; c < B / 32; ++c) {
     if (c * 32 >= nb) break;  // block-uniform
     const int i = c * 32 + lane;
-    const uint32_t v = i < nb ? smask[i] : 0u;
+    const SubMask<TW, TH, GL> v = i < nb ? smask[i] : 0u;
 #pragma unroll
-    for (int gg = 0; gg < 8; ++gg) {
-      const uint32_t m = __ballot_sync(0xffffffffu, (v >> group_sub<TW, TH>(half, gg)) & 1u);
-      if (grp == gg && gl == (c & 3)) mk[c >> 2] = m;
+    for (int gg = 0; gg < 32 / GL; ++gg) {
+      const uint32_t m = __ballot_sync(0xffffffffu, (uint32_t)(v >> group_sub<TW, TH, GL>(half, gg)) & 1u);
+      if (grp == gg && gl == c % GL) mk[c / GL] = m;
     }
   }
 }
@@ -265,21 +286,22 @@ __device__ __forceinline__ void batch_masks(const uint32_t* smask, int nb, int h
 // order, and returns their number.  The walk then reads its next splat from the list at a
 // position that depends on the step count alone, so no step waits on the previous one to find
 // its splat.  Every lane of the warp takes part.
-template <int CH>
+template <int GL, int CH>
 __device__ __forceinline__ int compact_candidates(const uint32_t (&mk)[CH], uint8_t* list, int slot_base,
                                                   bool desc) {
-  const int gl = threadIdx.x & 3;
+  const int gl = threadIdx.x % GL;
   int before[CH], total = 0;
 #pragma unroll
   for (int q = 0; q < CH; ++q) {
     const int c = __popc(mk[q]);
     int inc = c;
-    int t = __shfl_up_sync(0xffffffffu, inc, 1, 4);
-    if (gl >= 1) inc += t;
-    t = __shfl_up_sync(0xffffffffu, inc, 2, 4);
-    if (gl >= 2) inc += t;
+#pragma unroll
+    for (int d = 1; d < GL; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, d, GL);
+      if (gl >= d) inc += t;
+    }
     before[q] = total + inc - c;
-    total += __shfl_sync(0xffffffffu, inc, 3, 4);
+    total += __shfl_sync(0xffffffffu, inc, GL - 1, GL);
   }
 #pragma unroll
   for (int q = 0; q < CH; ++q) {
@@ -288,7 +310,7 @@ __device__ __forceinline__ int compact_candidates(const uint32_t (&mk)[CH], uint
     while (mm) {
       const int bit = __ffs(mm) - 1;
       mm &= mm - 1;
-      list[desc ? total - 1 - k : k] = (uint8_t)(slot_base + (q * 4 + gl) * 32 + bit);
+      list[desc ? total - 1 - k : k] = (uint8_t)(slot_base + (q * GL + gl) * 32 + bit);
       ++k;
     }
   }
@@ -299,9 +321,10 @@ __device__ __forceinline__ int compact_candidates(const uint32_t (&mk)[CH], uint
 // Splat indices of a batch (thread t holds entries t, t + kTileThreads, ...), loaded one batch
 // ahead of their copies.
 template <int B, int NT>
-__device__ __forceinline__ void load_vals(uint32_t (&kv)[B / NT], const uint32_t* vals, uint32_t b0, int nb) {
+__device__ __forceinline__ void load_vals(uint32_t (&kv)[per_thread<B, NT>()], const uint32_t* vals, uint32_t b0,
+                                          int nb) {
 #pragma unroll
-  for (int c = 0; c < B / NT; ++c) {
+  for (int c = 0; c < per_thread<B, NT>(); ++c) {
     const int i = c * NT + threadIdx.x;
     kv[c] = i < nb ? __ldg(vals + b0 + i) : 0u;
   }
@@ -309,11 +332,12 @@ __device__ __forceinline__ void load_vals(uint32_t (&kv)[B / NT], const uint32_t
 
 // Issues the asynchronous copies of a batch's records into buffer `buf` (one commit group).
 // A sun view composites depth alone and needs only the first feature vector.
-template <int B, int NW>
-__device__ __forceinline__ void stage_issue(TileStage<B, NW>& S, int buf, const uint32_t (&kv)[B / (32 * NW)],
+template <int B, int NW, typename M, int GL>
+__device__ __forceinline__ void stage_issue(TileStage<B, NW, M, GL>& S, int buf,
+                                            const uint32_t (&kv)[per_thread<B, 32 * NW>()],
                                             int nb, const RasterParams& p, int64_t recbase, bool sun) {
 #pragma unroll
-  for (int c = 0; c < B / (32 * NW); ++c) {
+  for (int c = 0; c < per_thread<B, 32 * NW>(); ++c) {
     const int i = c * (32 * NW) + threadIdx.x;
     if (i < nb) {
       const int64_t rec = recbase + kv[c];
@@ -332,16 +356,17 @@ __device__ __forceinline__ void stage_issue(TileStage<B, NW>& S, int buf, const 
 
 // Sub-block masks of a landed batch: each thread reads the records it copied itself (before the
 // barrier that publishes copies and masks to the block).
-template <int TW, int TH, int B, int NW>
-__device__ __forceinline__ void stage_masks(TileStage<B, NW>& S, int buf, int nb, const LaneGeom& lg,
+template <int TW, int TH, int B, int NW, int GL>
+__device__ __forceinline__ void stage_masks(TileStage<B, NW, SubMask<TW, TH, GL>, GL>& S, int buf, int nb,
+                                            const LaneGeom& lg,
                                             const RasterParams& p) {
 #pragma unroll
-  for (int c = 0; c < B / (32 * NW); ++c) {
+  for (int c = 0; c < per_thread<B, 32 * NW>(); ++c) {
     const int i = c * (32 * NW) + threadIdx.x;
     if (i < nb)
-      S.mask[i] = p.subblock_cull ? subblock_mask<TW, TH>(S.g[buf][i][0], S.g[buf][i][1], S.g[buf][i][2], lg.x0,
+      S.mask[i] = p.subblock_cull ? subblock_mask<TW, TH, GL>(S.g[buf][i][0], S.g[buf][i][1], S.g[buf][i][2], lg.x0,
                                                           lg.y0, p.cull)
-                                  : 0xffffu;
+                                  : ~SubMask<TW, TH, GL>(0);
   }
 }
 
@@ -443,15 +468,15 @@ __device__ __forceinline__ uint32_t composite(FwdPair& s, const PairEval2& e, bo
 
 // COUNT: the launch also counts the walked pairs (the algorithmic work of the roofline) into the
 // status block; the training step runs without it.
-template <int TW, int TH, int B, bool PERSIST, bool DIST, bool COUNT>
+template <int TW, int TH, int B, int GL, bool PERSIST, bool DIST, bool COUNT>
 __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), 16 / tile_warps<TW, TH>())
     raster_fwd_kernel(const __grid_constant__ RasterParams p) {
   constexpr int NW = tile_warps<TW, TH>(), NT = 32 * NW;
   static_assert(TW * TH == NW * kWarpPixels, "whole warps per tile");
   constexpr int kBufs = stage_bufs<B>();
-  __shared__ TileStage<B, NW> S;
+  __shared__ TileStage<B, NW, SubMask<TW, TH, GL>, GL> S;
   __shared__ int s_item;
-  const int lane = threadIdx.x & 31, grp = lane >> 2, half = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, grp = lane / GL, half = threadIdx.x >> 5;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   ItemQueue<PERSIST> q;
   q.begin(&p.status->work_fwd, &s_item);
@@ -460,7 +485,7 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), 16 / tile_warps<TW,
     const int tile = q.item;
     const int t = find_target(p.tcams, p.n_targets, tile);
     const TargetCam& cam = p.tcams[t];
-    const LaneGeom lg = lane_geom<TW, TH>(cam, tile, half);
+    const LaneGeom lg = lane_geom<TW, TH, GL>(cam, tile, half);
     const bool sun = cam.sun != 0;
     const float x = (float)lg.px + 0.5f;
     const float yb = (float)lg.py0 + 0.5f;
@@ -476,12 +501,12 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), 16 / tile_warps<TW,
     // k - 1 is walked
     const int n = (int)(range.y - range.x), nbat = (n + B - 1) / B;
     auto nb_of = [&](int k) { return min(n - k * B, B); };
-    uint8_t* list = S.list[half * 8 + grp];
-    uint32_t kv[B / NT];  // splat indices of the next batch to copy
+    uint8_t* list = S.list[half * (32 / GL) + grp];
+    uint32_t kv[per_thread<B, NT>()];  // splat indices of the next batch to copy
     if (nbat > 0) {
       load_vals<B, NT>(kv, p.vals, range.x, nb_of(0));
       if (kBufs == 2) {
-        stage_issue<B, NW>(S, 0, kv, nb_of(0), p, recbase, sun);
+        stage_issue(S, 0, kv, nb_of(0), p, recbase, sun);
         if (nbat > 1) load_vals<B, NT>(kv, p.vals, range.x + B, nb_of(1));
       }
     }
@@ -494,27 +519,28 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), 16 / tile_warps<TW,
       if (__syncthreads_and(all_done)) break;
       if (kBufs == 1) {
         // one buffer: this batch's copies, the next batch's indices loaded meanwhile
-        stage_issue<B, NW>(S, 0, kv, nb, p, recbase, sun);
+        stage_issue(S, 0, kv, nb, p, recbase, sun);
         if (bi + 1 < nbat) load_vals<B, NT>(kv, p.vals, range.x + (uint32_t)((bi + 1) * B), nb_of(bi + 1));
         cp_async_wait_all();
       } else if (bi + 1 < nbat) {
         // the next batch's copies overlap this batch's walk
-        stage_issue<B, NW>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
+        stage_issue(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
         if (bi + 2 < nbat) load_vals<B, NT>(kv, p.vals, range.x + (uint32_t)((bi + 2) * B), nb_of(bi + 2));
         cp_async_wait_prev();
       } else {
         cp_async_wait_all();
       }
-      stage_masks<TW, TH, B, NW>(S, buf, nb, lg, p);
+      stage_masks<TW, TH, B, NW, GL>(S, buf, nb, lg, p);
       __syncthreads();  // every thread's copies and masks of this batch are visible to the block
-      uint32_t mk[mask_chunks<B>()];
-      batch_masks<TW, TH, B>(S.mask, nb, half, mk);
+      uint32_t mk[mask_chunks<B, GL>()];
+      batch_masks<TW, TH, B, GL>(S.mask, nb, half, mk);
       // a group whose 16 pixels have all stopped walks nothing
-      if (((__ballot_sync(0xffffffffu, all_done) >> (lane & 28)) & 0xfu) == 0xfu) {
+      constexpr uint32_t kGroupBits = (1u << GL) - 1u;
+      if (((__ballot_sync(0xffffffffu, all_done) >> (lane & ~(GL - 1))) & kGroupBits) == kGroupBits) {
 #pragma unroll
-        for (int q = 0; q < mask_chunks<B>(); ++q) mk[q] = 0u;
+        for (int q = 0; q < mask_chunks<B, GL>(); ++q) mk[q] = 0u;
       }
-      const int total = compact_candidates(mk, list, buf * B, false);
+      const int total = compact_candidates<GL>(mk, list, buf * B, false);
       const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
       auto walk = [&](auto sun_c) {
         constexpr bool SUN = decltype(sun_c)::value;
@@ -529,7 +555,7 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), 16 / tile_warps<TW,
           const float4 f1 = SUN ? zero4 : fs[1];
           const PairEval2 eA = eval_pair2(g0, g1, g2, x, yA, p.k);
           const PairEval2 eB = eval_pair2(g0, g1, g2, x, yB, p.k);
-          const uint32_t pos = b0 + (uint32_t)(slot & (B - 1)) + 1u;
+          const uint32_t pos = b0 + (uint32_t)(kBufs == 1 ? slot : (slot & (B - 1))) + 1u;
           const uint32_t wa = composite<SUN, DIST>(sA, eA, has, g2, f0, f1, pos, p.t_min);
           const uint32_t wb = composite<SUN, DIST>(sB, eB, has, g2, f0, f1, pos, p.t_min);
           if (COUNT) walked += wa + wb;
@@ -702,16 +728,16 @@ __device__ __forceinline__ BwdTerms bwd_pair(BwdPair& s, const PairEval2& e, uin
 }
 
 // The distortion's per-pixel state needs more registers: that variant runs 12 warps per SM.
-template <int TW, int TH, int B, bool PERSIST, bool DIST>
+template <int TW, int TH, int B, int GL, bool PERSIST, bool DIST>
 __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / tile_warps<TW, TH>())
     raster_bwd_kernel(const __grid_constant__ RasterParams p) {
   constexpr int NW = tile_warps<TW, TH>(), NT = 32 * NW;
   static_assert(TW * TH == NW * kWarpPixels, "whole warps per tile");
   constexpr int kBufs = stage_bufs<B>();
-  __shared__ TileStage<B, NW> S;
+  __shared__ TileStage<B, NW, SubMask<TW, TH, GL>, GL> S;
   __shared__ int s_item;
   __shared__ uint32_t s_hi[NW];
-  const int lane = threadIdx.x & 31, grp = lane >> 2, gl = lane & 3, half = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, grp = lane / GL, gl = lane % GL, half = threadIdx.x >> 5;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const float two_inv2s2 = 2.0f * p.k.inv2s2;
   ItemQueue<PERSIST> q;
@@ -721,7 +747,7 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
     const int tile = q.item;
     const int t = find_target(p.tcams, p.n_targets, tile);
     const TargetCam& cam = p.tcams[t];
-    const LaneGeom lg = lane_geom<TW, TH>(cam, tile, half);
+    const LaneGeom lg = lane_geom<TW, TH, GL>(cam, tile, half);
     const bool sun = cam.sun != 0;
     const float x = (float)lg.px + 0.5f;
     const float yb = (float)lg.py0 + 0.5f;
@@ -741,8 +767,8 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
     // the group's last walked position (exclusive): its walk ends there; the warp's batches start
     // at the largest one
     uint32_t glast = max(max(sA.last0, sA.last1), max(sB.last0, sB.last1));
-    glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 1));
-    glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, 2));
+#pragma unroll
+    for (int d = 1; d < GL; d <<= 1) glast = max(glast, __shfl_xor_sync(0xffffffffu, glast, d));
     // the tile's largest last walked position: the block's batches start there
     const uint32_t whi = __reduce_max_sync(0xffffffffu, glast);
     if (lane == 0) s_hi[half] = whi;
@@ -758,12 +784,12 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
       return top - range.x > (uint32_t)B ? top - B : range.x;
     };
     auto nb_of = [&](int k) { return (int)(hi_all - (uint32_t)(k * B) - lo_of(k)); };
-    uint8_t* list = S.list[half * 8 + grp];
-    uint32_t kv[B / NT];  // splat indices of the next batch to copy
+    uint8_t* list = S.list[half * (32 / GL) + grp];
+    uint32_t kv[per_thread<B, NT>()];  // splat indices of the next batch to copy
     if (nbat > 0) {
       load_vals<B, NT>(kv, p.vals, lo_of(0), nb_of(0));
       if (kBufs == 2) {
-        stage_issue<B, NW>(S, 0, kv, nb_of(0), p, recbase, sun);
+        stage_issue(S, 0, kv, nb_of(0), p, recbase, sun);
         if (nbat > 1) load_vals<B, NT>(kv, p.vals, lo_of(1), nb_of(1));
       }
     }
@@ -773,28 +799,28 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
       const int nb = nb_of(bi);
       if (bi > 0) __syncthreads();  // both warps are done with the buffer refilled next
       if (kBufs == 1) {
-        stage_issue<B, NW>(S, 0, kv, nb, p, recbase, sun);
+        stage_issue(S, 0, kv, nb, p, recbase, sun);
         if (bi + 1 < nbat) load_vals<B, NT>(kv, p.vals, lo_of(bi + 1), nb_of(bi + 1));
         cp_async_wait_all();
       } else if (bi + 1 < nbat) {
         // the next (lower) batch's copies overlap this batch's walk
-        stage_issue<B, NW>(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
+        stage_issue(S, buf ^ 1, kv, nb_of(bi + 1), p, recbase, sun);
         if (bi + 2 < nbat) load_vals<B, NT>(kv, p.vals, lo_of(bi + 2), nb_of(bi + 2));
         cp_async_wait_prev();
       } else {
         cp_async_wait_all();
       }
-      stage_masks<TW, TH, B, NW>(S, buf, nb, lg, p);
+      stage_masks<TW, TH, B, NW, GL>(S, buf, nb, lg, p);
       __syncthreads();  // every thread's copies and masks of this batch are visible to the block
-      uint32_t mk[mask_chunks<B>()];
-      batch_masks<TW, TH, B>(S.mask, nb, half, mk);
+      uint32_t mk[mask_chunks<B, GL>()];
+      batch_masks<TW, TH, B, GL>(S.mask, nb, half, mk);
 #pragma unroll
-      for (int q = 0; q < mask_chunks<B>(); ++q) {
+      for (int q = 0; q < mask_chunks<B, GL>(); ++q) {
         // candidates at or after the group's last walked position are not walked
-        const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - ((q * 4 + gl) << 5);
+        const int lim = (int)min(max((int64_t)glast - (int64_t)b0, (int64_t)0), (int64_t)nb) - ((q * GL + gl) << 5);
         mk[q] = lim <= 0 ? 0u : (lim >= 32 ? mk[q] : mk[q] & ((1u << lim) - 1u));
       }
-      const int total = compact_candidates(mk, list, buf * B, true);
+      const int total = compact_candidates<GL>(mk, list, buf * B, true);
       const int nsteps = (int)__reduce_max_sync(0xffffffffu, (unsigned)total);
       auto walk = [&](auto sun_c) {
         constexpr bool SUN = decltype(sun_c)::value;
@@ -803,7 +829,7 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
           // nothing (j = ~0 is never below a pixel's last walked position)
           const bool ok = st < total;
           const int slot = ok ? (int)list[st] : buf * B;
-          const uint32_t j = ok ? b0 + (uint32_t)(slot & (B - 1)) : 0xffffffffu;
+          const uint32_t j = ok ? b0 + (uint32_t)(kBufs == 1 ? slot : (slot & (B - 1))) : 0xffffffffu;
           const float4* gs = &S.g[0][0][0] + slot * 3;
           const float4* fs = &S.f[0][0][0] + slot * 2;
           const float4 g0 = gs[0], g1 = gs[1], g2 = gs[2];
@@ -841,11 +867,16 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
           v[GF_CX] = hsum(add2(rA.dps, rB.dps)) * dx - (g1.x * sdu + g1.z * sdv);
           v[GF_CY] = hsum(fma2(rB.dps, eB.dy, mul2(rA.dps, eA.dy))) - (g1.y * sdu + g1.w * sdv);
           const bool any = cA0 || cA1 || cB0 || cB1;
-          const bool gany = ((__ballot_sync(0xffffffffu, any) >> (lane & 28)) & 0xfu) != 0u;
-          const float4 sum = group_reduce16(v);
-          // a sun view's fields 12 .. 15 (normal z, colour) are zero
-          if (gany && !(SUN && gl == 3))
-            red_add_v4(p.grad + (recbase + kk) * kGradFields + 4 * gl, sum.x, sum.y, sum.z, sum.w);
+          constexpr uint32_t kGroupBits = (1u << GL) - 1u;
+          const bool gany = ((__ballot_sync(0xffffffffu, any) >> (lane & ~(GL - 1))) & kGroupBits) != 0u;
+          group_reduce16<GL>(v);
+          constexpr int F = 16 / GL;  // fields summed by each lane
+          float* dst = p.grad + (recbase + kk) * kGradFields + F * gl;
+#pragma unroll
+          for (int r = 0; r < F / 4; ++r) {
+            // a sun view's fields 12 .. 15 (normal z, colour) are zero
+            if (gany && !(SUN && F * gl + 4 * r >= 12)) red_add_v4(dst + 4 * r, v[4 * r], v[4 * r + 1], v[4 * r + 2], v[4 * r + 3]);
+          }
         }
       };
       if (sun) walk(std::true_type{}); else walk(std::false_type{});
@@ -896,38 +927,40 @@ cudaError_t launch_items(K kernel, int threads, const RasterParams& p, bool pers
   return cudaGetLastError();
 }
 
-template <int TW, int TH, int B, bool DIST, bool COUNT>
+template <int TW, int TH, bool DIST, bool COUNT>
 cudaError_t launch_fwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
+  constexpr int B = kFwdBatch, GL = kFwdGroupLanes, NT = 32 * tile_warps<TW, TH>();
   static int per_sm = 0;
-  if (persistent) return launch_items(raster_fwd_kernel<TW, TH, B, true, DIST, COUNT>, 32 * tile_warps<TW, TH>(), p, true, num_sms, per_sm, st);
-  return launch_items(raster_fwd_kernel<TW, TH, B, false, DIST, COUNT>, 32 * tile_warps<TW, TH>(), p, false, num_sms, per_sm, st);
+  if (persistent) return launch_items(raster_fwd_kernel<TW, TH, B, GL, true, DIST, COUNT>, NT, p, true, num_sms, per_sm, st);
+  return launch_items(raster_fwd_kernel<TW, TH, B, GL, false, DIST, COUNT>, NT, p, false, num_sms, per_sm, st);
 }
 
-template <int TW, int TH, int B, bool DIST>
+template <int TW, int TH, bool DIST>
 cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cudaStream_t st) {
+  constexpr int B = kBwdBatch, GL = kBwdGroupLanes, NT = 32 * tile_warps<TW, TH>();
   static int per_sm = 0;
-  if (persistent) return launch_items(raster_bwd_kernel<TW, TH, B, true, DIST>, 32 * tile_warps<TW, TH>(), p, true, num_sms, per_sm, st);
-  return launch_items(raster_bwd_kernel<TW, TH, B, false, DIST>, 32 * tile_warps<TW, TH>(), p, false, num_sms, per_sm, st);
+  if (persistent) return launch_items(raster_bwd_kernel<TW, TH, B, GL, true, DIST>, NT, p, true, num_sms, per_sm, st);
+  return launch_items(raster_bwd_kernel<TW, TH, B, GL, false, DIST>, NT, p, false, num_sms, per_sm, st);
 }
 
-// Instantiates the launchers of one tile shape for the staged batch of 256 splats per block, with
-// and without the distortion, and (forward) with and without the walked-pair count.
+// Instantiates the launchers of one tile shape (batches of 256 staged splats per block), with and
+// without the distortion, and (forward) with and without the walked-pair count.
 #define SS_RASTER_FWD_DISPATCH(TW, TH)                                                                      \
   cudaError_t launch_raster_fwd_##TW##x##TH(const RasterParams& p, int batch, bool persistent, int num_sms, \
-                                            cudaStream_t st) {                                             \
+                                            cudaStream_t st) {                                              \
     if (batch != 256) return cudaErrorInvalidValue;                                                         \
-    const bool dist = p.distort != 0, cnt = p.count_pairs != 0;                                            \
-    if (dist) return cnt ? launch_fwd_t<TW, TH, 256, true, true>(p, persistent, num_sms, st)                \
-                         : launch_fwd_t<TW, TH, 256, true, false>(p, persistent, num_sms, st);              \
-    return cnt ? launch_fwd_t<TW, TH, 256, false, true>(p, persistent, num_sms, st)                         \
-               : launch_fwd_t<TW, TH, 256, false, false>(p, persistent, num_sms, st);                       \
+    const bool dist = p.distort != 0, cnt = p.count_pairs != 0;                                             \
+    if (dist) return cnt ? launch_fwd_t<TW, TH, true, true>(p, persistent, num_sms, st)                     \
+                         : launch_fwd_t<TW, TH, true, false>(p, persistent, num_sms, st);                   \
+    return cnt ? launch_fwd_t<TW, TH, false, true>(p, persistent, num_sms, st)                              \
+               : launch_fwd_t<TW, TH, false, false>(p, persistent, num_sms, st);                            \
   }
 #define SS_RASTER_BWD_DISPATCH(TW, TH)                                                                      \
   cudaError_t launch_raster_bwd_##TW##x##TH(const RasterParams& p, int batch, bool persistent, int num_sms, \
-                                            cudaStream_t st) {                                             \
+                                            cudaStream_t st) {                                              \
     if (batch != 256) return cudaErrorInvalidValue;                                                         \
-    return p.distort ? launch_bwd_t<TW, TH, 256, true>(p, persistent, num_sms, st)                          \
-                     : launch_bwd_t<TW, TH, 256, false>(p, persistent, num_sms, st);                        \
+    return p.distort ? launch_bwd_t<TW, TH, true>(p, persistent, num_sms, st)                               \
+                     : launch_bwd_t<TW, TH, false>(p, persistent, num_sms, st);                             \
   }
 
 }  // namespace ss

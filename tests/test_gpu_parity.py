@@ -186,7 +186,7 @@ def needle_scene(seed=3):
     return scene
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32)])
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32), (32, 16), (16, 32)])
 def test_subblock_culling_changes_nothing(tile):
     """The per-splat sub-block masks are conservative: walking every staged splat in every
     sub-block gives bitwise-identical forward outputs and the same gradients."""
