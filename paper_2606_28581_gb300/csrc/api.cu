@@ -35,10 +35,11 @@ struct Layout {
   size_t counts, offsets, scan_scratch;
   size_t keys_a, vals_a, keys_b, vals_b;
   size_t hist, hist_off;
+  size_t segs;
   size_t ranges;
   size_t total;
   int64_t T, n, n_pad, total_tiles, capacity;
-  int key_bits;
+  int local_bits;  // bits of the largest target's tile ids, relative to its first tile
   int hbit_lo;
   ScanPlan count_scan;
   RadixPlan rp_tiles, rp_height;
@@ -46,10 +47,6 @@ struct Layout {
   TargetStatic tg[kMaxTargets];
 };
 
-// The tile sort's digit width: 9-bit digits where they save a pass over 8-bit ones (keys of 9 or
-// 17-18 bits), else 8-bit ones, whose passes are cheaper (smaller histograms, larger blocks).
-// The height sort takes 8-bit digits.
-int tile_digit_bits(int key_bits) { return (key_bits + 8) / 9 < (key_bits + 7) / 8 ? 9 : 8; }
 
 bool finite(float x) { return std::isfinite(x); }
 
@@ -146,14 +143,17 @@ ss_status make_layout(const ss_splats* s, const ss_camera* cams, int32_t n_cams,
     }
   }
   L->total_tiles = tiles;
-  int kb = 1;
-  while ((1LL << kb) < tiles) ++kb;
-  L->key_bits = kb;
+  // The emission leaves each target's overlaps contiguous, so the tile sort orders each target's
+  // segment by its local tile id: as many bits as the largest target's tile count needs.
+  int lb = 1;
+  for (int t = 0; t < (int)L->T; ++t)
+    while ((1LL << lb) < (int64_t)L->tg[t].tiles_x * L->tg[t].tiles_y) ++lb;
+  L->local_bits = lb;
   L->hbit_lo = (s->dtype == SS_BF16) ? 16 : 0;
   L->count_scan = plan_scan(L->T * L->n);
-  L->rp_tiles = plan_radix(capacity, tile_digit_bits(kb));
+  L->rp_tiles = plan_radix(capacity, segment_digit_bits(lb), (int)L->T);
   L->rp_height = plan_radix(s->n);
-  L->tiles_in_b = radix_pass_count(0, kb, tile_digit_bits(kb)) % 2 == 1;
+  L->tiles_in_b = radix_pass_count(0, lb, segment_digit_bits(lb)) % 2 == 1;
   L->height_in_b = radix_pass_count(L->hbit_lo, 32, 8) % 2 == 1;
 
   const size_t TN = (size_t)L->T * (size_t)L->n_pad;
@@ -191,6 +191,7 @@ ss_status make_layout(const ss_splats* s, const ss_camera* cams, int32_t n_cams,
   const int64_t hb = hb_t > hb_h ? hb_t : hb_h;  // histogram entries of the larger sort
   L->hist = take((size_t)hb * 4);
   L->hist_off = take((size_t)hb * 4);
+  L->segs = take(sizeof(SortSeg) * (kMaxTargets + 1));
   L->ranges = take((size_t)tiles * 8);
   L->total = off;
   return SS_OK;
@@ -426,12 +427,14 @@ ss_status ss_bin_and_sort(const ss_splats* splats, const ss_camera* cams, int32_
                                  total, st));
   SS_CUDA_TRY(launch_finish_count(status, nullptr, nullptr, total, capacity, st));
   SS_CUDA_TRY(launch_emit(bp, st));
-  // 3. stable sort of the overlaps by tile id, then per-tile ranges
+  // 3. stable sort of each target's overlaps by tile id, then per-tile ranges
   bool tin_b = false;
-  SS_CUDA_TRY(radix_sort_pairs(at<uint32_t>(ws, L.keys_a), at<uint32_t>(ws, L.vals_a), at<uint32_t>(ws, L.keys_b),
-                               at<uint32_t>(ws, L.vals_b), 0, &status->n_isect32, 0, L.key_bits,
-                               at<uint32_t>(ws, L.hist), at<uint32_t>(ws, L.hist_off), scratch, L.rp_tiles,
-                               &tin_b, st));
+  SortSeg* segs = at<SortSeg>(ws, L.segs);
+  SS_CUDA_TRY(launch_sort_segments(at<uint32_t>(ws, L.offsets), L.n, (int)L.T, bp.tcams, status,
+                                   radix_tile(L.rp_tiles.digit_bits), segs, st));
+  SS_CUDA_TRY(radix_sort_segments(at<uint32_t>(ws, L.keys_a), at<uint32_t>(ws, L.vals_a), at<uint32_t>(ws, L.keys_b),
+                                  at<uint32_t>(ws, L.vals_b), segs, (int)L.T, L.local_bits, at<uint32_t>(ws, L.hist),
+                                  at<uint32_t>(ws, L.hist_off), scratch, L.rp_tiles, &tin_b, st));
   const uint32_t* keys = at<uint32_t>(ws, tin_b ? L.keys_b : L.keys_a);
   SS_CUDA_TRY(cudaMemsetAsync(at<char>(ws, L.ranges), 0, (size_t)L.total_tiles * 8, st));
   SS_CUDA_TRY(launch_ranges(keys, status, at<uint2>(ws, L.ranges), capacity, st));

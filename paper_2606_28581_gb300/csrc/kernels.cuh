@@ -124,7 +124,11 @@ constexpr int kRadixItems = 16;
 constexpr int kRadixTile = kRadixThreads * kRadixItems;
 int radix_tile(int digit_bits);
 int radix_pass_count(int bit_lo, int bit_hi, int digit_bits);
-RadixPlan plan_radix(int64_t capacity, int digit_bits = 8);
+// segments > 0: the plan of a segmented sort over that many segments (radix_sort_segments)
+RadixPlan plan_radix(int64_t capacity, int digit_bits = 8, int segments = 0);
+// Digit width of a segmented sort of key_bits-bit keys: as few passes as 9-bit digits allow, the
+// bits shared evenly among them, at least 7.
+int segment_digit_bits(int key_bits);
 // Stable LSD radix sort of (key, value) pairs on key bits [bit_lo, bit_hi).  The element
 // count is n_host, or *n_dev when n_dev is not null (device-resident count).  Returns in
 // *in_b whether the sorted result ended in the b buffers.
@@ -132,6 +136,25 @@ cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_
                              int64_t n_host, const uint32_t* n_dev, int bit_lo, int bit_hi,
                              uint32_t* hist, uint32_t* hist_off, unsigned long long* scan_scratch,
                              const RadixPlan& plan, bool* in_b, cudaStream_t st);
+
+// A segment of a segmented sort: elements [start, start + len), sorted among themselves on the
+// bits of key - key_base, by blocks [blk0, blk0 + nblk) of the sort's grid.  An array of nseg + 1
+// entries, the last holding in blk0 the number of blocks in use.
+struct SortSeg {
+  uint32_t start, len;
+  uint32_t blk0, nblk;
+  uint32_t key_base;
+  uint32_t pad[3];
+};
+// Stable LSD radix sort of each segment on bits [0, key_bits) of key - key_base; the segments
+// (device array, filled by launch_sort_segments) stay where they are.
+cudaError_t radix_sort_segments(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
+                                const SortSeg* segs, int nseg, int key_bits, uint32_t* hist, uint32_t* hist_off,
+                                unsigned long long* scan_scratch, const RadixPlan& plan, bool* in_b,
+                                cudaStream_t st);
+// The tile sort's segments: one per target, from the scanned per-(target, splat) tile counts.
+cudaError_t launch_sort_segments(const uint32_t* offsets, int64_t n, int nt, const TargetCam* tcams,
+                                 const StatusBlock* status, int tile, SortSeg* segs, cudaStream_t st);
 
 cudaError_t launch_height_keys(const void* means, int dtype, int64_t n, int64_t n_pad, uint32_t* keys,
                                uint32_t* vals, cudaStream_t st);

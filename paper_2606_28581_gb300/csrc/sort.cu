@@ -3,11 +3,16 @@
 // The visibility key is the height-based depth of a splat's centre (Eq. depth_affine_camera),
 // which is the same for every view, so one stable sort of the splats by height (descending,
 // ties by index) serves all targets.  Every (target, splat, tile) overlap is then emitted in
-// that order and stably sorted by the global tile id: within a tile the list stays front to
-// back.  Both sorts are a hand-written stable LSD radix sort (per-block digit histograms, a
-// device-wide exclusive scan, and a stable scatter that ranks equal digits with warp match masks
-// in element order); the height sort takes 8-bit digits, the tile sort 9-bit digits where they
-// save a pass (tile ids of 17-18 bits take two 9-bit passes instead of three 8-bit ones).
+// that order, target after target, and each target's overlaps are stably sorted by tile id:
+// within a tile the list stays front to back, and since the targets' tile ids are consecutive
+// ranges the whole array ends sorted by global tile id.  Both sorts are a hand-written stable
+// LSD radix sort (per-block digit histograms, a device-wide exclusive scan, and a stable scatter
+// that ranks equal digits with warp match masks in element order).  The height sort takes 8-bit
+// digits.  The tile sort works on each target's segment with the digits of the tile id relative
+// to the target's first tile (14 bits for a 2048^2 view of 16 x 16 tiles): two 7-bit passes where
+// the global ids of 16 views (18 bits) took two 9-bit ones, and 4M splats over 32 views
+// (20 bits) three 8-bit ones.  Its blocks never straddle two segments, and its histograms are
+// laid out segment after segment, so one scan gives each block its positions in its segment.
 #include "kernels.cuh"
 
 namespace ss {
@@ -164,51 +169,97 @@ __device__ __forceinline__ int64_t radix_count(int64_t n_host, const uint32_t* n
   return n_dev ? (int64_t)(*n_dev) : n_host;
 }
 
-// Digit histograms of one block's tile, RB-bit digits.
-template <int RB, int ITEMS>
+// The elements a block of the sort takes.  Whole-array sort (SEG false): block b takes
+// [b TILE, b TILE + TILE) of the n elements, and its count of digit d goes to d nblocks + b.
+// Segmented sort (SEG true): the block belongs to the segment s whose blocks include b, takes
+// the segment's elements from its start, and its count of digit d goes to
+// blk0 2^RB + d nblk + (b - blk0), so that one exclusive scan of the histograms, segment after
+// segment, gives every block its output positions inside its own segment; digits are taken from
+// key - key_base.
+struct BlockSpan {
+  int64_t base;      // first element
+  int count;         // elements (0: none)
+  int64_t hbase;     // histogram entry of digit 0
+  int64_t hstride;   // step between digits
+  uint32_t key_base;
+};
+
+template <bool SEG, int RB, int TILE>
+__device__ __forceinline__ bool block_span(int64_t b, int64_t n, int64_t nblocks, const SortSeg* segs, int nseg,
+                                           BlockSpan& sp) {
+  if (!SEG) {
+    sp.base = b * TILE;
+    sp.count = sp.base < n ? (int)min((int64_t)TILE, n - sp.base) : 0;
+    sp.hbase = b;
+    sp.hstride = nblocks;
+    sp.key_base = 0u;
+    return true;
+  }
+  if (b >= (int64_t)segs[nseg].blk0) return false;
+  int lo = 0, hi = nseg - 1;  // the last segment whose first block is at or before b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int64_t)segs[mid].blk0 <= b) lo = mid; else hi = mid - 1;
+  }
+  const SortSeg g = segs[lo];
+  const int64_t bis = b - (int64_t)g.blk0;
+  sp.base = (int64_t)g.start + bis * TILE;
+  sp.count = (int)min((int64_t)TILE, (int64_t)g.len - bis * TILE);
+  sp.hbase = ((int64_t)g.blk0 << RB) + bis;
+  sp.hstride = g.nblk;
+  sp.key_base = g.key_base;
+  return true;
+}
+
+// Digit histograms of one block's elements, RB-bit digits.
+template <int RB, int ITEMS, bool SEG>
 __global__ void __launch_bounds__(kRadixThreads) radix_upsweep_kernel(const uint32_t* keys, int64_t n_host,
                                                                        const uint32_t* n_dev, int shift,
                                                                        uint32_t mask, uint32_t* hist,
-                                                                       int64_t nblocks) {
+                                                                       int64_t nblocks, const SortSeg* segs,
+                                                                       int nseg) {
   constexpr int NB = 1 << RB, TILE = kRadixThreads * ITEMS;
   __shared__ uint32_t h[NB];
+  const int64_t n = SEG ? 0 : radix_count(n_host, n_dev);
+  BlockSpan sp;
+  if (!block_span<SEG, RB, TILE>(blockIdx.x, n, nblocks, segs, nseg, sp)) return;
   for (int d = threadIdx.x; d < NB; d += kRadixThreads) h[d] = 0;
   __syncthreads();
-  const int64_t n = radix_count(n_host, n_dev);
-  const int64_t base = (int64_t)blockIdx.x * TILE;
-  if (base < n) {
 #pragma unroll 4
-    for (int i = 0; i < ITEMS; ++i) {
-      const int64_t idx = base + (int64_t)i * kRadixThreads + threadIdx.x;
-      if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & mask], 1u);
-    }
+  for (int i = 0; i < ITEMS; ++i) {
+    const int j = i * kRadixThreads + threadIdx.x;
+    if (j < sp.count) atomicAdd(&h[((keys[sp.base + j] - sp.key_base) >> shift) & mask], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < NB; d += kRadixThreads) hist[(int64_t)d * nblocks + blockIdx.x] = h[d];
+  for (int d = threadIdx.x; d < NB; d += kRadixThreads) hist[sp.hbase + (int64_t)d * sp.hstride] = h[d];
 }
 
 // Stable scatter of one block's tile: ranks within the block (warps own consecutive
 // sub-chunks, equal digits ranked in element order with warp match masks), the tile reordered
 // by digit in shared memory, then written out in runs that are contiguous in the output.
-template <int RB, int ITEMS>
+template <int RB, int ITEMS, bool SEG>
 __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n_host, const uint32_t* n_dev, int shift, uint32_t mask,
-    const uint32_t* hist_off, int64_t nblocks) {
+    const uint32_t* hist_off, int64_t nblocks, const SortSeg* segs, int nseg) {
   constexpr int kWarps = kRadixThreads / 32;
-  constexpr int NB = 1 << RB, TILE = kRadixThreads * ITEMS, DPT = NB / kRadixThreads;  // digits per thread
-  static_assert(NB % kRadixThreads == 0, "whole digits per thread");
+  constexpr int NB = 1 << RB, TILE = kRadixThreads * ITEMS;
+  // digits per thread; with fewer digits than threads, thread d < NB owns digit d
+  constexpr int DPT = NB >= kRadixThreads ? NB / kRadixThreads : 1;
+  static_assert(NB < kRadixThreads || NB % kRadixThreads == 0, "whole digits per thread");
   __shared__ uint32_t whist[kWarps][NB];
   __shared__ uint32_t dbase[NB];   // output position of the block's first element of each digit
   __shared__ uint32_t dstart[NB];  // block-local position of the first element of each digit
   __shared__ uint32_t sk[TILE], sv[TILE];
-  const int64_t n = radix_count(n_host, n_dev);
-  const int64_t base = (int64_t)blockIdx.x * TILE;
-  if (base >= n) return;
-  const int count = (int)min((int64_t)TILE, n - base);
+  const int64_t n = SEG ? 0 : radix_count(n_host, n_dev);
+  BlockSpan sp;
+  if (!block_span<SEG, RB, TILE>(blockIdx.x, n, nblocks, segs, nseg, sp) || sp.count <= 0) return;
+  const int64_t base = sp.base;
+  const int count = sp.count;
+  const uint32_t kb = sp.key_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * NB; i += kRadixThreads) (&whist[0][0])[i] = 0;
-  for (int d = threadIdx.x; d < NB; d += kRadixThreads) dbase[d] = hist_off[(int64_t)d * nblocks + blockIdx.x];
+  for (int d = threadIdx.x; d < NB; d += kRadixThreads) dbase[d] = hist_off[sp.hbase + (int64_t)d * sp.hstride];
   __syncthreads();
   const uint32_t lt = (1u << lane) - 1u;
   const int wbase = warp * (ITEMS * 32);
@@ -219,7 +270,7 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
     const bool valid = idx < count;
     k[i] = valid ? keys_in[base + idx] : 0u;
     v[i] = valid ? vals_in[base + idx] : 0u;
-    const uint32_t d = valid ? ((k[i] >> shift) & mask) : (uint32_t)NB;
+    const uint32_t d = valid ? (((k[i] - kb) >> shift) & mask) : (uint32_t)NB;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
     if (valid) before = whist[warp][d];
@@ -232,26 +283,31 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
   {
     // per digit: exclusive scan of the warps' counts; then over the digits (each thread owns
     // DPT consecutive digits)
+    const bool owns = NB >= kRadixThreads || threadIdx.x < NB;
     uint32_t tsum = 0, dsum[DPT];
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
       const int d = threadIdx.x * DPT + q;
       uint32_t run = 0;
+      if (owns) {
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = whist[w][d];
-        whist[w][d] = run;
-        run += c;
+        for (int w = 0; w < kWarps; ++w) {
+          const uint32_t c = whist[w][d];
+          whist[w][d] = run;
+          run += c;
+        }
       }
       dsum[q] = run;
       tsum += run;
     }
     unsigned long long tot;
     uint32_t pre = (uint32_t)block_exclusive_scan((unsigned long long)tsum, &tot);
+    if (owns) {
 #pragma unroll
-    for (int q = 0; q < DPT; ++q) {
-      dstart[threadIdx.x * DPT + q] = pre;
-      pre += dsum[q];
+      for (int q = 0; q < DPT; ++q) {
+        dstart[threadIdx.x * DPT + q] = pre;
+        pre += dsum[q];
+      }
     }
   }
   __syncthreads();
@@ -259,7 +315,7 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
   for (int i = 0; i < ITEMS; ++i) {
     const int idx = wbase + i * 32 + lane;
     if (idx < count) {
-      const uint32_t d = (k[i] >> shift) & mask;
+      const uint32_t d = ((k[i] - kb) >> shift) & mask;
       const uint32_t lp = dstart[d] + whist[warp][d] + rk[i];
       sk[lp] = k[i];
       sv[lp] = v[i];
@@ -268,45 +324,53 @@ __global__ void __launch_bounds__(kRadixThreads) radix_downsweep_kernel(
   __syncthreads();
   for (int j = threadIdx.x; j < count; j += kRadixThreads) {
     const uint32_t kk = sk[j];
-    const uint32_t d = (kk >> shift) & mask;
+    const uint32_t d = ((kk - kb) >> shift) & mask;
     const uint32_t pos = dbase[d] + (uint32_t)j - dstart[d];
     keys_out[pos] = kk;
     vals_out[pos] = sv[j];
   }
 }
 
-// Elements per block for a digit width: 8-bit digits take 16 per thread, 9-bit digits 12 (their
-// 512-bucket rank tables leave less shared memory for the tile).
+// Elements per block for a digit width: 7- and 8-bit digits take 16 per thread, 9-bit digits 12
+// (their 512-bucket rank tables leave less shared memory for the tile).
 int radix_tile(int digit_bits) { return kRadixThreads * (digit_bits == 9 ? 12 : kRadixItems); }
 
 int radix_pass_count(int bit_lo, int bit_hi, int digit_bits) {
   return (bit_hi - bit_lo + digit_bits - 1) / digit_bits;
 }
 
-RadixPlan plan_radix(int64_t capacity, int digit_bits) {
+RadixPlan plan_radix(int64_t capacity, int digit_bits, int segments) {
   RadixPlan p{};
   p.capacity = capacity;
   p.digit_bits = digit_bits;
-  p.nblocks = (capacity + radix_tile(digit_bits) - 1) / radix_tile(digit_bits);
+  // a segment's last block may be partial: one block more per segment
+  p.nblocks = (capacity + radix_tile(digit_bits) - 1) / radix_tile(digit_bits) + segments;
   if (p.nblocks < 1) p.nblocks = 1;
   p.hist_scan = plan_scan((int64_t)(1 << digit_bits) * p.nblocks);
   return p;
 }
 
+int segment_digit_bits(int key_bits) {
+  const int passes = (key_bits + 8) / 9;
+  const int rb = (key_bits + passes - 1) / passes;
+  return rb < 7 ? 7 : rb;
+}
+
 namespace {
-template <int RB, int ITEMS>
+template <int RB, int ITEMS, bool SEG>
 cudaError_t radix_pass(const uint32_t* ki, const uint32_t* vi, uint32_t* ko, uint32_t* vo, int64_t n_host,
                        const uint32_t* n_dev, int shift, uint32_t mask, uint32_t* hist, uint32_t* hist_off,
-                       unsigned long long* scan_scratch, const ScanPlan& hs, int64_t nblocks, cudaStream_t st) {
+                       unsigned long long* scan_scratch, const ScanPlan& hs, int64_t nblocks, const SortSeg* segs,
+                       int nseg, cudaStream_t st) {
   count_launch();
-  radix_upsweep_kernel<RB, ITEMS><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, n_host, n_dev, shift, mask,
-                                                                               hist, nblocks);
+  radix_upsweep_kernel<RB, ITEMS, SEG><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
+      ki, n_host, n_dev, shift, mask, hist, nblocks, segs, nseg);
   cudaError_t e = exclusive_scan_u32(hist, hist_off, (int64_t)(1 << RB) * nblocks, scan_scratch, hs,
                                      scan_scratch + hs.scratch_elems - 1, st);
   if (e != cudaSuccess) return e;
   count_launch();
-  radix_downsweep_kernel<RB, ITEMS><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n_host, n_dev,
-                                                                                 shift, mask, hist_off, nblocks);
+  radix_downsweep_kernel<RB, ITEMS, SEG><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
+      ki, vi, ko, vo, n_host, n_dev, shift, mask, hist_off, nblocks, segs, nseg);
   return cudaGetLastError();
 }
 }  // namespace
@@ -326,10 +390,42 @@ cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_
     const int bits = (bit_hi - shift) < db ? (bit_hi - shift) : db;
     const uint32_t mask = (1u << bits) - 1u;
     const cudaError_t e =
-        db == 9 ? radix_pass<9, 12>(ki, vi, ko, vo, n_host, n_dev, shift, mask, hist, hist_off, scan_scratch, hs,
-                                    nblocks, st)
-                : radix_pass<8, kRadixItems>(ki, vi, ko, vo, n_host, n_dev, shift, mask, hist, hist_off,
-                                             scan_scratch, hs, nblocks, st);
+        db == 9 ? radix_pass<9, 12, false>(ki, vi, ko, vo, n_host, n_dev, shift, mask, hist, hist_off, scan_scratch,
+                                           hs, nblocks, nullptr, 0, st)
+                : radix_pass<8, kRadixItems, false>(ki, vi, ko, vo, n_host, n_dev, shift, mask, hist, hist_off,
+                                                    scan_scratch, hs, nblocks, nullptr, 0, st);
+    if (e != cudaSuccess) return e;
+    uint32_t* t;
+    t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+    *in_b = !*in_b;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t radix_sort_segments(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
+                                const SortSeg* segs, int nseg, int key_bits, uint32_t* hist, uint32_t* hist_off,
+                                unsigned long long* scan_scratch, const RadixPlan& plan, bool* in_b,
+                                cudaStream_t st) {
+  *in_b = false;
+  const int db = plan.digit_bits;
+  if (nseg == 0 || plan.nblocks == 0) return cudaSuccess;
+  uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
+  for (int shift = 0; shift < key_bits; shift += db) {
+    const int bits = (key_bits - shift) < db ? (key_bits - shift) : db;
+    const uint32_t mask = (1u << bits) - 1u;
+    cudaError_t e;
+    if (db == 7)
+      e = radix_pass<7, kRadixItems, true>(ki, vi, ko, vo, 0, nullptr, shift, mask, hist, hist_off, scan_scratch,
+                                           plan.hist_scan, plan.nblocks, segs, nseg, st);
+    else if (db == 8)
+      e = radix_pass<8, kRadixItems, true>(ki, vi, ko, vo, 0, nullptr, shift, mask, hist, hist_off, scan_scratch,
+                                           plan.hist_scan, plan.nblocks, segs, nseg, st);
+    else if (db == 9)
+      e = radix_pass<9, 12, true>(ki, vi, ko, vo, 0, nullptr, shift, mask, hist, hist_off, scan_scratch,
+                                  plan.hist_scan, plan.nblocks, segs, nseg, st);
+    else
+      return cudaErrorInvalidValue;
     if (e != cudaSuccess) return e;
     uint32_t* t;
     t = ki; ki = ko; ko = t;
@@ -430,6 +526,45 @@ cudaError_t launch_finish_count(StatusBlock* status, const uint32_t*, const uint
                                 const unsigned long long* total, int64_t capacity, cudaStream_t st) {
   count_launch();
   finish_count_kernel<<<1, 1, 0, st>>>(status, total, capacity);
+  return cudaGetLastError();
+}
+
+// The tile sort's segments: target t's overlaps are [offsets[t n], offsets[(t + 1) n]) of the
+// emitted array (the emission is target-major), clipped to the count the sort takes; each
+// segment gets the blocks its elements fill, in target order.  One thread: there are at most a
+// few hundred targets.
+__global__ void sort_segments_kernel(const uint32_t* offsets, int64_t n, int nt, const TargetCam* tcams,
+                                     const StatusBlock* status, int tile, SortSeg* segs) {
+  if (threadIdx.x != 0) return;
+  const uint32_t total = status->n_isect32;
+  uint32_t blk = 0;
+  for (int t = 0; t < nt; ++t) {
+    const uint32_t s0 = n > 0 ? min(offsets[(int64_t)t * n], total) : 0u;
+    const uint32_t s1 = (t + 1 < nt && n > 0) ? min(offsets[(int64_t)(t + 1) * n], total) : total;
+    SortSeg g;
+    g.start = s0;
+    g.len = s1 > s0 ? s1 - s0 : 0u;
+    g.blk0 = blk;
+    g.nblk = (g.len + (uint32_t)tile - 1u) / (uint32_t)tile;
+    g.key_base = (uint32_t)tcams[t].tile_base;
+    g.pad[0] = g.pad[1] = g.pad[2] = 0u;
+    segs[t] = g;
+    blk += g.nblk;
+  }
+  SortSeg e;
+  e.start = total;
+  e.len = 0u;
+  e.blk0 = blk;
+  e.nblk = 0u;
+  e.key_base = 0u;
+  e.pad[0] = e.pad[1] = e.pad[2] = 0u;
+  segs[nt] = e;
+}
+
+cudaError_t launch_sort_segments(const uint32_t* offsets, int64_t n, int nt, const TargetCam* tcams,
+                                 const StatusBlock* status, int tile, SortSeg* segs, cudaStream_t st) {
+  count_launch();
+  sort_segments_kernel<<<1, 32, 0, st>>>(offsets, n, nt, tcams, status, tile, segs);
   return cudaGetLastError();
 }
 
