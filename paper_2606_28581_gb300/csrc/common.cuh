@@ -241,50 +241,60 @@ __device__ __forceinline__ float warp_reduce16_transposed(float v[16]) {
 }
 
 // ---------------------------------------------------------------- footprint culling
-// Can the splat reach alpha >= alpha_min at a pixel centre inside [xa, xb] x [ya, yb]?
-// The support is the ellipse |Q (x - c)|^2 <= r2 united with the disc |x - c|^2 <= sigma^2 r2,
-// r2 = 2 (ln o - ln alpha_min).  The test is conservative: the radius, the rectangle and the
-// centre (its low part is ignored) carry slack far above the FP32 error of eval_pair, so
-// it never rejects a pair that eval_pair accepts.  Used for warp blocks (raster) and for
-// whole tiles (binning).
+// The support of a splat is {alpha >= alpha_min}: the ellipse |Q (x - c)|^2 <= r2 united with the
+// disc |x - c|^2 <= sigma^2 r2, r2 = 2 (ln o - ln alpha_min).  The binning keeps the tiles of a
+// splat's rectangle that the support can reach, and the rasterizer the sub-blocks of a tile; both
+// test the support conservatively, with slack far above the FP32 error of the pair evaluation,
+// so that no pair the evaluation accepts is ever dropped.
 struct CullConsts {
   float ln_amin;
   float sigma2;  // sigma^2
 };
 
-__device__ __forceinline__ float edge_min_sq(float px, float py, float qx, float qy, float len) {
-  // min over t in [0, len] of |p + t q|^2
-  const float qq = qx * qx + qy * qy;
-  float t = qq > 0.0f ? -(px * qx + py * qy) / qq : 0.0f;
-  t = fminf(fmaxf(t, 0.0f), len);
-  const float ax = fmaf(t, qx, px), ay = fmaf(t, qy, py);
-  return ax * ax + ay * ay;
-}
-
-__device__ __forceinline__ bool may_touch(const float4 g0, const float4 g1, const float4 g2, float xa, float xb,
-                                          float ya, float yb, const CullConsts& cc) {
-  xa -= 1e-3f; ya -= 1e-3f; xb += 1e-3f; yb += 1e-3f;
-  const float cx = g0.x, cy = g0.y;
-  const float nx = fminf(fmaxf(cx, xa), xb), ny = fminf(fmaxf(cy, ya), yb);
-  const float ddx = nx - cx, ddy = ny - cy;
-  if (fabsf(ddx) > fabsf(g2.y) || fabsf(ddy) > g2.z) return false;  // axis-aligned extent
-  const float r2 = fmaxf(2.0f * (g2.x - cc.ln_amin), 0.0f) * 1.001f + 1e-3f;
-  if (ddx * ddx + ddy * ddy <= r2 * cc.sigma2 * 1.001f + 1e-3f) return true;  // screen-space disc
-  if (g2.y < 0.0f) return false;                                             // degenerate: disc only
-  if (ddx == 0.0f && ddy == 0.0f) return true;                               // centre inside
-  // the ellipse: its nearest approach lies on an edge facing the centre
-  const float Q00 = g1.x, Q01 = g1.y, Q10 = g1.z, Q11 = g1.w;
-  float best = INFINITY;
-  if (ddx != 0.0f) {  // vertical edge x = nx, y in [ya, yb]
-    const float ax = nx - cx, ay = ya - cy;
-    best = fminf(best, edge_min_sq(Q00 * ax + Q01 * ay, Q10 * ax + Q11 * ay, Q01, Q11, yb - ya));
+// Slices of the support through bands of rows.  For a band of rows yl <= y - cy <= yh, range()
+// gives an x-range, relative to cx, that holds the support's slice through the band: exact for
+// the ellipse and for the disc, their union bounded by the hull of the two ranges; empty
+// (lo > hi) when the band misses both.  A convex set meets a rectangle exactly when its slice
+// through the rectangle's rows meets the rectangle's columns, so this tests a row of rectangles
+// at once.  On the ellipse's boundary at height y, x = (-A01 y +- sqrt(A00 r2 - det(Q)^2 y^2)) / A00
+// with A = Q^T Q, extreme at y = -+A01 X / A11.  Conservative: r2 is inflated by 0.2 % (far above
+// the FP32 error of the slice formulas and of the pair evaluation); callers pad the rectangles by
+// 2e-3 px (the centre's low part is ignored).  Degenerate splats (record ex < 0) have the disc only.
+struct SupportSlices {
+  float Ar2, dA, A01, iA00, Xe, Ye, yr, rd2;
+  bool ell;
+  __device__ __forceinline__ void init(const float4 g1, const float4 g2, const CullConsts& cc) {
+    const float r2 = fmaxf(2.0f * (g2.x - cc.ln_amin), 0.0f) * 1.002f + 1e-4f;
+    rd2 = r2 * cc.sigma2;
+    ell = g2.y >= 0.0f;
+    const float Q00 = g1.x, Q01 = g1.y, Q10 = g1.z, Q11 = g1.w;
+    const float A00 = Q00 * Q00 + Q10 * Q10, A11 = Q01 * Q01 + Q11 * Q11;
+    A01 = Q00 * Q01 + Q10 * Q11;
+    const float dq = fabsf(det2(Q00, Q01, Q10, Q11));
+    dA = dq * dq;
+    Ar2 = A00 * r2;
+    Xe = sqrtf(r2 * A11) / dq;  // x half-extent of the ellipse
+    Ye = sqrtf(Ar2) / dq;       // y half-extent
+    yr = -A01 * Xe / A11;       // height of the rightmost point (leftmost: -yr)
+    iA00 = 1.0f / A00;
   }
-  if (ddy != 0.0f) {  // horizontal edge y = ny, x in [xa, xb]
-    const float ax = xa - cx, ay = ny - cy;
-    best = fminf(best, edge_min_sq(Q00 * ax + Q01 * ay, Q10 * ax + Q11 * ay, Q00, Q10, xb - xa));
+  __device__ __forceinline__ void range(float yl, float yh, float& lo, float& hi) const {
+    lo = INFINITY;
+    hi = -INFINITY;
+    if (ell && yh >= -Ye && yl <= Ye) {
+      const float er = fminf(fmaxf(yr, yl), yh), el = fminf(fmaxf(-yr, yl), yh);
+      const float hr = sqrtf(fmaxf(Ar2 - dA * er * er, 0.0f)), hl = sqrtf(fmaxf(Ar2 - dA * el * el, 0.0f));
+      hi = er == yr ? Xe : (hr - A01 * er) * iA00;
+      lo = el == -yr ? -Xe : (-hl - A01 * el) * iA00;
+    }
+    const float dy = fminf(fmaxf(0.0f, yl), yh);
+    if (dy * dy <= rd2) {
+      const float hw = sqrtf(rd2 - dy * dy);
+      lo = fminf(lo, -hw);
+      hi = fmaxf(hi, hw);
+    }
   }
-  return best <= r2;
-}
+};
 
 // Host-side count of the kernels this library has launched (or captured into a graph).
 void count_launch();

@@ -245,19 +245,26 @@ __global__ void __launch_bounds__(256, 3) project_kernel(ProjectParams p) {
             mask = 0xffffffffu;
             count = (uint32_t)(ntx * nty);
           } else {
-            // exact footprint against each tile's pixel-centre rectangle
+            // per row of the rectangle, the tiles whose pixel-centre rectangles (padded by
+            // 2e-3 px) meet the support's slice through the row's pixel rows
+            constexpr float kPad = 2e-3f;
+            const float inv_tw = 1.0f / (float)p.tile_w;  // tile widths are powers of two
+            SupportSlices sl;
+            sl.init(g1, g2, p.cull);
             for (int ty = ty0; ty <= ty1; ++ty) {
-              const float ya = (float)(ty * p.tile_h) + 0.5f;
-              const float yb = (float)(min((ty + 1) * p.tile_h, cam.H) - 1) + 0.5f;
-              for (int tx = tx0; tx <= tx1; ++tx) {
-                const float xa = (float)(tx * p.tile_w) + 0.5f;
-                const float xb = (float)(min((tx + 1) * p.tile_w, cam.W) - 1) + 0.5f;
-                if (may_touch(g0, g1, g2, xa, xb, ya, yb, p.cull)) {
-                  mask |= 1u << ((ty - ty0) * ntx + (tx - tx0));
-                  ++count;
-                }
+              const float yl = ((float)(ty * p.tile_h) + 0.5f - cy) - kPad;
+              const float yh = ((float)(min((ty + 1) * p.tile_h, cam.H) - 1) + 0.5f - cy) + kPad;
+              float lo, hi;
+              sl.range(yl, yh, lo, hi);
+              // tiles tx with [tx w + 0.5, tx w + w - 0.5] - cx (padded) meeting [lo, hi]
+              const float cl = fmaxf(ceilf(((lo + cx) - 0.5f - kPad - (float)(p.tile_w - 1)) * inv_tw), (float)tx0);
+              const float ch = fminf(floorf(((hi + cx) - 0.5f + kPad) * inv_tw), (float)tx1);
+              if (cl <= ch) {
+                const int a = (int)cl - tx0, z = (int)ch - tx0;
+                mask |= ((2u << z) - (1u << a)) << ((ty - ty0) * ntx);
               }
             }
+            count = (uint32_t)__popc(mask);
           }
         }
         if (count > 0) {

@@ -199,16 +199,9 @@ __device__ __forceinline__ LaneGeom lane_geom(const TargetCam& cam, int tile, in
 }
 
 // The GL x 4 sub-blocks of a tile that a splat can reach: bit (row * TW / GL + col) is set when the
-// support {alpha >= alpha_min} can contain a pixel centre of sub-block (col, row).  The support is
-// the ellipse |Q d|^2 <= r2 united with the disc |d|^2 <= sigma^2 r2 (d = x - c,
-// r2 = 2 (ln o - ln alpha_min)).  A convex set meets a rectangle exactly when its slice through
-// the rectangle's rows meets the rectangle's columns, so per row of sub-blocks the x-range of
-// each slice is formed and compared with the columns: exact for the ellipse and for the disc,
-// their union bounded by the hull of the two ranges.  On the ellipse's boundary at height y,
-// x = (-A01 y +- sqrt(A00 r2 - det(Q)^2 y^2)) / A00 with A = Q^T Q, extreme at y = -+A01 X / A11.
-// Conservative: r2 is inflated by 0.2 % (far above the FP32 error of the slice formulas and of
-// eval_pair) and the rectangles are padded by 2e-3 px (the centre's low part is ignored).
-// Degenerate splats (record ex < 0) have the disc only.
+// support {alpha >= alpha_min} can contain a pixel centre of sub-block (col, row), tested a row of
+// sub-blocks at a time against the support's slice through its rows (SupportSlices), with the
+// sub-blocks padded by 2e-3 px.
 template <int TW, int TH, int GL>
 __device__ __forceinline__ SubMask<TW, TH, GL> subblock_mask(const float4 g0, const float4 g1, const float4 g2,
                                                             float x0, float y0, const CullConsts& cc) {
@@ -216,37 +209,15 @@ __device__ __forceinline__ SubMask<TW, TH, GL> subblock_mask(const float4 g0, co
   constexpr int SW = GL, SBX = TW / SW, SBY = TH / 4;
   constexpr float kInvSW = 1.0f / SW;
   constexpr float kPad = 2e-3f;
-  const float r2 = fmaxf(2.0f * (g2.x - cc.ln_amin), 0.0f) * 1.002f + 1e-4f;
-  const float rd2 = r2 * cc.sigma2;
-  const bool ell = g2.y >= 0.0f;
-  const float Q00 = g1.x, Q01 = g1.y, Q10 = g1.z, Q11 = g1.w;
-  const float A00 = Q00 * Q00 + Q10 * Q10, A11 = Q01 * Q01 + Q11 * Q11, A01 = Q00 * Q01 + Q10 * Q11;
-  const float dq = fabsf(det2(Q00, Q01, Q10, Q11));
-  const float dA = dq * dq;
-  const float Ar2 = A00 * r2;
-  const float Xe = sqrtf(r2 * A11) / dq;  // x half-extent of the ellipse
-  const float Ye = sqrtf(Ar2) / dq;       // y half-extent
-  const float yr = -A01 * Xe / A11;       // height of the rightmost point (leftmost: -yr)
-  const float iA00 = 1.0f / A00;
+  SupportSlices sl;
+  sl.init(g1, g2, cc);
   // tile-relative offsets: pixel centre (x0 + i + 0.5) - cx
   const float ox = x0 + 0.5f - g0.x, oy = y0 + 0.5f - g0.y;
   M mask = 0;
 #pragma unroll
   for (int b = 0; b < SBY; ++b) {
-    const float yl = oy + (float)(4 * b) - kPad, yh = oy + (float)(4 * b + 3) + kPad;
-    float lo = INFINITY, hi = -INFINITY;
-    if (ell && yh >= -Ye && yl <= Ye) {
-      const float er = fminf(fmaxf(yr, yl), yh), el = fminf(fmaxf(-yr, yl), yh);
-      const float hr = sqrtf(fmaxf(Ar2 - dA * er * er, 0.0f)), hl = sqrtf(fmaxf(Ar2 - dA * el * el, 0.0f));
-      hi = er == yr ? Xe : (hr - A01 * er) * iA00;
-      lo = el == -yr ? -Xe : (-hl - A01 * el) * iA00;
-    }
-    const float dy = fminf(fmaxf(0.0f, yl), yh);
-    if (dy * dy <= rd2) {
-      const float hw = sqrtf(rd2 - dy * dy);
-      lo = fminf(lo, -hw);
-      hi = fmaxf(hi, hw);
-    }
+    float lo, hi;
+    sl.range(oy + (float)(4 * b) - kPad, oy + (float)(4 * b + 3) + kPad, lo, hi);
     // columns c with [ox + SW c, ox + SW c + SW - 1] (padded) meeting [lo, hi]
     const float cl = fmaxf(ceilf((lo - ox - (float)(SW - 1) - kPad) * kInvSW), 0.0f);
     const float ch = fminf(floorf((hi - ox + kPad) * kInvSW), (float)(SBX - 1));
