@@ -150,15 +150,6 @@ __device__ __forceinline__ uint32_t float_order(float x) {
 // stay finite (|x - c| is bounded by the splat's extent), so w * u never forms inf * 0.
 constexpr float kDegenerateQ = 1e18f;
 
-struct PairEval {
-  float dx, dy;   // x - c
-  float u, v;     // uv coordinates (finite but meaningless for degenerate splats)
-  float alpha;    // min(alpha_max, o G^)
-  bool uwin;      // the uv Gaussian won the max (ties: uv)
-  bool clamped;   // alpha_max reached
-  bool contrib;   // alpha >= alpha_min
-};
-
 struct EvalConsts {
   float inv2s2;   // 1 / (2 sigma^2)
   float amin, amax;
@@ -180,28 +171,6 @@ __device__ __forceinline__ float rcp_ftz(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-__device__ __forceinline__ PairEval eval_pair(const float4 g0, const float4 g1, const float4 g2,
-                                              float x, float y, const EvalConsts& k) {
-  PairEval e;
-  e.dx = __fsub_rn(__fsub_rn(x, g0.x), g0.z);
-  e.dy = __fsub_rn(__fsub_rn(y, g0.y), g0.w);
-  e.u = __fmaf_rn(g1.y, e.dy, __fmul_rn(g1.x, e.dx));
-  e.v = __fmaf_rn(g1.w, e.dy, __fmul_rn(g1.z, e.dx));
-  // log2 of the two Gaussians of the lower-bounded max
-  const float pu = __fmul_rn(k.c_uv, __fmaf_rn(e.u, e.u, __fmul_rn(e.v, e.v)));
-  const float ps = __fmul_rn(k.c_xy, __fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)));
-  e.uwin = pu >= ps;  // only the backward reads it
-  const float lp = __fadd_rn(fmaxf(pu, ps), __fmul_rn(g2.x, kLog2e));  // log2(o G^) <= 0
-  // branch free: the kernels evaluate several pairs side by side.  ex2 is accurate to a few ulp,
-  // so alpha >= alpha_min decides the same as log2(o G^) >= log2(alpha_min) except within that
-  // error of the threshold, and both kernels take the decision from this same value.
-  const float og = ex2_ftz(lp);
-  e.clamped = og > k.amax;  // only the backward reads it
-  e.alpha = fminf(og, k.amax);
-  e.contrib = e.alpha >= k.amin;
-  return e;
 }
 
 // ---------------------------------------------------------------- warp reductions

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(256, 3) project_kernel(ProjectParams p) {
 // K5: chain the per-(target, splat) gradient records through the projection
 // ------------------------------------------------------------------------------------------
 template <typename Tst>
-__global__ void __launch_bounds__(256, 3) project_bwd_kernel(ProjectBwdParams p) {
+__global__ void __launch_bounds__(256, 2) project_bwd_kernel(ProjectBwdParams p) {
   __shared__ TargetCam scam[kMaxTargets];
   // the block's camera-delta and colour sums per target: d/d[B' | b'] (8) and d/dC (9)
   __shared__ float sred[kMaxTargets][17];
@@ -316,20 +316,32 @@ __global__ void __launch_bounds__(256, 3) project_bwd_kernel(ProjectBwdParams p)
   float dR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   const int64_t np = p.c.n_pad;
   const int lane = threadIdx.x & 31;
-  // the next target's tile count is loaded one target ahead, so that a target's gradient record
-  // is requested without first waiting for its count
-  uint32_t count_next = alive ? p.rect[k].w : 0u;
+  // a target's gradient record is loaded one target ahead, and its tile count two ahead, so that
+  // each request goes out a whole target's work before its use
+  const int nt = p.c.n_targets;
+  const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  auto load_rec = [&](int64_t rec, float4 (&r)[4]) {
+    const float4* gp = reinterpret_cast<const float4*>(p.grad + rec * kGradFields);
+    r[0] = gp[0]; r[1] = gp[1]; r[2] = gp[2]; r[3] = gp[3];
+  };
+  uint32_t count_cur = alive ? p.rect[k].w : 0u;
+  uint32_t count_next = (alive && nt > 1) ? p.rect[np + k].w : 0u;
+  float4 rnext[4] = {z4, z4, z4, z4};
+  if (count_cur > 0u) load_rec(k, rnext);
   for (int t = 0; t < p.c.n_targets; ++t) {
     const TargetCam& cam = scam[t];
     // per target: d/d[B' | b'] (8) and d/dC of the colour correction's 3x3 block (9)
     float dBp[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     float dC22 = 0.0f;
     const int64_t rec = (int64_t)t * np + k;
-    const bool live = count_next > 0u;  // the pair was emitted to at least one tile
-    if (alive && t + 1 < p.c.n_targets) count_next = p.rect[rec + np].w;
+    const bool live = count_cur > 0u;  // the pair was emitted to at least one tile
+    const float4 a = rnext[0], b = rnext[1], c = rnext[2], d = rnext[3];
+    if (t + 1 < nt) {
+      if (count_next > 0u) load_rec(rec + np, rnext);
+      count_cur = count_next;
+      count_next = (alive && t + 2 < nt) ? p.rect[rec + 2 * np].w : 0u;
+    }
     if (live) {
-      const float4* gp = reinterpret_cast<const float4*>(p.grad + rec * kGradFields);
-      const float4 a = gp[0], b = gp[1], c = gp[2], d = gp[3];
       const float g[16] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
       const SplatProj sp = project_one(s, cam, p.det_eps);
       // Q = M^-1: dM = -Q^T dQ Q^T

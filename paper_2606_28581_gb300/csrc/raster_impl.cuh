@@ -73,8 +73,13 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float hsum(float2 v) { return v.x + v.y; }
 
-// eval_pair (common.cuh) of one splat at two pixels (x, y.x) and (x, y.y) of one column, with
-// the same operations in the same order: bitwise the same alpha and decisions as two scalar calls.
+// Evaluation of one splat at two pixels (x, y.x) and (x, y.y) of one column (Eq. rasterization):
+// the offset from the float-pair centre, the uv coordinates u = Q (x - c), the log2 of the two
+// Gaussians of the lower-bounded max, and alpha = min(alpha_max, 2^(log2 o + log2 G^)).  Branch
+// free: the kernels evaluate several pairs side by side.  ex2 is accurate to a few ulp, so
+// alpha >= alpha_min decides the same as log2(o G^) >= log2(alpha_min) except within that error of
+// the threshold, and both kernels take every decision from this same function, so the backward
+// retraces the forward's decisions bit for bit.
 struct PairEval2 {
   float dx;                   // x - c (the two pixels share a column)
   float2 dy, u, v, alpha;
@@ -406,11 +411,12 @@ template <bool SUN, bool DIST>
 __device__ __forceinline__ uint32_t composite(FwdPair& s, const PairEval2& e, bool has, const float4& g2,
                                               const float4& f0, const float4& f1, uint32_t pos, float t_min) {
   const bool ck0 = has && !s.done0 && e.contrib0, ck1 = has && !s.done1 && e.contrib1;
-  const float2 Tn = mul2(s.T, add2(bc2(1.0f), neg2(e.alpha)));
+  // T after the splat: T - alpha T (the weight is alpha T)
+  const float2 aT = mul2(e.alpha, s.T);
+  const float2 Tn = add2(s.T, neg2(aT));
   // a splat that takes T below t_min ends the walk and is not composited
   const bool stop0 = ck0 && Tn.x < t_min, stop1 = ck1 && Tn.y < t_min;
   const bool take0 = ck0 && !stop0, take1 = ck1 && !stop1;
-  const float2 aT = mul2(e.alpha, s.T);
   const float2 w = make_float2(take0 ? aT.x : 0.0f, take1 ? aT.y : 0.0f);
   const float2 z = fma2(bc2(f0.y), e.v, fma2(bc2(f0.x), e.u, bc2(g2.w)));
   if (DIST) {
@@ -429,7 +435,7 @@ __device__ __forceinline__ uint32_t composite(FwdPair& s, const PairEval2& e, bo
     s.N1 = fma2(w, bc2(f0.w), s.N1);
     s.N2 = fma2(w, bc2(f1.x), s.N2);
   }
-  s.T = make_float2(take0 ? Tn.x : s.T.x, take1 ? Tn.y : s.T.y);
+  s.T = add2(s.T, neg2(w));  // Tn where the splat is taken, else T unchanged (w = 0)
   s.last0 = take0 ? pos : s.last0;
   s.last1 = take1 ? pos : s.last1;
   s.done0 = s.done0 || stop0;
