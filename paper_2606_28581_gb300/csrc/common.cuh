@@ -172,6 +172,12 @@ __device__ __forceinline__ float rcp_ftz(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// sqrt(x) on the MUFU unit (PTX sqrt.approx.ftz), a few ulp: the footprint tests' slack covers it.
+__device__ __forceinline__ float sqrt_ftz(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // ---------------------------------------------------------------- warp reductions
 // Transposed warp reduction of 16 values: lanes 2f and 2f + 1 end with the warp sum of field f
@@ -227,8 +233,9 @@ struct CullConsts {
 // through the rectangle's rows meets the rectangle's columns, so this tests a row of rectangles
 // at once.  On the ellipse's boundary at height y, x = (-A01 y +- sqrt(A00 r2 - det(Q)^2 y^2)) / A00
 // with A = Q^T Q, extreme at y = -+A01 X / A11.  Conservative: r2 is inflated by 0.2 % (far above
-// the FP32 error of the slice formulas and of the pair evaluation); callers pad the rectangles by
-// 2e-3 px (the centre's low part is ignored).  Degenerate splats (record ex < 0) have the disc only.
+// the FP32 error of the slice formulas, whose square roots and quotients take the MUFU
+// approximations of a few ulp, and of the pair evaluation); callers pad the rectangles by 2e-3 px
+// (the centre's low part is ignored).  Degenerate splats (record ex < 0) have the disc only.
 struct SupportSlices {
   float Ar2, dA, A01, iA00, Xe, Ye, yr, rd2;
   bool ell;
@@ -242,23 +249,24 @@ struct SupportSlices {
     const float dq = fabsf(det2(Q00, Q01, Q10, Q11));
     dA = dq * dq;
     Ar2 = A00 * r2;
-    Xe = sqrtf(r2 * A11) / dq;  // x half-extent of the ellipse
-    Ye = sqrtf(Ar2) / dq;       // y half-extent
-    yr = -A01 * Xe / A11;       // height of the rightmost point (leftmost: -yr)
-    iA00 = 1.0f / A00;
+    const float idq = rcp_ftz(dq);
+    Xe = sqrt_ftz(r2 * A11) * idq;  // x half-extent of the ellipse
+    Ye = sqrt_ftz(Ar2) * idq;       // y half-extent
+    yr = -A01 * Xe * rcp_ftz(A11);  // height of the rightmost point (leftmost: -yr)
+    iA00 = rcp_ftz(A00);
   }
   __device__ __forceinline__ void range(float yl, float yh, float& lo, float& hi) const {
     lo = INFINITY;
     hi = -INFINITY;
     if (ell && yh >= -Ye && yl <= Ye) {
       const float er = fminf(fmaxf(yr, yl), yh), el = fminf(fmaxf(-yr, yl), yh);
-      const float hr = sqrtf(fmaxf(Ar2 - dA * er * er, 0.0f)), hl = sqrtf(fmaxf(Ar2 - dA * el * el, 0.0f));
+      const float hr = sqrt_ftz(fmaxf(Ar2 - dA * er * er, 0.0f)), hl = sqrt_ftz(fmaxf(Ar2 - dA * el * el, 0.0f));
       hi = er == yr ? Xe : (hr - A01 * er) * iA00;
       lo = el == -yr ? -Xe : (-hl - A01 * el) * iA00;
     }
     const float dy = fminf(fmaxf(0.0f, yl), yh);
     if (dy * dy <= rd2) {
-      const float hw = sqrtf(rd2 - dy * dy);
+      const float hw = sqrt_ftz(rd2 - dy * dy);
       lo = fminf(lo, -hw);
       hi = fmaxf(hi, hw);
     }
