@@ -163,7 +163,9 @@ struct TileStage {
   float4 g[stage_bufs<B>()][B][3];
   float4 f[stage_bufs<B>()][B][2];
   uint32_t k[stage_bufs<B>()][B];
-  M mask[B];
+  // per sub-block of the tile, its candidate masks of the batch's 32-entry chunks (rows padded
+  // by a word so that a warp's stores of one chunk fall in different banks)
+  uint32_t words[8 * sizeof(M)][B / 32 + 1];
   uint8_t list[32 / GL * NW][B + 4];  // per group its candidates' slots (buffer * B + index); rows
                                         // padded so that the groups read at one position from
                                         // different banks
@@ -234,27 +236,35 @@ __device__ __forceinline__ SubMask<TW, TH, GL> subblock_mask(const float4 g0, co
   return mask;
 }
 
-// Candidate masks of a staged batch: lane gl of a group ends with the group's masks of chunks
-// gl, gl + GL, ... (staged splats [32 c, 32 c + 32)).  Holding every chunk at once lets a
-// group walk its candidates across chunk boundaries.
-template <int TW, int TH, int B, int GL>
-__device__ __forceinline__ void batch_masks(const SubMask<TW, TH, GL>* smask, int nb, int half,
+// Candidate masks of a staged batch: lane gl of a group reads the group's masks of chunks
+// gl, gl + GL, ... (staged splats [32 c, 32 c + 32)).  Holding every chunk at once lets a group
+// walk its candidates across chunk boundaries.
+template <int B, int GL, int ROWS>
+__device__ __forceinline__ void batch_masks(const uint32_t (&words)[ROWS][B / 32 + 1], int sub,
                                             uint32_t (&mk)[mask_chunks<B, GL>()]) {
   static_assert(B % 32 == 0 && B / 32 <= GL * mask_chunks<B, GL>(), "chunks per lane of a group");
-  const int lane = threadIdx.x & 31, grp = lane / GL, gl = lane % GL;
+  const int gl = threadIdx.x % GL;
 #pragma unroll
-  for (int q = 0; q < mask_chunks<B, GL>(); ++q) mk[q] = 0u;
-#pragma unroll
-  for (int c = 0; c < B / 32; ++c) {
-    if (c * 32 >= nb) break;  // block-uniform
-    const int i = c * 32 + lane;
-    const SubMask<TW, TH, GL> v = i < nb ? smask[i] : 0u;
-#pragma unroll
-    for (int gg = 0; gg < 32 / GL; ++gg) {
-      const uint32_t m = __ballot_sync(0xffffffffu, (uint32_t)(v >> group_sub<TW, TH, GL>(half, gg)) & 1u);
-      if (grp == gg && gl == c % GL) mk[c / GL] = m;
-    }
+  for (int q = 0; q < mask_chunks<B, GL>(); ++q) {
+    const int c = q * GL + gl;
+    mk[q] = c < B / 32 ? words[sub][c] : 0u;
   }
+}
+
+// Transpose of a 32 x 32 bit matrix held one row per lane (bit c of lane r's word is entry
+// (r, c)): returns column `lane`.  Each level swaps the off-diagonal blocks of every 2j x 2j block,
+// from j = 16 down to 1.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+  constexpr uint32_t kLo[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    const int j = 16 >> l;
+    const uint32_t lo = kLo[l];  // the columns c with c & j == 0
+    const uint32_t t = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? (((t >> j) & lo) | (x & ~lo)) : ((x & lo) | ((t << j) & ~lo));
+  }
+  return x;
 }
 
 // Writes a group's candidates of a staged batch (the set bits of its chunk masks) to the group's
@@ -330,19 +340,27 @@ __device__ __forceinline__ void stage_issue(TileStage<B, NW, M, GL>& S, int buf,
   cp_async_commit();
 }
 
-// Sub-block masks of a landed batch: each thread reads the records it copied itself (before the
-// barrier that publishes copies and masks to the block).
+// Sub-block masks of a landed batch: each thread forms the masks of the records it copied itself
+// (before the barrier that publishes copies and masks to the block).  A warp's records of one pass
+// are one 32-entry chunk, one record per lane, so transposing the warp's masks as a bit matrix gives
+// lane s the chunk's candidate mask of sub-block s.
 template <int TW, int TH, int B, int NW, int GL>
 __device__ __forceinline__ void stage_masks(TileStage<B, NW, SubMask<TW, TH, GL>, GL>& S, int buf, int nb,
-                                            const LaneGeom& lg,
-                                            const RasterParams& p) {
+                                            const LaneGeom& lg, const RasterParams& p) {
+  using M = SubMask<TW, TH, GL>;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int c = 0; c < per_thread<B, 32 * NW>(); ++c) {
     const int i = c * (32 * NW) + threadIdx.x;
+    const int chunk = i >> 5;  // the same for the whole warp
+    if (chunk >= B / 32) break;
+    M m = 0;
     if (i < nb)
-      S.mask[i] = p.subblock_cull ? subblock_mask<TW, TH, GL>(S.g[buf][i][0], S.g[buf][i][1], S.g[buf][i][2], lg.x0,
-                                                          lg.y0, p.cull)
-                                  : ~SubMask<TW, TH, GL>(0);
+      m = p.subblock_cull ? subblock_mask<TW, TH, GL>(S.g[buf][i][0], S.g[buf][i][1], S.g[buf][i][2], lg.x0, lg.y0,
+                                                     p.cull)
+                          : ~M(0);
+    S.words[lane][chunk] = warp_transpose32((uint32_t)m);
+    if (sizeof(M) == 8) S.words[32 + lane][chunk] = warp_transpose32((uint32_t)((unsigned long long)m >> 32));
   }
 }
 
@@ -510,7 +528,7 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), 16 / tile_warps<TW,
       stage_masks<TW, TH, B, NW, GL>(S, buf, nb, lg, p);
       __syncthreads();  // every thread's copies and masks of this batch are visible to the block
       uint32_t mk[mask_chunks<B, GL>()];
-      batch_masks<TW, TH, B, GL>(S.mask, nb, half, mk);
+      batch_masks<B, GL>(S.words, lg.sub, mk);
       // a group whose 16 pixels have all stopped walks nothing
       constexpr uint32_t kGroupBits = (1u << GL) - 1u;
       if (((__ballot_sync(0xffffffffu, all_done) >> (lane & ~(GL - 1))) & kGroupBits) == kGroupBits) {
@@ -790,7 +808,7 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
       stage_masks<TW, TH, B, NW, GL>(S, buf, nb, lg, p);
       __syncthreads();  // every thread's copies and masks of this batch are visible to the block
       uint32_t mk[mask_chunks<B, GL>()];
-      batch_masks<TW, TH, B, GL>(S.mask, nb, half, mk);
+      batch_masks<B, GL>(S.words, lg.sub, mk);
 #pragma unroll
       for (int q = 0; q < mask_chunks<B, GL>(); ++q) {
         // candidates at or after the group's last walked position are not walked
