@@ -802,7 +802,8 @@ def run_ours(args, dist):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD_TEXT[args.workload], "n_splats": scene.n, "views": len(cams),
                            "main_pixels_per_gpu": main_px, "sun_pixels_per_gpu": sun_px,
-                           "storage": args.storage, "tile": f"{opts.tile_w}x{opts.tile_h}", "batch": opts.batch,
+                           "storage": args.storage, "tile": f"{opts.tile_w}x{opts.tile_h}",
+                           "batch": "{} records per staged batch (forward), {} (backward)".format(*L.staging_batches()),
                            "pixels_per_thread": opts.pixels_per_thread,
                            "launch": "two CUDA graphs per step (forward part, backward part); persistent forward and backward launches over "
                                      "all (target, tile) items",

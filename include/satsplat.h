@@ -111,8 +111,9 @@ typedef struct {
 typedef struct {
   int32_t tile_w, tile_h; /* screen tile [16 x 16]; also 32 x 8, 8 x 32 (two warps per tile) and
                              32 x 16, 16 x 32 (four warps per tile) */
-  int32_t batch;          /* splats a tile block stages in shared memory per batch [256], the
-                             only value; the block copies each batch with cp.async */
+  int32_t batch;          /* [256], the only value: the kernels' own staging, in which a tile
+                             block copies the tile's sorted splat records into shared memory with
+                             cp.async in batches (ss_staging_batches gives their sizes) */
   int32_t persistent;     /* [0] one block (one warp per 128 pixels) per tile; 1: one persistent
                              launch whose blocks pull tiles from a queue */
   float sigma_px;         /* screen-space low-pass sigma, pixels [1/sqrt(2)] */
@@ -121,8 +122,8 @@ typedef struct {
   float alpha_max;        /* alpha = min(alpha_max, o G^) [0.99] */
   float t_min;            /* stop before the splat that takes T below t_min [1e-4] */
   int32_t pixels_per_thread; /* [4], the only value: each lane owns one column of four pixels
-                                of a sub-block (4 x 4 in the forward, 2 x 4 in the backward).
-                                Tile shape, batch and persistence never change an output. */
+                                of a 2 x 4 sub-block.  Tile shape, batch and persistence never
+                                change an output. */
   int32_t subblock_cull;  /* [1] each group of lanes walks only the staged splats whose support
                              can reach its sub-block; 0 walks every staged splat in every
                              sub-block.  The outputs are identical (the test is conservative);
@@ -187,6 +188,11 @@ void ss_default_opts(ss_raster_opts* opts);
 
 /* Human-readable name of a status code (static storage). */
 const char* ss_status_string(ss_status status);
+
+/* Records per staged batch of the forward (ss_rasterize_fwd) and the backward
+ * (ss_rasterize_bwd) rasterizer kernels, for reports.  Either pointer may be
+ * NULL.  Never fails; host only. */
+void ss_staging_batches(int32_t* fwd, int32_t* bwd);
 
 /* Bytes of device workspace a frame needs, for an intersection-list capacity
  * of `capacity` (tile, splat) pairs over all targets.  The workspace holds the

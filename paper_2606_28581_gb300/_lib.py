@@ -95,7 +95,7 @@ class ss_mcmc_opts(ctypes.Structure):
                 ("step", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
-EXPORTS = ["ss_default_opts", "ss_status_string", "ss_workspace_size", "ss_project_splats",
+EXPORTS = ["ss_default_opts", "ss_status_string", "ss_staging_batches", "ss_workspace_size", "ss_project_splats",
            "ss_bin_and_sort", "ss_rasterize_fwd", "ss_rasterize_bwd", "ss_project_bwd", "ss_shadow_depth",
            "ss_frame_status", "ss_device_info", "ss_kernel_launches", "ss_render_fwd_noalloc",
            "ss_noalloc_scratch_bytes", "ss_default_shade_opts", "ss_shade_fwd", "ss_shade_bwd",
@@ -131,6 +131,8 @@ def load(path: Optional[str] = None):
         L.ss_default_opts.restype = None
         L.ss_status_string.argtypes = [ctypes.c_int]
         L.ss_status_string.restype = ctypes.c_char_p
+        L.ss_staging_batches.argtypes = [ctypes.POINTER(I32), ctypes.POINTER(I32)]
+        L.ss_staging_batches.restype = None
         L.ss_workspace_size.argtypes = [PS, PC, I32, I32, PO, I64, ctypes.POINTER(SZ)]
         L.ss_project_splats.argtypes = [PS, PC, I32, I32, P, P, PO, P, SZ, I64, P]
         L.ss_bin_and_sort.argtypes = [PS, PC, I32, I32, PO, P, SZ, I64, ctypes.POINTER(I64), P]
@@ -170,12 +172,20 @@ def load(path: Optional[str] = None):
         L.ss_init_workspace_size.argtypes = [PD, I64, ctypes.POINTER(SZ)]
         L.ss_dsm_init.argtypes = [PD, PIN, PS, P, SZ, P]
         for name in EXPORTS:
-            if name not in ("ss_default_opts", "ss_status_string", "ss_device_info", "ss_kernel_launches",
+            if name not in ("ss_default_opts", "ss_status_string", "ss_staging_batches", "ss_device_info",
+                            "ss_kernel_launches",
                             "ss_noalloc_scratch_bytes", "ss_default_shade_opts", "ss_default_adam_opts",
                             "ss_default_mcmc_opts", "ss_default_init_opts"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
+
+
+def staging_batches() -> tuple:
+    """Records per staged batch of the forward and the backward rasterizer kernels."""
+    f, b = ctypes.c_int32(0), ctypes.c_int32(0)
+    load().ss_staging_batches(ctypes.byref(f), ctypes.byref(b))
+    return f.value, b.value
 
 
 def status_string(status: int) -> str:

@@ -321,6 +321,11 @@ void ss_default_opts(ss_raster_opts* o) {
   o->count_pairs = 0;
 }
 
+void ss_staging_batches(int32_t* fwd, int32_t* bwd) {
+  if (fwd) *fwd = ss::kFwdBatch;
+  if (bwd) *bwd = ss::kBwdBatch;
+}
+
 const char* ss_status_string(ss_status s) {
   switch (s) {
     case SS_OK: return "ok";

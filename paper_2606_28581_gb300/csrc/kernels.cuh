@@ -72,6 +72,15 @@ struct BinParams {
 };
 
 // Rasterization (K3 / K4) ----------------------------------------------------------------
+// Staging and grouping of the rasterizer (raster_impl.cuh).  Both directions walk 2 x 4 pixel
+// sub-blocks, one per group of two lanes: on the 16-view workload they evaluate 1.41 pairs per
+// walked pair where 4 x 4 sub-blocks evaluate 1.66, at the price (in the backward) of two L2 vector
+// reductions per lane and step instead of one.  The forward stages batches of 192 records and the
+// backward of 224: with their candidate lists they leave eight blocks per SM, and larger batches
+// measured no faster.
+constexpr int kFwdBatch = 192, kFwdGroupLanes = 2;
+constexpr int kBwdBatch = 224, kBwdGroupLanes = 2;
+
 struct RasterParams {
   const TargetCam* tcams;
   const float4* geom;

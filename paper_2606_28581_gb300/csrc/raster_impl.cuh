@@ -2,14 +2,13 @@
 //
 // Work decomposition.  A screen tile (16 x 16, 32 x 8, 8 x 32, 32 x 16 or 16 x 32 px) is rendered
 // by one block of one warp per 128 pixels (a 16 x 8 part, or 8 x 16 in 8-wide tiles).  A warp's
-// pixels are split into sub-blocks of GL columns by 4 rows, one per group of GL lanes: 4 x 4 in the
-// forward (eight groups of four lanes), 2 x 4 in the backward (sixteen groups of two).  Lane l of
-// a group owns column l of its sub-block, four pixels, kept as two pairs (rows 0-1 and 2-3) so
-// that the paired FP32 instructions of sm_100-family GPUs compute two pixels in one issue.  The
-// block stages the tile's sorted splat list in shared memory in batches of 256 records copied
-// with cp.async (the next batch's splat indices are loaded while a batch is walked); large
-// batches keep the groups of a warp, which walk their own candidate lists in lockstep, evenly
-// loaded.
+// pixels are split into sub-blocks of GL columns by 4 rows, one per group of GL lanes (GL = 2 in
+// both directions, kernels.cuh: sixteen groups per warp).  Lane l of a group owns column l of its
+// sub-block, four pixels, kept as two pairs (rows 0-1 and 2-3) so that the paired FP32
+// instructions of sm_100-family GPUs compute two pixels in one issue.  The block stages the tile's
+// sorted splat list in shared memory in batches of records copied with cp.async (the next batch's
+// splat indices are loaded while a batch is walked); large batches keep the groups of a warp,
+// which walk their own candidate lists in lockstep, evenly loaded.
 //
 // The thread that stages a splat forms the set of the tile's sub-blocks its support can reach
 // (`subblock_mask`); each group walks only the staged splats that reach its sub-block, in list
@@ -45,13 +44,6 @@ __host__ __device__ constexpr int tile_subblocks() { return TW * TH / (4 * GL); 
 // A tile's sub-block mask: one bit per sub-block.
 template <int TW, int TH, int GL>
 using SubMask = std::conditional_t<(tile_subblocks<TW, TH, GL>() > 32), unsigned long long, uint32_t>;
-// Staging and grouping of each direction.  Both stage batches of 256 records.  The forward walks
-// 4 x 4 sub-blocks (groups of four lanes).  The backward walks 2 x 4 sub-blocks (groups of two
-// lanes): on the 16-view workload they evaluate 1.41 pairs per walked pair against 1.66, at the
-// price of two L2 vector reductions per lane and step instead of one.  The forward, whose step has
-// no reduction, measured no faster with the finer grain.
-constexpr int kFwdBatch = 256, kFwdGroupLanes = 4;
-constexpr int kBwdBatch = 256, kBwdGroupLanes = 2;
 
 __device__ __forceinline__ int find_target(const TargetCam* tc, int n_targets, int tile) {
   int lo = 0, hi = n_targets - 1;
@@ -938,8 +930,9 @@ cudaError_t launch_bwd_t(const RasterParams& p, bool persistent, int num_sms, cu
   return launch_items(raster_bwd_kernel<TW, TH, B, GL, false, DIST>, NT, p, false, num_sms, per_sm, st);
 }
 
-// Instantiates the launchers of one tile shape (batches of 256 staged splats per block), with and
-// without the distortion, and (forward) with and without the walked-pair count.
+// Instantiates the launchers of one tile shape (the staging of kernels.cuh; the options' batch of
+// 256 selects it), with and without the distortion, and (forward) with and without the
+// walked-pair count.
 #define SS_RASTER_FWD_DISPATCH(TW, TH)                                                                      \
   cudaError_t launch_raster_fwd_##TW##x##TH(const RasterParams& p, int batch, bool persistent, int num_sms, \
                                             cudaStream_t st) {                                              \
