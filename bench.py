@@ -668,7 +668,8 @@ def run_ours(args, dist):
     flops = {"rasterize_fwd": walked * FLOPS_FWD_PER_PAIR, "rasterize_bwd": walked * FLOPS_BWD_PER_PAIR}
     dom = max(("rasterize_fwd", "rasterize_bwd"), key=lambda k: phase_ms[k])
     achieved = flops[dom] / (phase_ms[dom] * 1e-3) / 1e12
-    traffic = profiles_traffic("raster_bwd") if dom == "rasterize_bwd" else None
+    # the committed per-launch traffic is scaled to the 16-view batched step
+    traffic = profiles_traffic("raster_bwd") if dom == "rasterize_bwd" and args.workload == "batched" else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "flops_per_launch": flops[dom], "walked_pairs": walked,
