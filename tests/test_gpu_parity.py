@@ -248,6 +248,28 @@ def test_batched_frame_equals_single_view_calls():
         assert torch.equal(out.depth[3 + c], o1.depth[1]) and torch.equal(out.alpha[3 + c], o1.alpha[1])
 
 
+def test_targets_without_overlaps_between_others():
+    """The tile sort orders each target's overlaps on its own: a view (and its sun view) that sees
+    no splat, between views that do, leaves empty segments that change nothing elsewhere."""
+    scene = scenegen.make_scene(n=2500, extent_m=80.0, seed=14, views=[
+        dict(width=96, height=64, off_nadir=10.0, delta=True, color_noise=0.02),
+        dict(width=70, height=90, off_nadir=25.0, delta=True, color_noise=0.02),
+        dict(width=128, height=40, off_nadir=15.0, delta=True)])
+    scene.cameras[1].F_xy[0, 3] += np.float32(1e5)  # the middle view looks far off the scene
+    ds = DeviceScene(scene)
+    frame, out = run_forward(ds, passes=3, opts=L.default_opts(persistent=1))
+    assert torch.all(out.alpha[1] == 0) and torch.all(out.alpha[4] == 0)
+    for c in (0, 2):
+        sub = DeviceScene(scene)
+        sub.dF = ds.dF[c:c + 1].contiguous()
+        sub.color = ds.color[c:c + 1].contiguous()
+        _, o1 = run_forward(sub, passes=3, cams=[scene.cameras[c]])
+        assert torch.any(o1.alpha[0] > 0)
+        for k in ("rgb", "depth", "normal", "alpha"):
+            assert torch.equal(getattr(out, k)[c], getattr(o1, k)[0]), (c, k)
+        assert torch.equal(out.depth[3 + c], o1.depth[1]) and torch.equal(out.alpha[3 + c], o1.alpha[1])
+
+
 def test_capacity_overflow_is_reported_and_recovered():
     scene = ragged_scene(seed=8)
     ds = DeviceScene(scene)
