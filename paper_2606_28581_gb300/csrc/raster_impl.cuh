@@ -106,7 +106,9 @@ __device__ __forceinline__ PairEval2 eval_pair2(const float4 g0, const float4 g1
 // Transposed reduction of 16 values over the lanes of a group: lane gl of the group ends with the
 // group sums of fields F gl .. F gl + F - 1 (F = 16 / GL) in v[0 .. F - 1].  Each exchange
 // sends the half of the values that the partner keeps (8 shuffles for two lanes, 12 for four).
-template <int GL>
+// LOW12: only fields 0 .. 11 are wanted (a sun view's fields 12 .. 15 are zero and not added);
+// with two lanes, the upper lane's slots for fields 12 .. 15 then need no exchange of their own.
+template <int GL, bool LOW12 = false>
 __device__ __forceinline__ void group_reduce16(float v[16]) {
   static_assert(GL == 2 || GL == 4, "groups of two or four lanes");
   const int lane = threadIdx.x & 31;
@@ -115,6 +117,10 @@ __device__ __forceinline__ void group_reduce16(float v[16]) {
     const bool up = lane & s;
 #pragma unroll
     for (int i = 0; i < n / 2; ++i) {
+      if (LOW12 && GL == 2 && i >= 4) {
+        v[i] += __shfl_xor_sync(0xffffffffu, v[i], s);  // the lower lane's field i
+        continue;
+      }
       const float send = up ? v[i] : v[i + n / 2];
       const float keep = up ? v[i + n / 2] : v[i];
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
@@ -707,7 +713,7 @@ __device__ __forceinline__ BwdTerms bwd_pair(BwdPair& s, const PairEval2& e, uin
   const float2 dpa = mul2(fma2(Ti, gs, mul2(s.gAlT, rom)), a);
   r.dpw = make_float2(e.clamped0 ? 0.0f : dpa.x, e.clamped1 ? 0.0f : dpa.y);
   const float2 dpu = make_float2(e.uwin0 ? r.dpw.x : 0.0f, e.uwin1 ? r.dpw.y : 0.0f);
-  r.dps = mul2(make_float2(e.uwin0 ? 0.0f : r.dpw.x, e.uwin1 ? 0.0f : r.dpw.y), bc2(two_inv2s2));
+  r.dps = mul2(add2(r.dpw, neg2(dpu)), bc2(two_inv2s2));  // dpw - dpu is exact: dpw or 0
   // degenerate splats: zero slopes, and dpu = 0 except at u = v = 0
   r.du = fma2(r.dz, bc2(f0.x), neg2(mul2(dpu, e.u)));
   r.dv = fma2(r.dz, bc2(f0.y), neg2(mul2(dpu, e.v)));
@@ -856,7 +862,7 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
           const bool any = cA0 || cA1 || cB0 || cB1;
           constexpr uint32_t kGroupBits = (1u << GL) - 1u;
           const bool gany = ((__ballot_sync(0xffffffffu, any) >> (lane & ~(GL - 1))) & kGroupBits) != 0u;
-          group_reduce16<GL>(v);
+          group_reduce16<GL, SUN>(v);
           constexpr int F = 16 / GL;  // fields summed by each lane
           float* dst = p.grad + (recbase + kk) * kGradFields + F * gl;
 #pragma unroll
