@@ -53,14 +53,30 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
   return r;
 }
 
+// A thread's kScanItems consecutive elements: two 16-byte loads for a 32-bit input that starts
+// 16-byte aligned when all of them are in range, else element by element.
+template <typename Tin>
+__device__ __forceinline__ void scan_load(const Tin* in, int64_t base, int64_t n, unsigned long long (&v)[kScanItems]) {
+  if (sizeof(Tin) == 4 && base + kScanItems <= n && (reinterpret_cast<uintptr_t>(in) & 15u) == 0) {
+    static_assert(kScanItems == 8, "two 16-byte loads per thread");
+    const uint4 a = reinterpret_cast<const uint4*>(in + base)[0], b = reinterpret_cast<const uint4*>(in + base)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) v[i] = (base + i < n) ? (unsigned long long)in[base + i] : 0ull;
+  }
+}
+
 template <typename Tin>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const Tin* in, int64_t n,
                                                                     unsigned long long* sums) {
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  unsigned long long v[kScanItems];
+  scan_load(in, base, n, v);
   unsigned long long s = 0;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i)
-    if (base + i < n) s += (unsigned long long)in[base + i];
+  for (int i = 0; i < kScanItems; ++i) s += v[i];
   __shared__ unsigned long long tot;
   (void)block_exclusive_scan(s, &tot);
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
@@ -72,16 +88,27 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const Tin* in, 
                                                                   unsigned long long* total) {
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   unsigned long long v[kScanItems];
+  scan_load(in, base, n, v);
   unsigned long long s = 0;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    v[i] = (base + i < n) ? (unsigned long long)in[base + i] : 0ull;
-    s += v[i];
-  }
+  for (int i = 0; i < kScanItems; ++i) s += v[i];
   __shared__ unsigned long long tot;
   unsigned long long run = block_exclusive_scan(s, &tot);
   if (offs) run += offs[blockIdx.x];
   else if (threadIdx.x == 0 && total) *total = tot;
+  if (sizeof(Tout) == 4 && base + kScanItems <= n && (reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+    // two 16-byte stores of the saturated 32-bit prefixes
+    uint32_t o[kScanItems];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      o[i] = (uint32_t)(run > 0xffffffffull ? 0xffffffffull : run);
+      run += v[i];
+    }
+    uint4* dst = reinterpret_cast<uint4*>(out + base);
+    dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     if (base + i < n) {
