@@ -47,6 +47,15 @@ def test_default_opts_and_status_strings(lib):
     assert L.status_string(L.SS_ERR_CAPACITY) == "intersection capacity exceeded"
 
 
+def test_staging_batches_fit_the_kernels_slot_encoding(lib):
+    """The rasterizer's staged batches: whole 32-record chunks (the candidate masks) and at most
+    256 records (a candidate's slot is one byte)."""
+    from paper_2606_28581_gb300 import _lib as L
+    fwd, bwd = L.staging_batches()
+    for b in (fwd, bwd):
+        assert 32 <= b <= 256 and b % 32 == 0, b
+
+
 def test_workspace_size_validates_on_the_host(lib):
     import scenegen
     from paper_2606_28581_gb300 import _lib as L
