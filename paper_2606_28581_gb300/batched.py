@@ -10,8 +10,9 @@ status block, which the host reads after a replay (``check``).  From host
 buffers (``replay_from_host``) the upstream gradients are copied on a side
 stream while the forward part runs, and only the backward part waits for them.
 
-The autotuner times the candidate tile shapes and per-block splat batches on
-the actual workload and caches the winner per (GPU, workload) in a JSON file.
+The autotuner times the candidate tile shapes (each with the kernels' own staging,
+which the options' batch of 256 selects) on the actual workload and caches the
+winner per (GPU, workload) in a JSON file.
 """
 from __future__ import annotations
 
