@@ -512,14 +512,32 @@ __global__ void emit_kernel(BinParams p) {
   const uint4 rc = p.rect[t * p.n_pad + k];
   if (rc.w == 0u) return;
   const int x0 = (int)(rc.x & 0xffffu), y0 = (int)(rc.x >> 16), x1 = (int)(rc.y & 0xffffu), y1 = (int)(rc.y >> 16);
+  const int ntx = x1 - x0 + 1, nty = y1 - y0 + 1;
   const TargetCam& cam = p.tcams[t];
   int64_t pos = p.offsets[idx];
-  int bit = 0;
-  for (int ty = y0; ty <= y1; ++ty) {
-    for (int tx = x0; tx <= x1; ++tx, ++bit) {
-      if (bit < 32 && !((rc.z >> bit) & 1u)) continue;
+  uint32_t row_key = (uint32_t)(cam.tile_base + y0 * cam.tiles_x + x0);
+  if (ntx * nty <= 32) {
+    // the kept tiles only: each row's bits of the mask, lowest first
+    uint32_t m = rc.z;
+    const uint32_t row_bits = ntx >= 32 ? 0xffffffffu : ((1u << ntx) - 1u);
+    for (int r = 0; r < nty && m != 0u; ++r, row_key += (uint32_t)cam.tiles_x) {
+      uint32_t b = m & row_bits;
+      m = ntx >= 32 ? 0u : m >> ntx;
+      while (b != 0u) {
+        const int c = __ffs(b) - 1;
+        b &= b - 1u;
+        if (pos >= p.capacity) return;
+        p.keys[pos] = row_key + (uint32_t)c;
+        p.vals[pos] = k;
+        ++pos;
+      }
+    }
+    return;
+  }
+  for (int ty = 0; ty < nty; ++ty, row_key += (uint32_t)cam.tiles_x) {
+    for (int tx = 0; tx < ntx; ++tx) {
       if (pos >= p.capacity) return;
-      p.keys[pos] = (uint32_t)(cam.tile_base + ty * cam.tiles_x + tx);
+      p.keys[pos] = row_key + (uint32_t)tx;
       p.vals[pos] = k;
       ++pos;
     }
