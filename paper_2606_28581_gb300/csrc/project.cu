@@ -299,8 +299,11 @@ __global__ void __launch_bounds__(256, 3) project_kernel(ProjectParams p) {
 // ------------------------------------------------------------------------------------------
 // K5: chain the per-(target, splat) gradient records through the projection
 // ------------------------------------------------------------------------------------------
-template <typename Tst>
-__global__ void __launch_bounds__(256, 2) project_bwd_kernel(ProjectBwdParams p) {
+// AHEAD: each target's gradient record is loaded one target ahead, at two blocks per SM (the
+// registers it takes); without it, three blocks per SM load each record in its own iteration,
+// which suits frames of few targets.
+template <typename Tst, bool AHEAD>
+__global__ void __launch_bounds__(256, AHEAD ? 2 : 3) project_bwd_kernel(ProjectBwdParams p) {
   __shared__ TargetCam scam[kMaxTargets];
   // the block's camera-delta and colour sums per target: d/d[B' | b'] (8) and d/dC (9)
   __shared__ float sred[kMaxTargets][17];
@@ -316,8 +319,8 @@ __global__ void __launch_bounds__(256, 2) project_bwd_kernel(ProjectBwdParams p)
   float dR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   const int64_t np = p.c.n_pad;
   const int lane = threadIdx.x & 31;
-  // a target's gradient record is loaded one target ahead, and its tile count two ahead, so that
-  // each request goes out a whole target's work before its use
+  // with AHEAD a target's gradient record is loaded one target ahead; its tile count is loaded two
+  // ahead, so that each request goes out before its use
   const int nt = p.c.n_targets;
   const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   auto load_rec = [&](int64_t rec, float4 (&r)[4]) {
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(256, 2) project_bwd_kernel(ProjectBwdParams p)
   uint32_t count_cur = alive ? p.rect[k].w : 0u;
   uint32_t count_next = (alive && nt > 1) ? p.rect[np + k].w : 0u;
   float4 rnext[4] = {z4, z4, z4, z4};
-  if (count_cur > 0u) load_rec(k, rnext);
+  if (AHEAD && count_cur > 0u) load_rec(k, rnext);
   for (int t = 0; t < p.c.n_targets; ++t) {
     const TargetCam& cam = scam[t];
     // per target: d/d[B' | b'] (8) and d/dC of the colour correction's 3x3 block (9)
@@ -335,9 +338,10 @@ __global__ void __launch_bounds__(256, 2) project_bwd_kernel(ProjectBwdParams p)
     float dC22 = 0.0f;
     const int64_t rec = (int64_t)t * np + k;
     const bool live = count_cur > 0u;  // the pair was emitted to at least one tile
+    if (!AHEAD && live) load_rec(rec, rnext);
     const float4 a = rnext[0], b = rnext[1], c = rnext[2], d = rnext[3];
     if (t + 1 < nt) {
-      if (count_next > 0u) load_rec(rec + np, rnext);
+      if (AHEAD && count_next > 0u) load_rec(rec + np, rnext);
       count_cur = count_next;
       count_next = (alive && t + 2 < nt) ? p.rect[rec + 2 * np].w : 0u;
     }
@@ -506,12 +510,17 @@ cudaError_t launch_project(const ProjectParams& p, int dtype, cudaStream_t st) {
 cudaError_t launch_project_bwd(const ProjectBwdParams& p, int dtype, cudaStream_t st) {
   const int64_t nb = (p.c.n + 255) / 256;
   if (nb == 0) return cudaSuccess;
+  // records loaded a target ahead pay off over many targets (0.69 -> 0.53 ms at 32 targets); with
+  // two (a view and its sun view) the occupancy they cost weighs more (0.069 -> 0.080 ms)
+  const bool ahead = p.c.n_targets > 4;
   if (dtype == SS_BF16) {
     count_launch();
-    project_bwd_kernel<__nv_bfloat16><<<(unsigned)nb, 256, 0, st>>>(p);
+    if (ahead) project_bwd_kernel<__nv_bfloat16, true><<<(unsigned)nb, 256, 0, st>>>(p);
+    else project_bwd_kernel<__nv_bfloat16, false><<<(unsigned)nb, 256, 0, st>>>(p);
   } else {
     count_launch();
-    project_bwd_kernel<float><<<(unsigned)nb, 256, 0, st>>>(p);
+    if (ahead) project_bwd_kernel<float, true><<<(unsigned)nb, 256, 0, st>>>(p);
+    else project_bwd_kernel<float, false><<<(unsigned)nb, 256, 0, st>>>(p);
   }
   return cudaGetLastError();
 }
