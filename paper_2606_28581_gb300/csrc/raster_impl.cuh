@@ -748,6 +748,8 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
     const uint2 range = p.ranges[tile];
     const int64_t recbase = (int64_t)t * p.n_pad;
     const TargetIO& io = p.io[t];
+    // this lane's fields of the target's gradient records
+    float* const gtile = p.grad + recbase * kGradFields + (16 / GL) * gl;
     const int64_t hw = (int64_t)cam.W * cam.H;
     const bool inx = lg.px < cam.W;
     BwdPair sA, sB;
@@ -864,7 +866,7 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
           const bool gany = ((__ballot_sync(0xffffffffu, any) >> (lane & ~(GL - 1))) & kGroupBits) != 0u;
           group_reduce16<GL, SUN>(v);
           constexpr int F = 16 / GL;  // fields summed by each lane
-          float* dst = p.grad + (recbase + kk) * kGradFields + F * gl;
+          float* dst = gtile + (size_t)kk * kGradFields;
 #pragma unroll
           for (int r = 0; r < F / 4; ++r) {
             // a sun view's fields 12 .. 15 (normal z, colour) are zero
