@@ -861,16 +861,15 @@ __global__ void __launch_bounds__(32 * tile_warps<TW, TH>(), (DIST ? 12 : 16) / 
           v[GF_Q11] = hsum(fma2(rB.dv, eB.dy, mul2(rA.dv, eA.dy)));
           v[GF_CX] = hsum(add2(rA.dps, rB.dps)) * dx - (g1.x * sdu + g1.z * sdv);
           v[GF_CY] = hsum(fma2(rB.dps, eB.dy, mul2(rA.dps, eA.dy))) - (g1.y * sdu + g1.w * sdv);
-          const bool any = cA0 || cA1 || cB0 || cB1;
-          constexpr uint32_t kGroupBits = (1u << GL) - 1u;
-          const bool gany = ((__ballot_sync(0xffffffffu, any) >> (lane & ~(GL - 1))) & kGroupBits) != 0u;
+          // a real step adds its sums even where no pixel of the group contributed (zeros; 0.5 % of
+          // the steps): only the stand-ins add nothing
           group_reduce16<GL, SUN>(v);
           constexpr int F = 16 / GL;  // fields summed by each lane
           float* dst = gtile + (size_t)kk * kGradFields;
 #pragma unroll
           for (int r = 0; r < F / 4; ++r) {
             // a sun view's fields 12 .. 15 (normal z, colour) are zero
-            if (gany && !(SUN && F * gl + 4 * r >= 12)) red_add_v4(dst + 4 * r, v[4 * r], v[4 * r + 1], v[4 * r + 2], v[4 * r + 3]);
+            if (ok && !(SUN && F * gl + 4 * r >= 12)) red_add_v4(dst + 4 * r, v[4 * r], v[4 * r + 1], v[4 * r + 2], v[4 * r + 3]);
           }
         }
       };
